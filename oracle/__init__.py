@@ -1,0 +1,8 @@
+"""FP64 CPU oracle (test infrastructure only; never imported by the product path)."""
+from .oracle import (build, using, compile_source, matrices, backproject, backproject_slab, backproject_points,
+                     forward_project, ramp_filter, fdk, phantom_project, siddon,
+                     voxel_centres, default_angles, num_threads)
+
+__all__ = ["build", "using", "compile_source", "matrices", "backproject", "backproject_slab", "backproject_points",
+           "forward_project", "ramp_filter", "fdk", "phantom_project", "siddon",
+           "voxel_centres", "default_angles", "num_threads"]
