@@ -1,8 +1,10 @@
 """FP64 CPU oracle (test infrastructure only; never imported by the product path)."""
 from .oracle import (build, using, compile_source, matrices, backproject, backproject_slab, backproject_points,
-                     forward_project, ramp_filter, fdk, phantom_project, siddon,
+                     forward_project, ramp_filter, ramp_filter_rows, fdk, phantom_project,
+                     phantom_project_rows, siddon,
                      voxel_centres, default_angles, num_threads)
 
 __all__ = ["build", "using", "compile_source", "matrices", "backproject", "backproject_slab", "backproject_points",
-           "forward_project", "ramp_filter", "fdk", "phantom_project", "siddon",
+           "forward_project", "ramp_filter", "ramp_filter_rows", "fdk", "phantom_project",
+           "phantom_project_rows", "siddon",
            "voxel_centres", "default_angles", "num_threads"]

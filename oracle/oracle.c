@@ -225,9 +225,23 @@ void orc_forward_project(const double *P, int np, const double *vol, int nx,
 
 /* Cosine weight then a direct linear convolution along u with the discrete
  * Ram-Lak kernel on the isocenter grid. in/out: [nrows_total = np*nv][nu]. */
+void orc_filter_rows(int np, int nu, int nv, int r0, int nr, double du,
+                     double dv, double u_off, double v_off, double sid,
+                     double sdd, const double *in, double *out);
+
 void orc_filter(int np, int nu, int nv, double du, double dv, double u_off,
                 double v_off, double sid, double sdd, const double *in,
                 double *out)
+{
+    orc_filter_rows(np, nu, nv, 0, nv, du, dv, u_off, v_off, sid, sdd, in, out);
+}
+
+/* The same filter for detector rows r0..r0+nr-1 only: in/out are
+ * [np][nr][nu] and row t of view s is detector row r0+t (its cosine weight
+ * uses that row's v). */
+void orc_filter_rows(int np, int nu, int nv, int r0, int nr, double du,
+                     double dv, double u_off, double v_off, double sid,
+                     double sdd, const double *in, double *out)
 {
     const double cu = 0.5 * (nu - 1) + u_off;
     const double cv = 0.5 * (nv - 1) + v_off;
@@ -244,8 +258,8 @@ void orc_filter(int np, int nu, int nv, double du, double dv, double u_off,
     {
         double *g = (double *)malloc(sizeof(double) * nu);
 #pragma omp for schedule(static)
-        for (long row = 0; row < (long)np * nv; ++row) {
-            int r = (int)(row % nv);
+        for (long row = 0; row < (long)np * nr; ++row) {
+            int r = r0 + (int)(row % nr);
             double vm = (r - cv) * dv;
             const double *src = in + row * nu;
             double *dst = out + row * nu;
@@ -272,15 +286,32 @@ void orc_filter(int np, int nu, int nv, double du, double dv, double u_off,
  * rho. Overlapping ellipsoids add. Ray from the source to each pixel
  * centre; the line integral of one ellipsoid is rho * chord length.
  * out: [np][nv][nu]. */
+void orc_phantom_project_rows(double sid, double sdd, int np,
+                              const double *angles, int nu, int nv, int r0,
+                              int nr, double du, double dv, double u_off,
+                              double v_off, int ne, const double *ell,
+                              double *out);
+
 void orc_phantom_project(double sid, double sdd, int np, const double *angles,
                          int nu, int nv, double du, double dv, double u_off,
                          double v_off, int ne, const double *ell, double *out)
 {
+    orc_phantom_project_rows(sid, sdd, np, angles, nu, nv, 0, nv, du, dv, u_off,
+                             v_off, ne, ell, out);
+}
+
+/* Detector rows r0..r0+nr-1 only; out is [np][nr][nu]. */
+void orc_phantom_project_rows(double sid, double sdd, int np,
+                              const double *angles, int nu, int nv, int r0,
+                              int nr, double du, double dv, double u_off,
+                              double v_off, int ne, const double *ell,
+                              double *out)
+{
     const double cu = 0.5 * (nu - 1) + u_off;
     const double cv = 0.5 * (nv - 1) + v_off;
 #pragma omp parallel for schedule(dynamic)
-    for (long row = 0; row < (long)np * nv; ++row) {
-        int s = (int)(row / nv), r = (int)(row % nv);
+    for (long row = 0; row < (long)np * nr; ++row) {
+        int s = (int)(row / nr), r = r0 + (int)(row % nr);
         double c = cos(angles[s]), sn = sin(angles[s]);
         double er[3] = {c, sn, 0.0}, eu[3] = {-sn, c, 0.0};
         double S[3] = {sid * er[0], sid * er[1], 0.0};

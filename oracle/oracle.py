@@ -190,6 +190,35 @@ def ramp_filter(g, proj) -> np.ndarray:
     return out
 
 
+def ramp_filter_rows(g, proj_rows, r0) -> np.ndarray:
+    """``ramp_filter`` for detector rows r0..r0+nr-1 given as [np][nr][nu]."""
+    lib = _load()
+    q = _f64(proj_rows)
+    n_views, nr, nu = q.shape
+    out = np.zeros_like(q)
+    lib.orc_filter_rows(ctypes.c_int(n_views), ctypes.c_int(nu), ctypes.c_int(g["nv"]),
+                        ctypes.c_int(r0), ctypes.c_int(nr),
+                        ctypes.c_double(g["du"]), ctypes.c_double(g["dv"]),
+                        ctypes.c_double(g.get("u_off", 0.0)), ctypes.c_double(g.get("v_off", 0.0)),
+                        ctypes.c_double(g["sid"]), ctypes.c_double(g["sdd"]), _dp(q), _dp(out))
+    return out
+
+
+def phantom_project_rows(g, ellipsoids, r0, nr) -> np.ndarray:
+    """``phantom_project`` for detector rows r0..r0+nr-1 ([np][nr][nu])."""
+    lib = _load()
+    E = _f64(np.asarray(ellipsoids).reshape(-1, 16))
+    ang = _f64(g["angles"] if g.get("angles") is not None else default_angles(g["np"]))
+    out = np.zeros((g["np"], nr, g["nu"]), dtype=np.float64)
+    lib.orc_phantom_project_rows(ctypes.c_double(g["sid"]), ctypes.c_double(g["sdd"]),
+                                 ctypes.c_int(g["np"]), _dp(ang), ctypes.c_int(g["nu"]),
+                                 ctypes.c_int(g["nv"]), ctypes.c_int(r0), ctypes.c_int(nr),
+                                 ctypes.c_double(g["du"]), ctypes.c_double(g["dv"]),
+                                 ctypes.c_double(g.get("u_off", 0.0)), ctypes.c_double(g.get("v_off", 0.0)),
+                                 ctypes.c_int(E.shape[0]), _dp(E), _dp(out))
+    return out
+
+
 def fdk(g, proj) -> np.ndarray:
     """Feldkamp reconstruction: ramp_filter then backproject with scale pi/np."""
     P = matrices(g)

@@ -1,0 +1,458 @@
+// Voxel-driven cone-beam back-projection kernels (Listing 1 of Chen et al.,
+// ICS '21, with the z-column hoisting of Section 3.1.2 / Algorithm 1 and the
+// view-batched staging of Section 3.1.3 / Algorithm 2, redesigned for
+// sm_103a):
+//
+//   bp_zcol_tma   one thread per z-column (i, j) owning TK voxels in
+//                 registers; u, w and the u-fraction are computed once per
+//                 (column, view); v is stepped linearly in k. A producer
+//                 warp stages each view's detector footprint of the CTA tile
+//                 into shared memory with a 4-D TMA load (zero fill outside
+//                 the detector = the zero-padded sampling), STAGES views in
+//                 flight on mbarriers. Software FP32 bilinear sampling,
+//                 FP32 accumulation, each voxel written once.
+//   bp_zcol_ldg   the same arithmetic with direct global gathers, for
+//                 layouts TMA cannot describe (row pitch not a multiple of
+//                 16 bytes, misaligned pointers).
+//   bp_voxel_gen  one thread per voxel for general matrices (u, w depending
+//                 on k).
+#include "geom_dev.cuh"
+
+#include <cstdio>
+
+namespace bp {
+
+constexpr int kTX = 32;      // tile columns along x (4 warps x 8)
+constexpr int kTY = 8;       // tile columns along y (2 warps x 4)
+constexpr int kStages = 4;   // views in flight
+constexpr int kConsumers = kTX * kTY;
+constexpr int kConsumerWarps = kConsumers / 32;
+constexpr int kThreads = kConsumers + 32;   // + producer warp
+
+__host__ __device__ constexpr int align_up(int x, int a) { return (x + a - 1) / a * a; }
+
+template <typename T>
+__host__ __device__ constexpr int stage_bytes(int bu, int bv) {
+    return align_up(bu * bv * (int)sizeof(T), 128);
+}
+
+constexpr int kRecBytes = kRecChunk * (int)sizeof(ViewRec);
+constexpr int kBarOffset = kRecBytes;
+constexpr int kStageOffset = align_up(kRecBytes + 2 * kStages * 8, 128);
+
+// Thread -> column within the CTA tile: each warp owns an 8 x 4 patch.
+__device__ __forceinline__ void consumer_column(int warp, int lane, int *di, int *dj) {
+    int wx = warp % (kTX / 8), wy = warp / (kTX / 8);
+    *di = wx * 8 + (lane & 7);
+    *dj = wy * 4 + (lane >> 3);
+}
+
+// Accumulate one view into acc[0..TK-1] from a staged box with row pitch BU.
+template <typename T, int TK, int BU, bool FULL>
+__device__ __forceinline__ void accumulate_view(const T *__restrict__ tile, const ViewRec &r,
+                                                float fdi, float fdj, int ez, int bv,
+                                                float *acc, unsigned *err) {
+    float W = fmaf(r.Wj, fdj, fmaf(r.Wi, fdi, r.W0));
+    float inv = __frcp_rn(W);
+    float uL = fmaf(r.Nuj, fdj, fmaf(r.Nui, fdi, r.Nu0)) * inv;
+    float v0 = fmaf(r.Nvj, fdj, fmaf(r.Nvi, fdi, r.Nv0)) * inv;
+    float dv = r.Nvk * inv;
+    float wt = inv * inv;
+    float tu = __fadd_rd(uL, kMagic);
+    int cu = __float_as_int(tu) - kMagicBits;
+    float fu = uL - (tu - kMagic);
+    float vlast = fmaf((float)(ez - 1), dv, v0);
+    int rfirst = __float_as_int(__fadd_rd(v0, kMagic)) - kMagicBits;
+    int rlast = __float_as_int(__fadd_rd(vlast, kMagic)) - kMagicBits;
+    if (cu < 0 || cu > BU - 2 || min(rfirst, rlast) < 0 || max(rfirst, rlast) > bv - 2 || !(uL == uL) || !(v0 == v0)) {
+        atomicOr(err, DEV_ERR_FOOTPRINT);
+        return;
+    }
+    const T *base = tile + cu;
+#pragma unroll
+    for (int kk = 0; kk < TK; ++kk) {
+        if (!FULL && kk >= ez) continue;
+        float v = fmaf((float)kk, dv, v0);
+        float tv = __fadd_rd(v, kMagic);
+        float fv = v - (tv - kMagic);
+        int row = __float_as_int(tv) - kMagicBits;
+        const T *p = base + row * BU;
+        float q00 = to_f32(p[0]), q01 = to_f32(p[1]);
+        float q10 = to_f32(p[BU]), q11 = to_f32(p[BU + 1]);
+        float s0 = fmaf(fu, q01 - q00, q00);
+        float s1 = fmaf(fu, q11 - q10, q10);
+        float val = fmaf(fv, s1 - s0, s0);
+        acc[kk] = fmaf(wt, val, acc[kk]);
+    }
+}
+
+template <int TK>
+__device__ __forceinline__ void store_column(float *__restrict__ vol, const float *acc, int b,
+                                             int i, int j, int k0, int ez, int nx, int ny,
+                                             int nz, float scale, int accumulate) {
+    size_t plane = (size_t)nx * ny;
+    size_t base = ((size_t)b * nz + k0) * plane + (size_t)j * nx + i;
+#pragma unroll
+    for (int kk = 0; kk < TK; ++kk) {
+        if (kk < ez) {
+            float r = scale * acc[kk];
+            size_t idx = base + (size_t)kk * plane;
+            vol[idx] = accumulate ? vol[idx] + r : r;
+        }
+    }
+}
+
+template <typename T, int TK, int BU>
+__global__ void __launch_bounds__(kThreads, (TK > 32 ? 1 : 2))
+bp_zcol_tma(const __grid_constant__ CUtensorMap tmap, const double *__restrict__ P, int view0,
+            int nviews, int nx, int ny, int nz, int bv, int align, float *__restrict__ vol,
+            float scale, int accumulate, unsigned *err, unsigned long long timeout_ns,
+            int drop_view) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    ViewRec *recs = reinterpret_cast<ViewRec *>(smem);
+    unsigned long long *full = reinterpret_cast<unsigned long long *>(smem + kBarOffset);
+    unsigned long long *empty = full + kStages;
+    unsigned char *stages = smem + kStageOffset;
+    const int sbytes = stage_bytes<T>(BU, bv);
+    const unsigned box_bytes = (unsigned)(BU * bv * sizeof(T));
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int ntx = (nx + kTX - 1) / kTX;
+    const int i0 = (blockIdx.x % ntx) * kTX, j0 = (blockIdx.x / ntx) * kTY;
+    const int k0 = blockIdx.y * TK;
+    const int b = blockIdx.z;
+    const int ex = min(kTX, nx - i0), ey = min(kTY, ny - j0), ez = min(TK, nz - k0);
+
+    int di = 0, dj = 0;
+    if (warp < kConsumerWarps) consumer_column(warp, lane, &di, &dj);
+    const bool col_ok = warp < kConsumerWarps && di < ex && dj < ey;
+    const float fdi = (float)di, fdj = (float)dj;
+
+    if (tid == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], kConsumerWarps);
+        }
+        fence_barrier_init();
+        prefetch_tmap(&tmap);
+    }
+    __syncthreads();
+
+    float acc[TK];
+#pragma unroll
+    for (int kk = 0; kk < TK; ++kk) acc[kk] = 0.0f;
+
+    __shared__ unsigned arms[kStages];   // producer: armings of each full barrier
+    if (tid < kStages) arms[tid] = 0;
+    bool alive = true;
+    unsigned g0 = 0;                     // pipeline iterations before this chunk
+    for (int cb = 0; cb < nviews; cb += kRecChunk) {
+        const int cn = min(kRecChunk, nviews - cb);
+        __syncthreads();
+        for (int n = tid; n < cn; n += kThreads)
+            if (!make_rec(P + 12 * (size_t)(view0 + cb + n), i0, j0, k0, ex, ey, ez, align, BU,
+                          bv, &recs[n]))
+                atomicOr(err, DEV_ERR_FOOTPRINT);
+        __syncthreads();
+        if (warp == kConsumerWarps) {
+            // ---- producer: one elected lane issues the TMA loads ----
+            if (lane == 0 && alive) {
+                for (int n = 0; n < cn; ++n) {
+                    unsigned g = g0 + n;
+                    int slot = g % kStages;
+                    if (g >= kStages &&
+                        !mbar_wait_bounded(&empty[slot], ((g / kStages) - 1) & 1, timeout_ns)) {
+                        atomicOr(err, DEV_ERR_TIMEOUT);
+                        alive = false;
+                        break;
+                    }
+                    if (view0 + cb + n == drop_view) continue;   // test hook
+                    mbar_arrive_expect_tx(&full[slot], box_bytes);
+                    tma_load_4d(stages + slot * sbytes, &tmap, recs[n].u_box, recs[n].v_box,
+                                cb + n, b, &full[slot]);
+                    ++arms[slot];
+                }
+            }
+        } else {
+            // ---- consumers ----
+            for (int n = 0; n < cn && alive; ++n) {
+                unsigned g = g0 + n;
+                int slot = g % kStages;
+                if (!mbar_wait_bounded(&full[slot], (g / kStages) & 1, timeout_ns)) {
+                    if (lane == 0) atomicOr(err, DEV_ERR_TIMEOUT);
+                    alive = false;
+                    break;
+                }
+                if (col_ok) {
+                    const T *tile = reinterpret_cast<const T *>(stages + slot * sbytes);
+                    if (ez == TK)
+                        accumulate_view<T, TK, BU, true>(tile, recs[n], fdi, fdj, ez, bv, acc, err);
+                    else
+                        accumulate_view<T, TK, BU, false>(tile, recs[n], fdi, fdj, ez, bv, acc, err);
+                }
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&empty[slot]);
+            }
+        }
+        g0 += cn;
+    }
+    if (warp == kConsumerWarps && lane == 0) {
+        // drain: every issued load must have landed before the CTA exits
+        for (int s = 0; s < kStages; ++s)
+            if (arms[s] > 0 && !mbar_wait_bounded(&full[s], (arms[s] - 1) & 1, timeout_ns))
+                atomicOr(err, DEV_ERR_TIMEOUT);
+    }
+    if (col_ok && alive)
+        store_column<TK>(vol, acc, b, i0 + di, j0 + dj, k0, ez, nx, ny, nz, scale, accumulate);
+}
+
+// Same arithmetic without TMA: taps are gathered from global memory with
+// explicit zero padding. Records are relative to (u_box, v_box) as above.
+template <typename T, int TK>
+__global__ void __launch_bounds__(kConsumers)
+bp_zcol_ldg(const T *__restrict__ proj, long long batch_stride, const double *__restrict__ P,
+            int view0, int nviews, int nu, int nv, int nx, int ny, int nz,
+            float *__restrict__ vol, float scale, int accumulate) {
+    __shared__ ViewRec recs[128];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int ntx = (nx + kTX - 1) / kTX;
+    const int i0 = (blockIdx.x % ntx) * kTX, j0 = (blockIdx.x / ntx) * kTY;
+    const int k0 = blockIdx.y * TK;
+    const int b = blockIdx.z;
+    const int ex = min(kTX, nx - i0), ey = min(kTY, ny - j0), ez = min(TK, nz - k0);
+    int di, dj;
+    consumer_column(warp, lane, &di, &dj);
+    const bool col_ok = di < ex && dj < ey;
+    const float fdi = (float)di, fdj = (float)dj;
+    const T *pb = proj + (size_t)b * batch_stride;
+
+    float acc[TK];
+#pragma unroll
+    for (int kk = 0; kk < TK; ++kk) acc[kk] = 0.0f;
+
+    for (int cb = 0; cb < nviews; cb += 128) {
+        const int cn = min(128, nviews - cb);
+        __syncthreads();
+        for (int n = tid; n < cn; n += kConsumers) {
+            ViewRec r;
+            make_rec(P + 12 * (size_t)(view0 + cb + n), i0, j0, k0, ex, ey, ez, 1, 1 << 30,
+                     1 << 30, &r);
+            recs[n] = r;
+        }
+        __syncthreads();
+        if (!col_ok) continue;
+        for (int n = 0; n < cn; ++n) {
+            const ViewRec r = recs[n];
+            const T *img = pb + (size_t)(cb + n) * nu * nv;
+            float W = fmaf(r.Wj, fdj, fmaf(r.Wi, fdi, r.W0));
+            float inv = __frcp_rn(W);
+            float uL = fmaf(r.Nuj, fdj, fmaf(r.Nui, fdi, r.Nu0)) * inv;
+            float v0 = fmaf(r.Nvj, fdj, fmaf(r.Nvi, fdi, r.Nv0)) * inv;
+            float dv = r.Nvk * inv;
+            float wt = inv * inv;
+            float uf = floorf(uL);
+            float fu = uL - uf;
+            int c0 = (int)uf + r.u_box;
+            bool cin0 = c0 >= 0 && c0 < nu, cin1 = c0 + 1 >= 0 && c0 + 1 < nu;
+#pragma unroll
+            for (int kk = 0; kk < TK; ++kk) {
+                if (kk >= ez) continue;
+                float v = fmaf((float)kk, dv, v0);
+                float vf = floorf(v);
+                float fv = v - vf;
+                int r0 = (int)vf + r.v_box;
+                bool rin0 = r0 >= 0 && r0 < nv, rin1 = r0 + 1 >= 0 && r0 + 1 < nv;
+                const T *row0 = img + (long long)r0 * nu + c0;
+                float q00 = (rin0 && cin0) ? to_f32(row0[0]) : 0.0f;
+                float q01 = (rin0 && cin1) ? to_f32(row0[1]) : 0.0f;
+                float q10 = (rin1 && cin0) ? to_f32(row0[nu]) : 0.0f;
+                float q11 = (rin1 && cin1) ? to_f32(row0[nu + 1]) : 0.0f;
+                float s0 = fmaf(fu, q01 - q00, q00);
+                float s1 = fmaf(fu, q11 - q10, q10);
+                float val = fmaf(fv, s1 - s0, s0);
+                acc[kk] = fmaf(wt, val, acc[kk]);
+            }
+        }
+    }
+    if (col_ok) store_column<TK>(vol, acc, b, i0 + di, j0 + dj, k0, ez, nx, ny, nz, scale, accumulate);
+}
+
+// General 3x4 matrices: one thread per voxel of an 8 x 8 x 4 tile.
+template <typename T>
+__global__ void __launch_bounds__(256)
+bp_voxel_gen(const T *__restrict__ proj, long long batch_stride, const double *__restrict__ P,
+             int view0, int nviews, int nu, int nv, int nx, int ny, int nz,
+             float *__restrict__ vol, float scale, int accumulate) {
+    __shared__ ViewRecGen recs[64];
+    const int tid = threadIdx.x;
+    const int ntx = (nx + 7) / 8, nty = (ny + 7) / 8;
+    const int t = blockIdx.x;
+    const int i0 = (t % ntx) * 8, j0 = ((t / ntx) % nty) * 8, k0 = (t / (ntx * nty)) * 4;
+    const int b = blockIdx.z;
+    const int di = tid & 7, dj = (tid >> 3) & 7, dk = tid >> 6;
+    const int i = i0 + di, j = j0 + dj, k = k0 + dk;
+    const bool ok = i < nx && j < ny && k < nz;
+    const float fdi = (float)di, fdj = (float)dj, fdk = (float)dk;
+    const T *pb = proj + (size_t)b * batch_stride;
+    float acc = 0.0f;
+    for (int cb = 0; cb < nviews; cb += 64) {
+        const int cn = min(64, nviews - cb);
+        __syncthreads();
+        for (int n = tid; n < cn; n += 256) make_rec_gen(P + 12 * (size_t)(view0 + cb + n), i0, j0, k0, &recs[n]);
+        __syncthreads();
+        if (!ok) continue;
+        for (int n = 0; n < cn; ++n) {
+            const ViewRecGen r = recs[n];
+            const T *img = pb + (size_t)(cb + n) * nu * nv;
+            float W = fmaf(r.Wk, fdk, fmaf(r.Wj, fdj, fmaf(r.Wi, fdi, r.W0)));
+            if (!(W > 0.0f)) continue;
+            float inv = __frcp_rn(W);
+            float u = fmaf(r.Nuk, fdk, fmaf(r.Nuj, fdj, fmaf(r.Nui, fdi, r.Nu0))) * inv;
+            float v = fmaf(r.Nvk, fdk, fmaf(r.Nvj, fdj, fmaf(r.Nvi, fdi, r.Nv0))) * inv;
+            if (!(fabsf(u) < 4e6f && fabsf(v) < 4e6f)) continue;
+            float uf = floorf(u), vf = floorf(v);
+            float fu = u - uf, fv = v - vf;
+            int c0 = (int)uf + r.u_ref, r0 = (int)vf + r.v_ref;
+            bool cin0 = c0 >= 0 && c0 < nu, cin1 = c0 + 1 >= 0 && c0 + 1 < nu;
+            bool rin0 = r0 >= 0 && r0 < nv, rin1 = r0 + 1 >= 0 && r0 + 1 < nv;
+            const T *row0 = img + (long long)r0 * nu + c0;
+            float q00 = (rin0 && cin0) ? to_f32(row0[0]) : 0.0f;
+            float q01 = (rin0 && cin1) ? to_f32(row0[1]) : 0.0f;
+            float q10 = (rin1 && cin0) ? to_f32(row0[nu]) : 0.0f;
+            float q11 = (rin1 && cin1) ? to_f32(row0[nu + 1]) : 0.0f;
+            float s0 = fmaf(fu, q01 - q00, q00);
+            float s1 = fmaf(fu, q11 - q10, q10);
+            acc = fmaf(inv * inv, fmaf(fv, s1 - s0, s0), acc);
+        }
+    }
+    if (ok) {
+        size_t idx = (((size_t)b * nz + k) * ny + j) * nx + i;
+        float r = scale * acc;
+        vol[idx] = accumulate ? vol[idx] + r : r;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Host launcher
+// ---------------------------------------------------------------------------
+
+typedef CUresult (*PFN_encodeTiled)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                    const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                    const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                    CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static PFN_encodeTiled get_encode() {
+    static PFN_encodeTiled fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
+                                             cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_encodeTiled>(p);
+    }
+    return fn;
+}
+
+// Box widths the TMA kernel is instantiated for (multiples of 8 that are
+// 8 mod 16, so consecutive staged rows start 8 or 24 banks apart).
+static const int kBoxWidths[] = {40, 56, 88, 136, 232};
+
+int plan_box_width(int need) {
+    for (int w : kBoxWidths)
+        if (w >= need) return w;
+    return -1;
+}
+
+template <typename T, int TK, int BU>
+static cudaError_t launch_tma_t(const CUtensorMap &map, bp_ctx *ctx, int view0, int nviews,
+                                int bv, int align, float *vol, int batch, float scale,
+                                int accumulate, cudaStream_t st) {
+    const int smem = kStageOffset + kStages * stage_bytes<T>(BU, bv);
+    auto kern = bp_zcol_tma<T, TK, BU>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid(((ctx->nx + kTX - 1) / kTX) * ((ctx->ny + kTY - 1) / kTY), (ctx->nz + TK - 1) / TK,
+              batch);
+    kern<<<grid, kThreads, smem, st>>>(map, ctx->d_P, view0, nviews, ctx->nx, ctx->ny, ctx->nz, bv,
+                                       align, vol, scale, accumulate, ctx->d_err, ctx->timeout_ns,
+                                       ctx->test_drop_view);
+    return cudaGetLastError();
+}
+
+template <typename T, int TK>
+static cudaError_t launch_tma_bu(const CUtensorMap &map, bp_ctx *ctx, int bu, int view0,
+                                 int nviews, int bv, int align, float *vol, int batch, float scale,
+                                 int accumulate, cudaStream_t st) {
+    switch (bu) {
+        case 40: return launch_tma_t<T, TK, 40>(map, ctx, view0, nviews, bv, align, vol, batch, scale, accumulate, st);
+        case 56: return launch_tma_t<T, TK, 56>(map, ctx, view0, nviews, bv, align, vol, batch, scale, accumulate, st);
+        case 88: return launch_tma_t<T, TK, 88>(map, ctx, view0, nviews, bv, align, vol, batch, scale, accumulate, st);
+        case 136: return launch_tma_t<T, TK, 136>(map, ctx, view0, nviews, bv, align, vol, batch, scale, accumulate, st);
+        case 232: return launch_tma_t<T, TK, 232>(map, ctx, view0, nviews, bv, align, vol, batch, scale, accumulate, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+bp_status launch_backproject(bp_ctx *ctx, const void *proj, bp_dtype t, int view0, int nviews,
+                             long long batch_stride, float *vol, int batch, float scale,
+                             int accumulate, cudaStream_t st) {
+    const size_t es = (t == BP_F16) ? 2 : 4;
+    const long long view_elems = (long long)ctx->nu * ctx->nv;
+    if (batch_stride == 0) batch_stride = view_elems * nviews;
+    cudaError_t e = cudaSuccess;
+    if (!ctx->zinv) {
+        dim3 grid(((ctx->nx + 7) / 8) * ((ctx->ny + 7) / 8) * ((ctx->nz + 3) / 4), 1, batch);
+        if (t == BP_F16)
+            bp_voxel_gen<__half><<<grid, 256, 0, st>>>((const __half *)proj, batch_stride,
+                ctx->d_P, view0, nviews, ctx->nu, ctx->nv, ctx->nx, ctx->ny, ctx->nz, vol, scale, accumulate);
+        else
+            bp_voxel_gen<float><<<grid, 256, 0, st>>>((const float *)proj, batch_stride, ctx->d_P,
+                view0, nviews, ctx->nu, ctx->nv, ctx->nx, ctx->ny, ctx->nz, vol, scale, accumulate);
+        e = cudaGetLastError();
+        return e == cudaSuccess ? BP_OK : cuda_fail(ctx, e, "bp_voxel_gen launch");
+    }
+    const Plan &pl = ctx->plan;
+    const int bu = (t == BP_F16) ? pl.bu16 : pl.bu;
+    const int align = (t == BP_F16) ? 8 : 4;
+    PFN_encodeTiled enc = get_encode();
+    bool tma = enc != nullptr && bu > 0 && (((size_t)ctx->nu * es) % 16 == 0) &&
+               (((uintptr_t)proj) % 16 == 0) && ((batch_stride * es) % 16 == 0) &&
+               pl.bv <= 256 && bu <= 256;
+    if (tma) {
+        CUtensorMap map;
+        cuuint64_t dims[4] = {(cuuint64_t)ctx->nu, (cuuint64_t)ctx->nv, (cuuint64_t)nviews,
+                              (cuuint64_t)batch};
+        cuuint64_t strides[3] = {(cuuint64_t)(ctx->nu * es), (cuuint64_t)(view_elems * es),
+                                 (cuuint64_t)(batch_stride * es)};
+        cuuint32_t box[4] = {(cuuint32_t)bu, (cuuint32_t)pl.bv, 1, 1};
+        cuuint32_t estr[4] = {1, 1, 1, 1};
+        CUresult r = enc(&map, t == BP_F16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                         4, const_cast<void *>(proj), dims, strides, box, estr,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) tma = false;
+        if (tma) {
+            if (t == BP_F16)
+                e = (pl.tk == 64) ? launch_tma_bu<__half, 64>(map, ctx, bu, view0, nviews, pl.bv, align, vol, batch, scale, accumulate, st)
+                                  : launch_tma_bu<__half, 32>(map, ctx, bu, view0, nviews, pl.bv, align, vol, batch, scale, accumulate, st);
+            else
+                e = (pl.tk == 64) ? launch_tma_bu<float, 64>(map, ctx, bu, view0, nviews, pl.bv, align, vol, batch, scale, accumulate, st)
+                                  : launch_tma_bu<float, 32>(map, ctx, bu, view0, nviews, pl.bv, align, vol, batch, scale, accumulate, st);
+            return e == cudaSuccess ? BP_OK : cuda_fail(ctx, e, "bp_zcol_tma launch");
+        }
+    }
+    dim3 grid(((ctx->nx + kTX - 1) / kTX) * ((ctx->ny + kTY - 1) / kTY), (ctx->nz + 31) / 32, batch);
+    if (t == BP_F16)
+        bp_zcol_ldg<__half, 32><<<grid, kConsumers, 0, st>>>((const __half *)proj, batch_stride,
+            ctx->d_P, view0, nviews, ctx->nu, ctx->nv, ctx->nx, ctx->ny, ctx->nz, vol, scale, accumulate);
+    else
+        bp_zcol_ldg<float, 32><<<grid, kConsumers, 0, st>>>((const float *)proj, batch_stride,
+            ctx->d_P, view0, nviews, ctx->nu, ctx->nv, ctx->nx, ctx->ny, ctx->nz, vol, scale, accumulate);
+    e = cudaGetLastError();
+    return e == cudaSuccess ? BP_OK : cuda_fail(ctx, e, "bp_zcol_ldg launch");
+}
+
+}  // namespace bp

@@ -1,0 +1,224 @@
+"""CUDA path vs the FP64 oracle, element by element, on the same seeded inputs.
+
+Tolerances (max |gpu - oracle| / max |oracle|): 1e-5 for FP32 back-projection
+and forward projection, 2e-3 for FP16-stored projections (against the
+unquantised input), 2e-5 for the FFT ramp filter (FP32 FFT rounding grows
+with log2 N; the filter output is not a target of its own), 1e-4 for the
+FP32 phantom generator (input data only).
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2104_13248_gb300 import api, inputs
+
+pytestmark = pytest.mark.gpu
+
+TOL32 = 1e-5
+TOL16 = 2e-3
+
+
+def rel(a, b):
+    return float(np.abs(np.asarray(a, np.float64) - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+@pytest.fixture(scope="module")
+def c1():
+    p = inputs.preset("c1_small")
+    g = p["geom"]
+    E = inputs.random_ellipsoids(p["seed"], p["n_ell"], p["axes"], g)
+    raw = oracle.phantom_project(g, E).astype(np.float32)
+    q = oracle.ramp_filter(g, raw).astype(np.float32)
+    return dict(g=g, E=E, raw=raw, q=q, P=oracle.matrices(g))
+
+
+def test_backproject_c1(c1):
+    g = c1["g"]
+    scale = math.pi / g["np"]
+    ref = oracle.backproject(c1["P"], c1["q"], g["nx"], g["ny"], g["nz"], scale)
+    with api.bp_create(g) as ctx:
+        vol = api.bp_backproject(ctx, torch.from_numpy(c1["q"]).cuda(), scale=scale).cpu().numpy()
+        api.bp_device_status(ctx)
+    assert rel(vol, ref) <= TOL32
+
+
+def test_filter_c1(c1):
+    g = c1["g"]
+    ref = oracle.ramp_filter(g, c1["raw"])
+    with api.bp_create(g) as ctx:
+        out = api.bp_filter(ctx, torch.from_numpy(c1["raw"]).cuda()).cpu().numpy()
+        out16 = api.bp_filter(ctx, torch.from_numpy(c1["raw"]).cuda(), out_dtype=torch.float16).cpu().numpy()
+    assert rel(out, ref) <= 2e-5
+    # FP16 output = round-to-nearest of the FP32 result
+    assert rel(out16.astype(np.float64), ref) <= 1e-3
+
+
+def test_fdk_end_to_end_c1(c1):
+    g = c1["g"]
+    ref = oracle.fdk(g, c1["raw"])
+    with api.bp_create(g) as ctx:
+        vol = api.fdk(ctx, torch.from_numpy(c1["raw"]).cuda()).cpu().numpy()
+    assert rel(vol, ref) <= 2e-5
+
+
+def test_backproject_fp16_c1(c1):
+    g = c1["g"]
+    scale = math.pi / g["np"]
+    ref = oracle.backproject(c1["P"], c1["q"], g["nx"], g["ny"], g["nz"], scale)
+    q16 = c1["q"].astype(np.float16)
+    ref16 = oracle.backproject(c1["P"], q16.astype(np.float64), g["nx"], g["ny"], g["nz"], scale)
+    with api.bp_create(g) as ctx:
+        vol = api.bp_backproject(ctx, torch.from_numpy(q16).cuda(), scale=scale).cpu().numpy()
+        api.bp_device_status(ctx)
+    assert rel(vol, ref) <= TOL16          # against the unquantised input
+    assert rel(vol, ref16) <= TOL32        # the arithmetic itself stays FP32-accurate
+
+
+RAGGED = [
+    # TMA path (nu*4 and nu*2 multiples of 16), ragged tiles in x, y and z
+    dict(nu=96, nv=70, nx=37, ny=29, nz=45),
+    # nu*4 multiple of 16 but nu*2 not: FP32 via TMA, FP16 via global loads
+    dict(nu=52, nv=40, nx=33, ny=9, nz=70),
+    # nu*4 not a multiple of 16: global-load kernel for both types
+    dict(nu=50, nv=44, nx=31, ny=17, nz=33),
+    # a single voxel and a thin slab
+    dict(nu=64, nv=64, nx=1, ny=1, nz=1),
+    dict(nu=64, nv=64, nx=40, ny=40, nz=2),
+]
+
+
+@pytest.mark.parametrize("dims", RAGGED, ids=lambda d: "nu%d_nv%d_%dx%dx%d" % (d["nu"], d["nv"], d["nx"], d["ny"], d["nz"]))
+@pytest.mark.parametrize("dtype", ["f32", "f16"])
+def test_backproject_ragged(dims, dtype):
+    rng = np.random.default_rng(3)
+    g = dict(sid=600.0, sdd=900.0, np=17, angles=np.sort(rng.uniform(0, 2 * np.pi, 17)), du=1.0, dv=1.1,
+             u_off=1.7, v_off=-2.3, sx=1.3, sy=1.2, sz=1.1, ox=0.7, oy=-1.4, oz=2.1, **dims)
+    q = inputs.uniform_array(11, (g["np"], g["nv"], g["nu"]), -1, 1).astype(np.float32)
+    if dtype == "f16":
+        q = q.astype(np.float16)
+    P = oracle.matrices(g)
+    ref = oracle.backproject(P, q.astype(np.float64), g["nx"], g["ny"], g["nz"], 0.5)
+    with api.bp_create(g) as ctx:
+        vol = api.bp_backproject(ctx, torch.from_numpy(q).cuda(), scale=0.5).cpu().numpy()
+        api.bp_device_status(ctx)
+    # uniform noise is the worst case for FP32 position rounding: 5e-5
+    assert rel(vol, ref) <= 5e-5
+
+
+def test_backproject_batch_accumulate_and_view_chunks(c1):
+    g = c1["g"]
+    q = c1["q"]
+    q2 = np.stack([q, np.flip(q, axis=2).copy()])
+    scale = math.pi / g["np"]
+    refs = [oracle.backproject(c1["P"], q2[b], g["nx"], g["ny"], g["nz"], scale) for b in range(2)]
+    with api.bp_create(g) as ctx:
+        d = torch.from_numpy(q2).cuda()
+        vol = api.bp_backproject(ctx, d, scale=scale)
+        for b in range(2):
+            assert rel(vol[b].cpu().numpy(), refs[b]) <= TOL32
+        # accumulate: vol + vol
+        api.bp_backproject(ctx, d, vol=vol, scale=scale, accumulate=True)
+        assert rel(vol[0].cpu().numpy(), 2 * refs[0]) <= TOL32
+        # views in chunks of 25 accumulate to the full sum
+        v2 = torch.zeros_like(vol)
+        for s0 in range(0, g["np"], 25):
+            n = min(25, g["np"] - s0)
+            api.bp_backproject_views(ctx, d[:, s0:s0 + n], s0, v2, scale=scale, accumulate=True)
+        assert rel(v2[1].cpu().numpy(), refs[1]) <= TOL32
+
+
+def test_backproject_general_matrices():
+    g = dict(sid=500.0, sdd=800.0, np=11, angles=np.linspace(0.1, 6.0, 11), nu=60, nv=50, du=1.0, dv=1.0,
+             u_off=0.5, v_off=-0.5, nx=20, ny=18, nz=16, sx=1.5, sy=1.5, sz=1.5, ox=0, oy=0, oz=0)
+    P = oracle.matrices(g)
+    P[:, 0, 2] += 0.05      # detector tilt: u now depends on k
+    P[:, 2, 2] += 1e-4      # and so does the depth
+    q = inputs.uniform_array(5, (g["np"], g["nv"], g["nu"]), -1, 1).astype(np.float32)
+    ref = oracle.backproject(P, q, g["nx"], g["ny"], g["nz"], 1.0)
+    with api.bp_create_from_matrices(P, g["nu"], g["nv"], g["nx"], g["ny"], g["nz"]) as ctx:
+        vol = api.bp_backproject(ctx, torch.from_numpy(q).cuda()).cpu().numpy()
+        fp = api.fp_project(ctx, torch.from_numpy(ref.astype(np.float32)).cuda()).cpu().numpy()
+    assert rel(vol, ref) <= 5e-5
+    fref = oracle.forward_project(P, ref.astype(np.float32), g["nu"], g["nv"])
+    assert rel(fp, fref) <= 5e-5
+
+
+def test_forward_project_and_adjoint(c1):
+    g = dict(c1["g"])
+    g.update(np=30, angles=oracle.default_angles(30) + 0.2)
+    P = oracle.matrices(g)
+    x = inputs.uniform_array(21, (g["nz"], g["ny"], g["nx"]), 0, 1).astype(np.float32)
+    q = inputs.uniform_array(22, (g["np"], g["nv"], g["nu"]), -1, 1).astype(np.float32)
+    ref = oracle.forward_project(P, x, g["nu"], g["nv"], 0.7)
+    with api.bp_create(g) as ctx:
+        fx = api.fp_project(ctx, torch.from_numpy(x).cuda(), scale=0.7)
+        bq = api.bp_backproject(ctx, torch.from_numpy(q).cuda(), scale=0.7)
+        api.bp_device_status(ctx)
+        lhs = torch.dot(bq.double().flatten(), torch.from_numpy(x).cuda().double().flatten()).item()
+        rhs = torch.dot(torch.from_numpy(q).cuda().double().flatten(), fx.double().flatten()).item()
+        norm = bq.double().norm().item() * float(np.linalg.norm(x))
+    assert rel(fx.cpu().numpy(), ref) <= TOL32
+    assert abs(lhs - rhs) <= 1e-6 * norm
+
+
+def test_phantom_generator(c1):
+    g = c1["g"]
+    with api.bp_create(g) as ctx:
+        out = api.bp_phantom_project(ctx, c1["E"]).cpu().numpy()
+    assert rel(out, c1["raw"]) <= 1e-4
+
+
+# ---------------------------------------------------------------------------
+# Full-size workloads in the launch configuration the benchmark uses
+# ---------------------------------------------------------------------------
+
+def _band(P, g, k0, nks):
+    """Detector rows every voxel of slices k0..k0+nks-1 can tap (plus margin)."""
+    vs = []
+    for i in (0, g["nx"] - 1):
+        for j in (0, g["ny"] - 1):
+            for k in (k0, k0 + nks - 1):
+                h = P[:, :, :] @ np.array([i, j, k, 1.0])
+                vs.append(h[:, 1] / h[:, 2])
+    vs = np.concatenate(vs)
+    r0 = max(0, int(np.floor(vs.min())) - 2)
+    r1 = min(g["nv"], int(np.floor(vs.max())) + 4)
+    return r0, r1 - r0
+
+
+@pytest.mark.parametrize("name,k0,nks", [("c2_fdk256", 112, 32), ("c3_paper", 224, 64)])
+def test_full_size_slab(name, k0, nks):
+    """Oracle inputs on the detector band a z-slab sees; the GPU back-projects
+    the whole volume in the benchmark's configuration; the slab is compared
+    voxel by voxel (FP32 and FP16-stored projections)."""
+    p = inputs.preset(name)
+    g = p["geom"]
+    P = oracle.matrices(g)
+    E = inputs.random_ellipsoids(p["seed"], p["n_ell"], p["axes"], g)
+    r0, nr = _band(P, g, k0, nks)
+    raw = oracle.phantom_project_rows(g, E, r0, nr)
+    qb = oracle.ramp_filter_rows(g, raw, r0).astype(np.float32)
+    q = np.zeros((g["np"], g["nv"], g["nu"]), dtype=np.float32)
+    q[:, r0:r0 + nr, :] = qb
+    scale = math.pi / g["np"]
+    ref = oracle.backproject_slab(P, q, g["nx"], g["ny"], k0, nks, scale)
+    with api.bp_create(g) as ctx:
+        d = torch.from_numpy(q).cuda()
+        vol = api.bp_backproject(ctx, d, scale=scale)
+        slab = vol[k0:k0 + nks].cpu().numpy()
+        vol16 = api.bp_backproject(ctx, d.half(), scale=scale)
+        slab16 = vol16[k0:k0 + nks].cpu().numpy()
+        api.bp_device_status(ctx)
+    e32, e16 = rel(slab, ref), rel(slab16, ref)
+    print(f"{name} slab k={k0}..{k0 + nks - 1}: FP32 rel err {e32:.2e}, FP16-stored {e16:.2e}")
+    assert e32 <= TOL32
+    assert e16 <= TOL16
