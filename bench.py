@@ -1,0 +1,349 @@
+#!/usr/bin/env python
+"""Benchmark: FDK back-projection throughput (GUPS) on GB300.
+
+One step = one FDK pass of the paper-scale workload (1248x960 detector, 496
+views over 360 deg, 512^3 volume at 0.25 mm, 50-ellipsoid phantom): the
+cosine-weighted Ram-Lak filter of every projection, then the back-projection
+of all views into the volume. GUPS = nx*ny*nz*np / t / 1e9 (the paper's
+metric). Inputs are generated on the device before timing and are larger
+than L2 (2.38 GB of projections), so no L2 flush is needed between steps.
+
+Prints one JSON line (rank 0). ``--impl reference`` times the FP64 CPU
+oracle on a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+UPD_PER_CLK_SM = 8        # smem-bound FP32 bilinear: 4 x 4-byte taps per update at 128 B/clk/SM
+
+
+def parse_args(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="c3_paper")
+    ap.add_argument("--tk", type=int, default=0, help="voxels per thread along z (32/64; 0 = plan)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args(argv)
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples every 200 ms while the timed region runs."""
+
+    FIELDS = ("index,uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid: str | None):
+        self.uuid = uuid
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            cmd = ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                   "-lms", "200", "-f", self.path]
+            if self.uuid:
+                cmd += ["-i", self.uuid]
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        return False
+
+    def summary(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        try:
+            rows = [r.split(", ") for r in open(self.path).read().strip().splitlines() if r.strip()]
+        except Exception:
+            return out
+        finally:
+            if self.path and os.path.exists(self.path):
+                os.unlink(self.path)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[2]))
+                mx.append(float(r[3]))
+                for n, v in zip(names, r[6:10]):
+                    if v.strip() == "Active":
+                        reasons.add(n)
+            except Exception:
+                continue
+        if sm:
+            out.update(sm_mhz=statistics.median(sm), sm_max_mhz=max(mx), reasons=sorted(reasons),
+                       samples=len(sm))
+        return out
+
+
+def cpu_baseline(g, budget_s=15.0, max_slices=32, chunk=4):
+    """The FP64 oracle back-projecting a z-slab of the workload on the host
+    cores (bounded: stops after ~budget_s seconds). Data: seeded uniform
+    projections (the oracle's cost does not depend on the values)."""
+    import numpy as np
+
+    import oracle
+    from paper_2104_13248_gb300 import inputs
+    P = oracle.matrices(g)
+    q = inputs.uniform_array(99, (g["np"], g["nv"], g["nu"]), -1.0, 1.0)
+    k0 = g["nz"] // 2 - max_slices // 2
+    done, t = 0, 0.0
+    while done < max_slices and t < budget_s:
+        t0 = time.perf_counter()
+        oracle.backproject_slab(P, q, g["nx"], g["ny"], k0 + done, chunk, math.pi / g["np"])
+        t += time.perf_counter() - t0
+        done += chunk
+    upd = float(g["nx"]) * g["ny"] * done * g["np"]
+    return {"value": upd / t / 1e9, "unit": "GUPS", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"FP64 oracle back-projection of slices {k0}..{k0 + done - 1} "
+                      f"({g['nx']}x{g['ny']}x{done} voxels x {g['np']} views, {upd:.3g} updates, {t:.1f} s)"}
+
+
+def run_reference(args):
+    """Reference arm: the FP64 CPU oracle timed on a bounded sample (rank 0 only)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import numpy as np
+
+    import oracle
+    from paper_2104_13248_gb300 import inputs
+    oracle.build()
+    g = inputs.preset(args.workload)["geom"]
+    P = oracle.matrices(g)
+    q = inputs.uniform_array(99, (g["np"], g["nv"], g["nu"]), -1.0, 1.0)
+    nks = 2
+    k0 = g["nz"] // 2 - 1
+    scale = math.pi / g["np"]
+    for _ in range(max(1, args.warmup)):
+        oracle.backproject_slab(P, q, g["nx"], g["ny"], k0, nks, scale)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.backproject_slab(P, q, g["nx"], g["ny"], k0, nks, scale)
+        times.append(time.perf_counter() - t0)
+    upd = float(g["nx"]) * g["ny"] * nks * g["np"]
+    t = statistics.mean(times)
+    val = upd / t / 1e9
+    sample = (f"each step: FP64 oracle back-projection of a {g['nx']}x{g['ny']}x{nks} slab "
+              f"({g['np']} views, {upd:.3g} updates) of the {args.workload} workload")
+    line = {"impl": "reference", "metric": "fdk_backprojection_gups", "value": val, "unit": "GUPS",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "sample": sample},
+            "cpu_baseline": {"value": val, "unit": "GUPS", "cores": oracle.num_threads(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": val, "unit": "GUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2104_13248_gb300 import api, inputs
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def max_over_ranks(x: float) -> float:
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    p = inputs.preset(args.workload)
+    g = p["geom"]
+    ctx = api.bp_create(g)
+    if args.tk:
+        api.bp_set_tile_depth(ctx, args.tk)
+    plan = api.bp_get_plan(ctx)
+    E = inputs.random_ellipsoids(p["seed"] + 7919 * rank, p["n_ell"], p["axes"], g)
+    raw = api.bp_phantom_project(ctx, E)
+    q32 = torch.empty_like(raw)
+    q16 = torch.empty(raw.shape, dtype=torch.float16, device=dev)
+    vol = torch.empty(ctx.vol_shape(), dtype=torch.float32, device=dev)
+    scale = math.pi / g["np"]
+    U = float(g["nx"]) * g["ny"] * g["nz"] * g["np"]
+    stream = torch.cuda.current_stream()
+
+    def time_steps(q, n_steps, bp_events):
+        for _ in range(args.warmup):
+            api.bp_filter(ctx, raw, out=q)
+            api.bp_backproject(ctx, q, vol=vol, scale=scale)
+        barrier()
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for i in range(n_steps):
+            api.bp_filter(ctx, raw, out=q)
+            bp_events[i][0].record(stream)
+            api.bp_backproject(ctx, q, vol=vol, scale=scale)
+            bp_events[i][1].record(stream)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        step_ms = ev0.elapsed_time(ev1) / n_steps
+        bp_ms = statistics.mean(a.elapsed_time(b) for a, b in bp_events[:n_steps])
+        return step_ms, bp_ms
+
+    K = args.steps
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        pass
+    with ClockSampler(uuid) as clk:
+        step_ms, bp_ms = time_steps(q32, K, evs)
+    clocks = clk.summary()
+    api.bp_device_status(ctx)
+    step_ms_max = max_over_ranks(step_ms)
+    bp_ms_max = max_over_ranks(bp_ms)
+    step16_ms, bp16_ms = time_steps(q16, K, evs)
+    api.bp_device_status(ctx)
+    step16_ms = max_over_ranks(step16_ms)
+    bp16_ms = max_over_ranks(bp16_ms)
+
+    peaks, peak_src = measured_peaks()
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    peak_gups = n_sm * UPD_PER_CLK_SM * sm_mhz * 1e6 / 1e9
+    achieved = U / (bp_ms_max * 1e-3) / 1e9
+    traffic = None
+    tp = os.path.join(ROOT, "profiles", "bp_zcol_tma_c3_traffic.json")
+    if os.path.exists(tp):
+        try:
+            traffic = json.load(open(tp)).get("dram_bytes_per_launch")
+        except Exception:
+            traffic = None
+
+    # end to end through the public API: pinned host projections in, volume out
+    e2e = None
+    if not args.no_e2e:
+        host_proj = torch.empty(raw.shape, dtype=torch.float32, pin_memory=True)
+        host_proj.copy_(raw)
+        host_vol = torch.empty(ctx.vol_shape(), dtype=torch.float32, pin_memory=True)
+        pipe = api.HostPipeline(ctx, chunks=8)
+        for _ in range(args.warmup):
+            pipe.run(host_proj, host_vol)
+        torch.cuda.synchronize()
+        barrier()
+        n_e2e = max(3, min(K, 10))
+        t0 = time.perf_counter()
+        for _ in range(n_e2e):
+            pipe.run(host_proj, host_vol)
+            torch.cuda.current_stream().synchronize()
+            float(host_vol[g["nz"] // 2, g["ny"] // 2, g["nx"] // 2])   # read the result
+        t_e2e = (time.perf_counter() - t0) / n_e2e
+        barrier()
+        t_e2e = max_over_ranks(t_e2e)
+        api.bp_device_status(ctx)
+        e2e = {"value": world * U / t_e2e / 1e9, "unit": "GUPS",
+               "h2d_bytes_per_step": host_proj.numel() * 4, "d2h_bytes_per_step": host_vol.numel() * 4,
+               "ms_per_step": t_e2e * 1e3}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(g)
+
+    # the launches inside the timed region: filter + back-projection per step
+    line = {
+        "metric": "fdk_backprojection_gups",
+        "value": world * U / (step_ms_max * 1e-3) / 1e9,
+        "unit": "GUPS",
+        "n_gpus": world, "steps": K, "warmup": args.warmup,
+        "ms_per_step": step_ms_max,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": f"{args.workload}: {g['nu']}x{g['nv']}x{g['np']} -> "
+                               f"{g['nx']}x{g['ny']}x{g['nz']}, FP32 projections, filter + back-projection",
+                   "l2": "inputs larger than L2 (projections %.2f GB), no flush" % (raw.numel() * 4 / 1e9),
+                   "parallelism": "replicas" if world > 1 else "single-gpu",
+                   "plan": plan},
+        "gpu_launches": 2 * K,
+        "roofline": {"bound": "alu", "resource": "shared-memory taps (4 x 4 B per update at 128 B/clk/SM)",
+                     "achieved": achieved, "peak": peak_gups, "unit": "GUPS",
+                     "frac": achieved / peak_gups, "traffic": traffic,
+                     "peak_basis": f"{n_sm} SMs x {UPD_PER_CLK_SM} updates/clk x {sm_mhz:.0f} MHz "
+                                   f"(sm_max_mhz, {peak_src})",
+                     "kernel_ms": bp_ms_max},
+        "clocks": clocks,
+        "variants": {"fp16_storage": {"value": world * U / (step16_ms * 1e-3) / 1e9, "unit": "GUPS",
+                                      "ms_per_step": step16_ms, "bp_kernel_ms": bp16_ms,
+                                      "bp_kernel_gups": U / (bp16_ms * 1e-3) / 1e9}},
+    }
+    if e2e:
+        line["e2e"] = e2e
+    if cpu:
+        line["cpu_baseline"] = cpu
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

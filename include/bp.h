@@ -104,6 +104,14 @@ bp_status bp_filter(bp_ctx *ctx, const float *proj, void *out, bp_dtype out_t,
                     int batch, void *stream);
 
 /*
+ * As bp_filter, for a block of n_views consecutive views of one scan
+ * ([batch][n_views][nv][nu], contiguous). The filter acts on each detector
+ * row on its own, so which views the block holds does not matter.
+ */
+bp_status bp_filter_views(bp_ctx *ctx, const float *proj, void *out, bp_dtype out_t,
+                          int n_views, int batch, void *stream);
+
+/*
  * Back-projection (Listing 1): for every voxel and view s,
  *   vol += scale * bilinear(proj_s, u, v) / w^2
  * with (u*w, v*w, w) = P_s (i, j, k, 1), floor-based bilinear sampling and

@@ -45,6 +45,7 @@ PROTOTYPES = {
     "bp_create": (_i, [ctypes.POINTER(bp_geometry), ctypes.POINTER(_vp)]),
     "bp_create_from_matrices": (_i, [_dptr, _i, _i, _i, _i, _i, _i, ctypes.POINTER(_vp)]),
     "bp_filter": (_i, [_vp, _vp, _vp, _i, _i, _vp]),
+    "bp_filter_views": (_i, [_vp, _vp, _vp, _i, _i, _i, _vp]),
     "bp_backproject": (_i, [_vp, _vp, _i, _vp, _i, _f, _i, _vp]),
     "bp_backproject_views": (_i, [_vp, _vp, _i, _i, _i, _ll, _vp, _i, _f, _i, _vp]),
     "fp_project": (_i, [_vp, _vp, _vp, _i, _f, _vp]),

@@ -176,6 +176,19 @@ def bp_filter(ctx: Context, proj: torch.Tensor, out: torch.Tensor | None = None,
     return out
 
 
+def bp_filter_views(ctx: Context, proj: torch.Tensor, out: torch.Tensor) -> torch.Tensor:
+    """Filter a contiguous ([B,]n,nv,nu) block of views into ``out`` (FP32 or FP16)."""
+    _need_cuda(proj, "proj")
+    _need_cuda(out, "out")
+    if proj.dtype != torch.float32 or tuple(proj.shape[-2:]) != (ctx.nv, ctx.nu) or out.shape != proj.shape:
+        raise ValueError("proj must be float32 (..., n, nv, nu) and out of the same shape")
+    n = proj.shape[-3]
+    batch = proj.numel() // (n * ctx.nv * ctx.nu)
+    check(_lib.load().bp_filter_views(ctx.handle, _ptr(proj), _ptr(out), _dtype_code(out), n, batch,
+                                      _stream(proj)), ctx.handle)
+    return out
+
+
 def bp_backproject(ctx: Context, proj: torch.Tensor, vol: torch.Tensor | None = None,
                    scale: float = 1.0, accumulate: bool = False) -> torch.Tensor:
     """Back-projection of ([B,]np,nv,nu) FP32/FP16 projections into FP32 volumes."""
@@ -242,6 +255,43 @@ def bp_phantom_project(ctx: Context, ellipsoids, out: torch.Tensor | None = None
     return out
 
 
+class HostPipeline:
+    """FDK from host memory with the host-to-device copy overlapped.
+
+    Views are split into ``chunks`` blocks: block c+1 is copied on a copy
+    stream while block c is filtered and back-projected (accumulating) on
+    the compute stream; the volume is copied back at the end. Device
+    buffers are allocated once, here, and reused by every call.
+    """
+
+    def __init__(self, ctx: Context, chunks: int = 8, dtype: torch.dtype = torch.float32):
+        self.ctx = ctx
+        self.chunks = max(1, min(int(chunks), ctx.n_views))
+        edges = np.linspace(0, ctx.n_views, self.chunks + 1).round().astype(int)
+        self.blocks = [(int(a), int(b)) for a, b in zip(edges[:-1], edges[1:]) if b > a]
+        self.raw = torch.empty(ctx.proj_shape(), dtype=torch.float32, device="cuda")
+        self.filt = torch.empty(ctx.proj_shape(), dtype=dtype, device="cuda")
+        self.vol = torch.empty(ctx.vol_shape(), dtype=torch.float32, device="cuda")
+        self.copy_stream = torch.cuda.Stream()
+        self.events = [torch.cuda.Event() for _ in self.blocks]
+
+    def run(self, proj_host: torch.Tensor, vol_host: torch.Tensor) -> torch.Tensor:
+        """proj_host: pinned FP32 (np,nv,nu); vol_host: pinned FP32 (nz,ny,nx)."""
+        comp = torch.cuda.current_stream()
+        self.copy_stream.wait_stream(comp)
+        with torch.cuda.stream(self.copy_stream):
+            for (a, b), ev in zip(self.blocks, self.events):
+                self.raw[a:b].copy_(proj_host[a:b], non_blocking=True)
+                ev.record(self.copy_stream)
+        scale = math.pi / self.ctx.n_views
+        for i, ((a, b), ev) in enumerate(zip(self.blocks, self.events)):
+            comp.wait_event(ev)
+            bp_filter_views(self.ctx, self.raw[a:b], self.filt[a:b])
+            bp_backproject_views(self.ctx, self.filt[a:b], a, self.vol, scale=scale, accumulate=i > 0)
+        vol_host.copy_(self.vol, non_blocking=True)
+        return vol_host
+
+
 def fdk(ctx: Context, proj: torch.Tensor, out_dtype: torch.dtype = torch.float32,
         filtered: torch.Tensor | None = None, vol: torch.Tensor | None = None) -> torch.Tensor:
     """Feldkamp reconstruction: bp_filter then bp_backproject with scale pi/np."""
@@ -249,7 +299,7 @@ def fdk(ctx: Context, proj: torch.Tensor, out_dtype: torch.dtype = torch.float32
     return bp_backproject(ctx, q, vol=vol, scale=math.pi / ctx.n_views)
 
 
-__all__ = ["Context", "BPError", "bp_create", "bp_create_from_matrices", "bp_destroy", "bp_filter",
+__all__ = ["Context", "BPError", "HostPipeline", "bp_filter_views", "bp_create", "bp_create_from_matrices", "bp_destroy", "bp_filter",
            "bp_backproject", "bp_backproject_views", "fp_project", "bp_phantom_project",
            "bp_get_matrices", "bp_get_plan", "bp_set_tile_depth", "bp_set_timeout",
            "bp_test_drop_view", "bp_device_status", "fdk"]

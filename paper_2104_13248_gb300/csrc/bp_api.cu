@@ -310,13 +310,20 @@ static bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
 bp_status bp_filter(bp_ctx *ctx, const float *proj, void *out, bp_dtype out_t, int batch,
                     void *stream) {
     if (!ctx) return fail(nullptr, BP_ERR_INVALID_ARG, "bp_filter: NULL context");
+    return bp_filter_views(ctx, proj, out, out_t, ctx->n_views, batch, stream);
+}
+
+bp_status bp_filter_views(bp_ctx *ctx, const float *proj, void *out, bp_dtype out_t, int n_views,
+                          int batch, void *stream) {
+    if (!ctx) return fail(nullptr, BP_ERR_INVALID_ARG, "bp_filter: NULL context");
+    if (n_views < 1) return fail(ctx, BP_ERR_INVALID_ARG, "bp_filter: n_views < 1");
     ctx->err.clear();
     if (!ctx->has_geometry) return fail(ctx, BP_ERR_UNSUPPORTED, "bp_filter: context has no physical geometry");
     if (!proj || !out || batch < 1) return fail(ctx, BP_ERR_INVALID_ARG, "bp_filter: NULL pointer or batch < 1");
     if (out_t != BP_F32 && out_t != BP_F16) return fail(ctx, BP_ERR_INVALID_ARG, "bp_filter: bad dtype");
     if (!aligned16(proj) || !aligned16(out)) return fail(ctx, BP_ERR_INVALID_ARG, "bp_filter: pointers must be 16-byte aligned");
     if (out_t == BP_F16 && (const void *)proj == out) return fail(ctx, BP_ERR_INVALID_ARG, "bp_filter: FP16 output may not alias the input");
-    return launch_filter(ctx, proj, out, out_t, batch, (cudaStream_t)stream);
+    return launch_filter(ctx, proj, out, out_t, (long long)batch * n_views, (cudaStream_t)stream);
 }
 
 bp_status bp_backproject_views(bp_ctx *ctx, const void *proj, bp_dtype t, int view0, int n_views,

@@ -91,8 +91,8 @@ bp_status launch_backproject(bp_ctx *ctx, const void *proj, bp_dtype t, int view
                              int accumulate, cudaStream_t st);
 bp_status launch_forward(bp_ctx *ctx, const float *vol, float *proj, int batch, float scale,
                          cudaStream_t st);
-bp_status launch_filter(bp_ctx *ctx, const float *proj, void *out, bp_dtype out_t, int batch,
-                        cudaStream_t st);
+bp_status launch_filter(bp_ctx *ctx, const float *proj, void *out, bp_dtype out_t,
+                        long long n_views_total, cudaStream_t st);
 bp_status launch_phantom(bp_ctx *ctx, const double *d_ell, int n_ell, float *proj,
                          cudaStream_t st);
 

@@ -94,11 +94,11 @@ ramp_filter_fft(const float *__restrict__ in, TO *__restrict__ out, long long nr
     }
 }
 
-bp_status launch_filter(bp_ctx *ctx, const float *proj, void *out, bp_dtype out_t, int batch,
-                        cudaStream_t st) {
+bp_status launch_filter(bp_ctx *ctx, const float *proj, void *out, bp_dtype out_t,
+                        long long n_views_total, cudaStream_t st) {
     const bp_geometry &g = ctx->g;
     const int N = ctx->fft_n;
-    const long long nrows = (long long)batch * ctx->n_views * ctx->nv;
+    const long long nrows = n_views_total * ctx->nv;
     const int pairs = N >= 4096 ? 1 : 4096 / N;
     const long long nblk = (nrows + 2LL * pairs - 1) / (2LL * pairs);
     const int smem = pairs * N * (int)sizeof(float2);
