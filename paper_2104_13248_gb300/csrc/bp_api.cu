@@ -17,7 +17,7 @@
 
 namespace bp {
 
-int plan_box_width(int need);   // k_backproject.cu
+int plan_box_width(int need, int elem_bytes);   // k_backproject.cu
 
 static thread_local std::string g_create_err;
 
@@ -147,8 +147,8 @@ static void make_plan(bp_ctx *ctx) {
     int bu32, bv32, bu16, bv16;
     max_footprint(ctx, pl.tx, pl.ty, pl.tk, 4, &bu32, &bv32);
     max_footprint(ctx, pl.tx, pl.ty, pl.tk, 8, &bu16, &bv16);
-    pl.bu = plan_box_width(bu32);
-    pl.bu16 = plan_box_width(bu16);
+    pl.bu = plan_box_width(bu32, 4);
+    pl.bu16 = plan_box_width(bu16, 2);
     pl.bv = std::max(bv32, bv16);
     // shared memory budget of the TMA kernel (records + barriers + 4 stages)
     const int rec = 256 * 48 + 2 * 4 * 8;
@@ -159,7 +159,7 @@ static void make_plan(bp_ctx *ctx) {
 }
 
 // Ramp filter tables: real spectrum of the circularly embedded Ram-Lak
-// kernel (times dp and 1/N, in bit-reversed order) and FFT twiddles.
+// kernel (times dp and 1/N, natural order) and the N FFT twiddles.
 static bp_status make_filter_tables(bp_ctx *ctx) {
     const bp_geometry &g = ctx->g;
     int n = 1, lg = 0;
@@ -172,30 +172,25 @@ static bp_status make_filter_tables(bp_ctx *ctx) {
         h[m] = (m == 0) ? 1.0 / (4.0 * dp * dp)
                : (m % 2 == 0) ? 0.0
                : -1.0 / (M_PI * M_PI * (double)m * (double)m * dp * dp);
-    // H[k] = h[0] + 2 sum_m h[m] cos(2 pi k m / N) (even kernel -> real spectrum)
-    std::vector<float> Hbr(n), tw(n);
-    std::vector<double> H(n);
+    // H[k] = h[0] + 2 sum_m h[m] cos(2 pi k m / N) (even kernel -> real spectrum),
+    // times dp (the convolution's quadrature weight) and 1/N (inverse FFT)
+    std::vector<float> Hf(n), tw(2 * (size_t)n);
     for (int k = 0; k < n; ++k) {
         double acc = h[0];
         for (int m = 1; m < g.nu; m += 2) acc += 2.0 * h[m] * std::cos(2.0 * M_PI * (double)((long long)k * m % n) / n);
-        H[k] = acc * dp / n;
+        Hf[k] = (float)(acc * dp / n);
     }
     for (int k = 0; k < n; ++k) {
-        int r = 0;
-        for (int b = 0; b < lg; ++b) r |= ((k >> b) & 1) << (lg - 1 - b);
-        Hbr[k] = (float)H[r];
-    }
-    for (int k = 0; k < n / 2; ++k) {
         tw[2 * k] = (float)std::cos(2.0 * M_PI * k / n);
         tw[2 * k + 1] = (float)-std::sin(2.0 * M_PI * k / n);
     }
     cudaError_t e = dev_alloc((void **)&ctx->d_H, sizeof(float) * n);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "filter spectrum");
-    e = dev_alloc((void **)&ctx->d_tw, sizeof(float2) * (n / 2));
+    e = dev_alloc((void **)&ctx->d_tw, sizeof(float2) * n);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "filter twiddles");
-    e = cudaMemcpy(ctx->d_H, Hbr.data(), sizeof(float) * n, cudaMemcpyHostToDevice);
+    e = cudaMemcpy(ctx->d_H, Hf.data(), sizeof(float) * n, cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
-        e = cudaMemcpy(ctx->d_tw, tw.data(), sizeof(float2) * (n / 2), cudaMemcpyHostToDevice);
+        e = cudaMemcpy(ctx->d_tw, tw.data(), sizeof(float2) * n, cudaMemcpyHostToDevice);
     return e == cudaSuccess ? BP_OK : cuda_fail(ctx, e, "filter tables upload");
 }
 

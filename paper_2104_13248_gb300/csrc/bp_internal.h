@@ -67,8 +67,8 @@ struct bp_ctx {
     unsigned *d_err = nullptr;  // device error word
     // ramp filter
     int fft_n = 0, fft_log2 = 0;
-    float *d_H = nullptr;       // [fft_n] real spectrum (times dp, times 1/N), bit-reversed order
-    float2 *d_tw = nullptr;     // [fft_n/2] twiddles exp(-2 pi i k / N)
+    float *d_H = nullptr;       // [fft_n] real spectrum (times dp, times 1/N), natural order
+    float2 *d_tw = nullptr;     // [fft_n] twiddles exp(-2 pi i k / N)
     float *d_phcoef = nullptr;  // [np][256][20] phantom coefficients (input generation)
     // launch plan
     bp::Plan plan{};

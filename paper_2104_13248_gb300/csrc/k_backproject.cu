@@ -47,11 +47,32 @@ __device__ __forceinline__ void consumer_column(int warp, int lane, int *di, int
     *dj = wy * 4 + (lane >> 3);
 }
 
+// Shared-memory tap loads at a 32-bit shared address plus a constant offset.
+template <int OFF>
+__device__ __forceinline__ float lds_tap(unsigned addr, float) {
+    float x;
+    asm volatile("ld.shared.f32 %0, [%1+%2];" : "=f"(x) : "r"(addr), "n"(OFF));
+    return x;
+}
+template <int OFF>
+__device__ __forceinline__ float lds_tap(unsigned addr, __half) {
+    unsigned short h;
+    asm volatile("ld.shared.b16 %0, [%1+%2];" : "=h"(h) : "r"(addr), "n"(OFF));
+    return __half2float(__ushort_as_half(h));
+}
+
 // Accumulate one view into acc[0..TK-1] from a staged box with row pitch BU.
+// Per (column, view): depth W, 1/W^2 weight, the u column and fraction, and
+// v at the tile's first slice plus its step per slice. Per voxel: v, its
+// floor (magic-number add with round-down), the fraction, one IMAD for the
+// tap address (the magic bias is folded into the column base), four taps,
+// two u-lerps, one v-lerp and the weighted accumulate.
 template <typename T, int TK, int BU, bool FULL>
-__device__ __forceinline__ void accumulate_view(const T *__restrict__ tile, const ViewRec &r,
-                                                float fdi, float fdj, int ez, int bv,
-                                                float *acc, unsigned *err) {
+__device__ __forceinline__ void accumulate_view(unsigned tile_s, const ViewRec &r, float fdi,
+                                                float fdj, int ez, int bv, float *acc,
+                                                unsigned *err) {
+    constexpr int ES = (int)sizeof(T);
+    constexpr unsigned ROW = (unsigned)(BU * ES);
     float W = fmaf(r.Wj, fdj, fmaf(r.Wi, fdi, r.W0));
     float inv = __frcp_rn(W);
     float uL = fmaf(r.Nuj, fdj, fmaf(r.Nui, fdi, r.Nu0)) * inv;
@@ -64,21 +85,22 @@ __device__ __forceinline__ void accumulate_view(const T *__restrict__ tile, cons
     float vlast = fmaf((float)(ez - 1), dv, v0);
     int rfirst = __float_as_int(__fadd_rd(v0, kMagic)) - kMagicBits;
     int rlast = __float_as_int(__fadd_rd(vlast, kMagic)) - kMagicBits;
-    if (cu < 0 || cu > BU - 2 || min(rfirst, rlast) < 0 || max(rfirst, rlast) > bv - 2 || !(uL == uL) || !(v0 == v0)) {
+    if (cu < 0 || cu > BU - 2 || min(rfirst, rlast) < 0 || max(rfirst, rlast) > bv - 2 ||
+        !(uL == uL) || !(v0 == v0)) {
         atomicOr(err, DEV_ERR_FOOTPRINT);
         return;
     }
-    const T *base = tile + cu;
+    // address of tap (row, cu) = bits(magic + row) * ROW + colbase  (mod 2^32)
+    const unsigned colbase = tile_s + (unsigned)cu * ES - (unsigned)kMagicBits * ROW;
 #pragma unroll
     for (int kk = 0; kk < TK; ++kk) {
         if (!FULL && kk >= ez) continue;
         float v = fmaf((float)kk, dv, v0);
         float tv = __fadd_rd(v, kMagic);
         float fv = v - (tv - kMagic);
-        int row = __float_as_int(tv) - kMagicBits;
-        const T *p = base + row * BU;
-        float q00 = to_f32(p[0]), q01 = to_f32(p[1]);
-        float q10 = to_f32(p[BU]), q11 = to_f32(p[BU + 1]);
+        unsigned addr = (unsigned)__float_as_int(tv) * ROW + colbase;
+        float q00 = lds_tap<0>(addr, T()), q01 = lds_tap<ES>(addr, T());
+        float q10 = lds_tap<(int)ROW>(addr, T()), q11 = lds_tap<(int)ROW + ES>(addr, T());
         float s0 = fmaf(fu, q01 - q00, q00);
         float s1 = fmaf(fu, q11 - q10, q10);
         float val = fmaf(fv, s1 - s0, s0);
@@ -184,11 +206,11 @@ bp_zcol_tma(const __grid_constant__ CUtensorMap tmap, const double *__restrict__
                     break;
                 }
                 if (col_ok) {
-                    const T *tile = reinterpret_cast<const T *>(stages + slot * sbytes);
+                    const unsigned tile_s = smem_addr(stages + slot * sbytes);
                     if (ez == TK)
-                        accumulate_view<T, TK, BU, true>(tile, recs[n], fdi, fdj, ez, bv, acc, err);
+                        accumulate_view<T, TK, BU, true>(tile_s, recs[n], fdi, fdj, ez, bv, acc, err);
                     else
-                        accumulate_view<T, TK, BU, false>(tile, recs[n], fdi, fdj, ez, bv, acc, err);
+                        accumulate_view<T, TK, BU, false>(tile_s, recs[n], fdi, fdj, ez, bv, acc, err);
                 }
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&empty[slot]);
@@ -356,13 +378,22 @@ static PFN_encodeTiled get_encode() {
     return fn;
 }
 
-// Box widths the TMA kernel is instantiated for (multiples of 8 that are
-// 8 mod 16, so consecutive staged rows start 8 or 24 banks apart).
-static const int kBoxWidths[] = {40, 56, 88, 136, 232};
+// Box widths (elements) the TMA kernel is instantiated for. A row pitch of
+// 16 mod 32 banks puts vertically adjacent taps half a bank cycle apart, so
+// the 8 x 4 columns of a warp (whose taps span ~2 rows and < 16 columns)
+// read without bank conflicts: FP32 widths are 16 mod 32 floats, FP16
+// widths 32 mod 64 halves.
+static const int kBoxWidths32[] = {48, 80, 112, 144, 176, 208, 240};
+static const int kBoxWidths16[] = {32, 96, 160, 224};
 
-int plan_box_width(int need) {
-    for (int w : kBoxWidths)
-        if (w >= need) return w;
+int plan_box_width(int need, int elem_bytes) {
+    if (elem_bytes == 2) {
+        for (int w : kBoxWidths16)
+            if (w >= need) return w;
+    } else {
+        for (int w : kBoxWidths32)
+            if (w >= need) return w;
+    }
     return -1;
 }
 
@@ -386,14 +417,21 @@ template <typename T, int TK>
 static cudaError_t launch_tma_bu(const CUtensorMap &map, bp_ctx *ctx, int bu, int view0,
                                  int nviews, int bv, int align, float *vol, int batch, float scale,
                                  int accumulate, cudaStream_t st) {
-    switch (bu) {
-        case 40: return launch_tma_t<T, TK, 40>(map, ctx, view0, nviews, bv, align, vol, batch, scale, accumulate, st);
-        case 56: return launch_tma_t<T, TK, 56>(map, ctx, view0, nviews, bv, align, vol, batch, scale, accumulate, st);
-        case 88: return launch_tma_t<T, TK, 88>(map, ctx, view0, nviews, bv, align, vol, batch, scale, accumulate, st);
-        case 136: return launch_tma_t<T, TK, 136>(map, ctx, view0, nviews, bv, align, vol, batch, scale, accumulate, st);
-        case 232: return launch_tma_t<T, TK, 232>(map, ctx, view0, nviews, bv, align, vol, batch, scale, accumulate, st);
-        default: return cudaErrorInvalidValue;
+#define BP_TMA_CASE(W) \
+    case W: return launch_tma_t<T, TK, W>(map, ctx, view0, nviews, bv, align, vol, batch, scale, accumulate, st);
+    if constexpr (sizeof(T) == 2) {
+        switch (bu) {
+            BP_TMA_CASE(32) BP_TMA_CASE(96) BP_TMA_CASE(160) BP_TMA_CASE(224)
+            default: return cudaErrorInvalidValue;
+        }
+    } else {
+        switch (bu) {
+            BP_TMA_CASE(48) BP_TMA_CASE(80) BP_TMA_CASE(112) BP_TMA_CASE(144) BP_TMA_CASE(176)
+            BP_TMA_CASE(208) BP_TMA_CASE(240)
+            default: return cudaErrorInvalidValue;
+        }
     }
+#undef BP_TMA_CASE
 }
 
 bp_status launch_backproject(bp_ctx *ctx, const void *proj, bp_dtype t, int view0, int nviews,

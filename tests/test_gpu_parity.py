@@ -62,6 +62,32 @@ def test_filter_c1(c1):
     assert rel(out16.astype(np.float64), ref) <= 1e-3
 
 
+@pytest.mark.parametrize("nu", [20, 33, 100, 300, 512, 1248, 2100])
+def test_filter_sizes(nu):
+    """Every FFT size class: N = 64 .. 8192 (radix-16 passes plus 2/4/8)."""
+    g = dict(sid=800.0, sdd=1300.0, np=3, angles=None, nu=nu, nv=7, du=0.45, dv=0.5, u_off=1.2,
+             v_off=-0.8, nx=8, ny=8, nz=8, sx=1.0, sy=1.0, sz=1.0, ox=0, oy=0, oz=0)
+    raw = inputs.uniform_array(40 + nu, (g["np"], g["nv"], g["nu"]), 0.0, 2.0).astype(np.float32)
+    ref = oracle.ramp_filter(g, raw)
+    with api.bp_create(g) as ctx:
+        out = api.bp_filter(ctx, torch.from_numpy(raw).cuda()).cpu().numpy()
+    assert rel(out, ref) <= 2e-5
+
+
+def test_host_pipeline_matches_device_fdk(c1):
+    g = c1["g"]
+    with api.bp_create(g) as ctx:
+        dev = torch.from_numpy(c1["raw"]).cuda()
+        ref = api.fdk(ctx, dev).cpu().numpy()
+        host = torch.from_numpy(c1["raw"]).pin_memory()
+        vol_host = torch.empty(ctx.vol_shape(), dtype=torch.float32).pin_memory()
+        pipe = api.HostPipeline(ctx, chunks=7)
+        for _ in range(2):
+            pipe.run(host, vol_host)
+            torch.cuda.synchronize()
+            assert rel(vol_host.numpy(), ref) <= 1e-6
+
+
 def test_fdk_end_to_end_c1(c1):
     g = c1["g"]
     ref = oracle.fdk(g, c1["raw"])
