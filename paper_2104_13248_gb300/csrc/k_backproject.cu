@@ -47,64 +47,114 @@ __device__ __forceinline__ void consumer_column(int warp, int lane, int *di, int
     *dj = wy * 4 + (lane >> 3);
 }
 
-// Shared-memory tap loads at a 32-bit shared address plus a constant offset.
-template <int OFF>
-__device__ __forceinline__ float lds_tap(unsigned addr, float) {
-    float x;
-    asm volatile("ld.shared.f32 %0, [%1+%2];" : "=f"(x) : "r"(addr), "n"(OFF));
-    return x;
+// Packed FP32 pair arithmetic (sm_100-family f32x2 instructions): each
+// operates on two independent FP32 lanes with IEEE rounding per lane, so a
+// pair of voxels costs one instruction where two scalar ones were needed.
+typedef unsigned long long f2;
+__device__ __forceinline__ f2 pk(float a, float b) {
+    f2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
 }
-template <int OFF>
-__device__ __forceinline__ float lds_tap(unsigned addr, __half) {
-    unsigned short h;
-    asm volatile("ld.shared.b16 %0, [%1+%2];" : "=h"(h) : "r"(addr), "n"(OFF));
-    return __half2float(__ushort_as_half(h));
+__device__ __forceinline__ void upk(f2 r, float &a, float &b) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r));
+}
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) {
+    f2 r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+__device__ __forceinline__ f2 sub2(f2 a, f2 b) {
+    f2 r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f2 add2_rd(f2 a, f2 b) {
+    f2 r;
+    asm("add.rm.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
 }
 
-// Accumulate one view into acc[0..TK-1] from a staged box with row pitch BU.
-// Per (column, view): depth W, 1/W^2 weight, the u column and fraction, and
-// v at the tile's first slice plus its step per slice. Per voxel: v, its
-// floor (magic-number add with round-down), the fraction, one IMAD for the
-// tap address (the magic bias is folded into the column base), four taps,
-// two u-lerps, one v-lerp and the weighted accumulate.
-template <typename T, int TK, int BU, bool FULL>
-__device__ __forceinline__ void accumulate_view(unsigned tile_s, const ViewRec &r, float fdi,
-                                                float fdj, int ez, int bv, float *acc,
-                                                unsigned *err) {
-    constexpr int ES = (int)sizeof(T);
-    constexpr unsigned ROW = (unsigned)(BU * ES);
+// Per (column, view) quantities of the z-column update: the 1/W^2 weight,
+// the staged-box column cu and u fraction fu, v at the tile's first slice
+// and its step per slice. Returns false (and flags the device error word)
+// if the taps would leave the staged box.
+struct ColView {
+    float wt, fu, v0, dv;
+    int cu;
+};
+
+template <int BU>
+__device__ __forceinline__ bool column_view(const ViewRec &r, float fdi, float fdj, int ez, int bv,
+                                            unsigned *err, ColView &c) {
     float W = fmaf(r.Wj, fdj, fmaf(r.Wi, fdi, r.W0));
     float inv = __frcp_rn(W);
     float uL = fmaf(r.Nuj, fdj, fmaf(r.Nui, fdi, r.Nu0)) * inv;
-    float v0 = fmaf(r.Nvj, fdj, fmaf(r.Nvi, fdi, r.Nv0)) * inv;
-    float dv = r.Nvk * inv;
-    float wt = inv * inv;
+    c.v0 = fmaf(r.Nvj, fdj, fmaf(r.Nvi, fdi, r.Nv0)) * inv;
+    c.dv = r.Nvk * inv;
+    c.wt = inv * inv;
     float tu = __fadd_rd(uL, kMagic);
-    int cu = __float_as_int(tu) - kMagicBits;
-    float fu = uL - (tu - kMagic);
-    float vlast = fmaf((float)(ez - 1), dv, v0);
-    int rfirst = __float_as_int(__fadd_rd(v0, kMagic)) - kMagicBits;
+    c.cu = __float_as_int(tu) - kMagicBits;
+    c.fu = uL - (tu - kMagic);
+    float vlast = fmaf((float)(ez - 1), c.dv, c.v0);
+    int rfirst = __float_as_int(__fadd_rd(c.v0, kMagic)) - kMagicBits;
     int rlast = __float_as_int(__fadd_rd(vlast, kMagic)) - kMagicBits;
-    if (cu < 0 || cu > BU - 2 || min(rfirst, rlast) < 0 || max(rfirst, rlast) > bv - 2 ||
-        !(uL == uL) || !(v0 == v0)) {
+    if (c.cu < 0 || c.cu > BU - 2 || min(rfirst, rlast) < 0 || max(rfirst, rlast) > bv - 2 ||
+        !(uL == uL) || !(c.v0 == c.v0)) {
         atomicOr(err, DEV_ERR_FOOTPRINT);
-        return;
+        return false;
     }
-    // address of tap (row, cu) = bits(magic + row) * ROW + colbase  (mod 2^32)
-    const unsigned colbase = tile_s + (unsigned)cu * ES - (unsigned)kMagicBits * ROW;
+    return true;
+}
+
+// Scalar update of acc[0..TK-1] (any element type; ragged tiles): per voxel
+// v, its floor (magic-number add rounding down), the fraction, four taps,
+// two u-lerps, one v-lerp and the weighted accumulate.
+template <typename T, int TK, int BU, bool FULL>
+__device__ __forceinline__ void accumulate_scalar(const T *__restrict__ tile, const ColView &c,
+                                                  int ez, float *acc) {
+    const T *base = tile + c.cu;
 #pragma unroll
     for (int kk = 0; kk < TK; ++kk) {
         if (!FULL && kk >= ez) continue;
-        float v = fmaf((float)kk, dv, v0);
+        float v = fmaf((float)kk, c.dv, c.v0);
         float tv = __fadd_rd(v, kMagic);
         float fv = v - (tv - kMagic);
-        unsigned addr = (unsigned)__float_as_int(tv) * ROW + colbase;
-        float q00 = lds_tap<0>(addr, T()), q01 = lds_tap<ES>(addr, T());
-        float q10 = lds_tap<(int)ROW>(addr, T()), q11 = lds_tap<(int)ROW + ES>(addr, T());
-        float s0 = fmaf(fu, q01 - q00, q00);
-        float s1 = fmaf(fu, q11 - q10, q10);
+        int row = __float_as_int(tv) - kMagicBits;
+        const T *p = base + row * BU;
+        float q00 = to_f32(p[0]), q01 = to_f32(p[1]);
+        float q10 = to_f32(p[BU]), q11 = to_f32(p[BU + 1]);
+        float s0 = fmaf(c.fu, q01 - q00, q00);
+        float s1 = fmaf(c.fu, q11 - q10, q10);
         float val = fmaf(fv, s1 - s0, s0);
-        acc[kk] = fmaf(wt, val, acc[kk]);
+        acc[kk] = fmaf(c.wt, val, acc[kk]);
+    }
+}
+
+// The same arithmetic on voxel pairs (kk, kk+1) with f32x2 instructions:
+// identical per-lane results, about 11 instructions per voxel instead of 17.
+template <int TK, int BU>
+__device__ __forceinline__ void accumulate_pairs(const float *__restrict__ tile, const ColView &c,
+                                                 f2 *acc2) {
+    const float *base = tile + c.cu;
+    const f2 M2 = pk(kMagic, kMagic), FU = pk(c.fu, c.fu), WT = pk(c.wt, c.wt);
+#pragma unroll
+    for (int m = 0; m < TK / 2; ++m) {
+        const float va = fmaf((float)(2 * m), c.dv, c.v0);
+        const float vb = fmaf((float)(2 * m + 1), c.dv, c.v0);
+        const f2 V = pk(va, vb);
+        const f2 TV = add2_rd(V, M2);
+        const f2 FV = sub2(V, sub2(TV, M2));
+        float ta, tb;
+        upk(TV, ta, tb);
+        const float *pa = base + (__float_as_int(ta) - kMagicBits) * BU;
+        const float *pb = base + (__float_as_int(tb) - kMagicBits) * BU;
+        const f2 Q00 = pk(pa[0], pb[0]), Q01 = pk(pa[1], pb[1]);
+        const f2 Q10 = pk(pa[BU], pb[BU]), Q11 = pk(pa[BU + 1], pb[BU + 1]);
+        const f2 S0 = fma2(FU, sub2(Q01, Q00), Q00);
+        const f2 S1 = fma2(FU, sub2(Q11, Q10), Q10);
+        const f2 VAL = fma2(FV, sub2(S1, S0), S0);
+        acc2[m] = fma2(WT, VAL, acc2[m]);
     }
 }
 
@@ -160,9 +210,14 @@ bp_zcol_tma(const __grid_constant__ CUtensorMap tmap, const double *__restrict__
     }
     __syncthreads();
 
-    float acc[TK];
+    // accumulators: FP32 pairs (kk, kk+1) for FP32 taps, scalars otherwise
+    constexpr bool kPairs = sizeof(T) == 4;
+    f2 acc2[TK / 2];
+    float acc[kPairs ? 1 : TK];
 #pragma unroll
-    for (int kk = 0; kk < TK; ++kk) acc[kk] = 0.0f;
+    for (int m = 0; m < TK / 2; ++m) acc2[m] = 0ull;
+#pragma unroll
+    for (int kk = 0; kk < (kPairs ? 1 : TK); ++kk) acc[kk] = 0.0f;
 
     __shared__ unsigned arms[kStages];   // producer: armings of each full barrier
     if (tid < kStages) arms[tid] = 0;
@@ -205,12 +260,26 @@ bp_zcol_tma(const __grid_constant__ CUtensorMap tmap, const double *__restrict__
                     alive = false;
                     break;
                 }
-                if (col_ok) {
-                    const unsigned tile_s = smem_addr(stages + slot * sbytes);
-                    if (ez == TK)
-                        accumulate_view<T, TK, BU, true>(tile_s, recs[n], fdi, fdj, ez, bv, acc, err);
-                    else
-                        accumulate_view<T, TK, BU, false>(tile_s, recs[n], fdi, fdj, ez, bv, acc, err);
+                ColView cv;
+                if (col_ok && column_view<BU>(recs[n], fdi, fdj, ez, bv, err, cv)) {
+                    const T *tile = reinterpret_cast<const T *>(stages + slot * sbytes);
+                    if constexpr (kPairs) {
+                        if (ez == TK) {
+                            accumulate_pairs<TK, BU>(tile, cv, acc2);
+                        } else {
+                            float tmp[TK];
+#pragma unroll
+                            for (int m = 0; m < TK / 2; ++m) upk(acc2[m], tmp[2 * m], tmp[2 * m + 1]);
+                            accumulate_scalar<T, TK, BU, false>(tile, cv, ez, tmp);
+#pragma unroll
+                            for (int m = 0; m < TK / 2; ++m) acc2[m] = pk(tmp[2 * m], tmp[2 * m + 1]);
+                        }
+                    } else {
+                        if (ez == TK)
+                            accumulate_scalar<T, TK, BU, true>(tile, cv, ez, acc);
+                        else
+                            accumulate_scalar<T, TK, BU, false>(tile, cv, ez, acc);
+                    }
                 }
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&empty[slot]);
@@ -224,8 +293,16 @@ bp_zcol_tma(const __grid_constant__ CUtensorMap tmap, const double *__restrict__
             if (arms[s] > 0 && !mbar_wait_bounded(&full[s], (arms[s] - 1) & 1, timeout_ns))
                 atomicOr(err, DEV_ERR_TIMEOUT);
     }
-    if (col_ok && alive)
-        store_column<TK>(vol, acc, b, i0 + di, j0 + dj, k0, ez, nx, ny, nz, scale, accumulate);
+    if (col_ok && alive) {
+        if constexpr (kPairs) {
+            float out[TK];
+#pragma unroll
+            for (int m = 0; m < TK / 2; ++m) upk(acc2[m], out[2 * m], out[2 * m + 1]);
+            store_column<TK>(vol, out, b, i0 + di, j0 + dj, k0, ez, nx, ny, nz, scale, accumulate);
+        } else {
+            store_column<TK>(vol, acc, b, i0 + di, j0 + dj, k0, ez, nx, ny, nz, scale, accumulate);
+        }
+    }
 }
 
 // Same arithmetic without TMA: taps are gathered from global memory with

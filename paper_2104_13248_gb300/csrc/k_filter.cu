@@ -135,6 +135,10 @@ struct FilterArgs {
     float sdd, du, dv, cu, cv;
 };
 
+// Shared-memory position of complex sample m: one pad slot every 16 samples,
+// so the stride-16 writes of the first Stockham pass hit distinct banks.
+__device__ __forceinline__ int pad16(int m) { return m + (m >> 4); }
+
 // Row pairs per CTA for transform size N: 4096 complex points per CTA.
 template <int N>
 struct PairsPerCta {
@@ -169,7 +173,8 @@ __device__ __forceinline__ void stockham_pass(float2 *buf, const FilterArgs &a, 
             for (int r = 0; r < R; ++r) {
                 const int m = j + r * G;
                 float xa = 0.0f, xb = 0.0f;
-                if (m < a.nu) {
+                // N >= 2 nu - 1 gives nu <= N/2 = (R/2) G, so r >= R/2 reads only padding
+                if (r < R / 2 && m < a.nu) {
                     float um = ((float)m - a.cu) * a.du;
                     um *= um;
                     if (ra < a.nrows) xa = a.in[ra * a.nu + m] * (a.sdd * rsqrtf(sdd2 + um + vma));
@@ -179,15 +184,25 @@ __device__ __forceinline__ void stockham_pass(float2 *buf, const FilterArgs &a, 
             }
         } else {
 #pragma unroll
-            for (int r = 0; r < R; ++r) v[q][r] = buf[p * N + j + r * G];
+            for (int r = 0; r < R; ++r) v[q][r] = buf[pad16(p * N + j + r * G)];
         }
         if (NS > 1) {
+            // twiddles w^r: powers of two from the table, the others as one
+            // product of two table entries (error of a few ulp at most)
+            float2 w[R];
+            w[0] = make_float2(1.0f, 0.0f);
 #pragma unroll
             for (int r = 1; r < R; ++r) {
-                float2 w = __ldg(&a.tw[(k * r) * (N / (NS * R))]);
-                if (DIR > 0) w.y = -w.y;
-                v[q][r] = cmul(v[q][r], w);
+                if ((r & (r - 1)) == 0) {
+                    w[r] = __ldg(&a.tw[(k * r) * (N / (NS * R))]);
+                    if (DIR > 0) w[r].y = -w[r].y;
+                } else {
+                    const int hb = 1 << (31 - __clz(r));
+                    w[r] = cmul(w[hb], w[r - hb]);
+                }
             }
+#pragma unroll
+            for (int r = 1; r < R; ++r) v[q][r] = cmul(v[q][r], w[r]);
         }
         Dft<R, DIR>::run(v[q]);
     }
@@ -202,8 +217,9 @@ __device__ __forceinline__ void stockham_pass(float2 *buf, const FilterArgs &a, 
         if (MODE == 3) {
             const long long ra = row0 + 2 * p, rb = ra + 1;
             TO *out = reinterpret_cast<TO *>(a.out);
+            // last pass: m = j + r G and only m < nu <= N/2 is kept, so r < R/2
 #pragma unroll
-            for (int r = 0; r < R; ++r) {
+            for (int r = 0; r < R / 2; ++r) {
                 const int m = dst + r * NS;
                 if (m < a.nu) {
                     if (ra < a.nrows) store_out<TO>(out + ra * a.nu + m, v[q][r].x);
@@ -265,7 +281,8 @@ __device__ __forceinline__ void run_passes(float2 *buf, const FilterArgs &a, lon
             __syncthreads();
             for (int t = threadIdx.x; t < PairsPerCta<N>::value * N; t += kFilterThreads) {
                 float h = __ldg(&a.H[t & (N - 1)]);
-                buf[t] = make_float2(buf[t].x * h, buf[t].y * h);
+                float2 x = buf[pad16(t)];
+                buf[pad16(t)] = make_float2(x.x * h, x.y * h);
             }
             __syncthreads();
         } else {
@@ -325,7 +342,7 @@ bp_status launch_filter(bp_ctx *ctx, const float *proj, void *out, bp_dtype out_
     a.cv = (float)(0.5 * (g.nv - 1) + g.v_off_px);
     const long long nblk = (a.nrows + 2LL * a.pairs - 1) / (2LL * a.pairs);
     if (nblk > 0x7fffffffLL) return fail(ctx, BP_ERR_INVALID_ARG, "bp_filter: too many rows");
-    const int smem = a.pairs * N * (int)sizeof(float2);
+    const int smem = (a.pairs * N + a.pairs * N / 16) * (int)sizeof(float2);
     cudaError_t e = (out_t == BP_F16) ? launch_lg<__half>(ctx->fft_log2, a, (unsigned)nblk, smem, st)
                                       : launch_lg<float>(ctx->fft_log2, a, (unsigned)nblk, smem, st);
     return e == cudaSuccess ? BP_OK : cuda_fail(ctx, e, "ramp_filter_stockham launch");
