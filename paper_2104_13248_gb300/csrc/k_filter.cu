@@ -236,7 +236,7 @@ __device__ __forceinline__ void stockham_pass(float2 *buf, const FilterArgs &a, 
                     x.x *= h;
                     x.y *= h;
                 }
-                buf[p * N + m] = x;
+                buf[pad16(p * N + m)] = x;
             }
         }
     }
