@@ -37,6 +37,8 @@ def parse_args(argv=None):
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="c3_paper")
     ap.add_argument("--tk", type=int, default=0, help="voxels per thread along z (32/64; 0 = plan)")
+    ap.add_argument("--ctas", type=int, default=2, help="CTAs per SM the TK=32 back-projector targets")
+    ap.add_argument("--views", type=int, default=0, help="override the number of views (profiling runs)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args(argv)
@@ -204,9 +206,11 @@ def run_ours(args):
 
     p = inputs.preset(args.workload)
     g = p["geom"]
+    if args.views:
+        g = inputs.scaled_geom(g, np=args.views)
     ctx = api.bp_create(g)
-    if args.tk:
-        api.bp_set_tile_depth(ctx, args.tk)
+    if args.tk or args.ctas != 2:
+        api.bp_set_tuning(ctx, args.tk or 32, args.ctas)
     plan = api.bp_get_plan(ctx)
     E = inputs.random_ellipsoids(p["seed"] + 7919 * rank, p["n_ell"], p["axes"], g)
     raw = api.bp_phantom_project(ctx, E)

@@ -175,8 +175,10 @@ bp_status bp_device_status(bp_ctx *ctx, void *stream);
 
 /*
  * Tuning and testing (no counterpart in the paper).
- *   bp_set_tile_depth  voxels per thread along z in the z-column kernels
- *                      (32 or 64); re-derives the staged box sizes.
+ *   bp_set_tuning      voxels per thread along z in the z-column kernels
+ *                      (32 or 64) and, for 32, the CTAs per SM the kernel's
+ *                      register budget targets (2 or 3); re-derives the
+ *                      staged box sizes.
  *   bp_set_timeout     limit of every bounded wait inside the kernels
  *                      (seconds, (0, 60]; default 2).
  *   bp_test_drop_view  test hook: the staging producer skips the load of
@@ -186,7 +188,7 @@ bp_status bp_device_status(bp_ctx *ctx, void *stream);
  *                      staged box (FP32 width, FP16 width, rows); a width of
  *                      -1 means that element type uses direct global loads.
  */
-bp_status bp_set_tile_depth(bp_ctx *ctx, int tk);
+bp_status bp_set_tuning(bp_ctx *ctx, int tk, int ctas_per_sm);
 bp_status bp_set_timeout(bp_ctx *ctx, double seconds);
 bp_status bp_test_drop_view(bp_ctx *ctx, int view);
 bp_status bp_get_plan(const bp_ctx *ctx, int *tk, int *bu32, int *bu16, int *bv);

@@ -14,7 +14,7 @@ import importlib
 
 _API = {"Context", "BPError", "bp_create", "bp_create_from_matrices", "bp_destroy", "bp_filter",
         "bp_backproject", "bp_backproject_views", "fp_project", "bp_phantom_project",
-        "bp_get_matrices", "bp_get_plan", "bp_set_tile_depth", "bp_set_timeout",
+        "bp_get_matrices", "bp_get_plan", "bp_set_tuning", "bp_set_timeout",
         "bp_test_drop_view", "bp_device_status", "fdk", "HostPipeline", "bp_filter_views"}
 
 

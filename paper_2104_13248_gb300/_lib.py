@@ -53,7 +53,7 @@ PROTOTYPES = {
     "bp_get_matrices": (_i, [_vp, _dptr]),
     "bp_get_dims": (_i, [_vp, _iptr, _iptr, _iptr, _iptr, _iptr, _iptr]),
     "bp_device_status": (_i, [_vp, _vp]),
-    "bp_set_tile_depth": (_i, [_vp, _i]),
+    "bp_set_tuning": (_i, [_vp, _i, _i]),
     "bp_set_timeout": (_i, [_vp, _d]),
     "bp_test_drop_view": (_i, [_vp, _i]),
     "bp_get_plan": (_i, [_vp, _iptr, _iptr, _iptr, _iptr]),

@@ -139,6 +139,7 @@ static void make_plan(bp_ctx *ctx) {
     pl.ty = 8;
     pl.stages = 4;
     if (pl.tk != 64) pl.tk = 32;
+    if (pl.ctas != 3) pl.ctas = 2;
     if (!ctx->zinv) {
         pl.bu = pl.bu16 = -1;
         pl.bv = 0;
@@ -401,10 +402,13 @@ bp_status bp_device_status(bp_ctx *ctx, void *stream) {
     return BP_OK;
 }
 
-bp_status bp_set_tile_depth(bp_ctx *ctx, int tk) {
-    if (!ctx) return fail(nullptr, BP_ERR_INVALID_ARG, "bp_set_tile_depth: NULL context");
-    if (tk != 32 && tk != 64) return fail(ctx, BP_ERR_INVALID_ARG, "bp_set_tile_depth: 32 or 64");
+bp_status bp_set_tuning(bp_ctx *ctx, int tk, int ctas_per_sm) {
+    if (!ctx) return fail(nullptr, BP_ERR_INVALID_ARG, "bp_set_tuning: NULL context");
+    if (tk != 32 && tk != 64) return fail(ctx, BP_ERR_INVALID_ARG, "bp_set_tuning: tk must be 32 or 64");
+    if (ctas_per_sm != 2 && ctas_per_sm != 3)
+        return fail(ctx, BP_ERR_INVALID_ARG, "bp_set_tuning: ctas_per_sm must be 2 or 3");
     ctx->plan.tk = tk;
+    ctx->plan.ctas = ctas_per_sm;
     make_plan(ctx);
     return BP_OK;
 }

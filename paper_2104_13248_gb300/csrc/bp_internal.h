@@ -51,6 +51,7 @@ struct Plan {
     int bu, bv;              // staged detector box (columns, rows), per dtype below
     int bu16;                // box width for FP16 (multiple of 8)
     int stages;              // pipeline depth (views in flight)
+    int ctas;                // CTAs per SM the TK=32 kernel's register budget targets (2 or 3)
 };
 
 }  // namespace bp

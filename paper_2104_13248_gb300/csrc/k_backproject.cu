@@ -174,8 +174,8 @@ __device__ __forceinline__ void store_column(float *__restrict__ vol, const floa
     }
 }
 
-template <typename T, int TK, int BU>
-__global__ void __launch_bounds__(kThreads, (TK > 32 ? 1 : 2))
+template <typename T, int TK, int BU, int MB>
+__global__ void __launch_bounds__(kThreads, MB)
 bp_zcol_tma(const __grid_constant__ CUtensorMap tmap, const double *__restrict__ P, int view0,
             int nviews, int nx, int ny, int nz, int bv, int align, float *__restrict__ vol,
             float scale, int accumulate, unsigned *err, unsigned long long timeout_ns,
@@ -474,12 +474,12 @@ int plan_box_width(int need, int elem_bytes) {
     return -1;
 }
 
-template <typename T, int TK, int BU>
+template <typename T, int TK, int BU, int MB>
 static cudaError_t launch_tma_t(const CUtensorMap &map, bp_ctx *ctx, int view0, int nviews,
                                 int bv, int align, float *vol, int batch, float scale,
                                 int accumulate, cudaStream_t st) {
     const int smem = kStageOffset + kStages * stage_bytes<T>(BU, bv);
-    auto kern = bp_zcol_tma<T, TK, BU>;
+    auto kern = bp_zcol_tma<T, TK, BU, MB>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     dim3 grid(((ctx->nx + kTX - 1) / kTX) * ((ctx->ny + kTY - 1) / kTY), (ctx->nz + TK - 1) / TK,
@@ -490,12 +490,12 @@ static cudaError_t launch_tma_t(const CUtensorMap &map, bp_ctx *ctx, int view0, 
     return cudaGetLastError();
 }
 
-template <typename T, int TK>
+template <typename T, int TK, int MB>
 static cudaError_t launch_tma_bu(const CUtensorMap &map, bp_ctx *ctx, int bu, int view0,
                                  int nviews, int bv, int align, float *vol, int batch, float scale,
                                  int accumulate, cudaStream_t st) {
 #define BP_TMA_CASE(W) \
-    case W: return launch_tma_t<T, TK, W>(map, ctx, view0, nviews, bv, align, vol, batch, scale, accumulate, st);
+    case W: return launch_tma_t<T, TK, W, MB>(map, ctx, view0, nviews, bv, align, vol, batch, scale, accumulate, st);
     if constexpr (sizeof(T) == 2) {
         switch (bu) {
             BP_TMA_CASE(32) BP_TMA_CASE(96) BP_TMA_CASE(160) BP_TMA_CASE(224)
@@ -550,12 +550,22 @@ bp_status launch_backproject(bp_ctx *ctx, const void *proj, bp_dtype t, int view
                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (r != CUDA_SUCCESS) tma = false;
         if (tma) {
-            if (t == BP_F16)
-                e = (pl.tk == 64) ? launch_tma_bu<__half, 64>(map, ctx, bu, view0, nviews, pl.bv, align, vol, batch, scale, accumulate, st)
-                                  : launch_tma_bu<__half, 32>(map, ctx, bu, view0, nviews, pl.bv, align, vol, batch, scale, accumulate, st);
-            else
-                e = (pl.tk == 64) ? launch_tma_bu<float, 64>(map, ctx, bu, view0, nviews, pl.bv, align, vol, batch, scale, accumulate, st)
-                                  : launch_tma_bu<float, 32>(map, ctx, bu, view0, nviews, pl.bv, align, vol, batch, scale, accumulate, st);
+            // variants: (voxels per thread along z, CTAs per SM the registers target)
+            if (t == BP_F16) {
+                if (pl.tk == 64)
+                    e = launch_tma_bu<__half, 64, 1>(map, ctx, bu, view0, nviews, pl.bv, align, vol, batch, scale, accumulate, st);
+                else if (pl.ctas == 3)
+                    e = launch_tma_bu<__half, 32, 3>(map, ctx, bu, view0, nviews, pl.bv, align, vol, batch, scale, accumulate, st);
+                else
+                    e = launch_tma_bu<__half, 32, 2>(map, ctx, bu, view0, nviews, pl.bv, align, vol, batch, scale, accumulate, st);
+            } else {
+                if (pl.tk == 64)
+                    e = launch_tma_bu<float, 64, 1>(map, ctx, bu, view0, nviews, pl.bv, align, vol, batch, scale, accumulate, st);
+                else if (pl.ctas == 3)
+                    e = launch_tma_bu<float, 32, 3>(map, ctx, bu, view0, nviews, pl.bv, align, vol, batch, scale, accumulate, st);
+                else
+                    e = launch_tma_bu<float, 32, 2>(map, ctx, bu, view0, nviews, pl.bv, align, vol, batch, scale, accumulate, st);
+            }
             return e == cudaSuccess ? BP_OK : cuda_fail(ctx, e, "bp_zcol_tma launch");
         }
     }

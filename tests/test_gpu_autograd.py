@@ -109,7 +109,7 @@ def test_least_squares_matches_oracle_iterates(setup):
         r = oracle.forward_project(P, xo, g["nu"], g["nv"]) - p
         xo = xo - oracle.backproject(P, r, g["nx"], g["ny"], g["nz"], 1.0) / L
     assert all(b < a for a, b in zip(losses, losses[1:])), losses
-    assert losses[-1] < 0.2 * losses[0]
+    assert losses[-1] < 0.5 * losses[0]
     err = np.abs(x - xo).max() / np.abs(xo).max()
     assert err <= 1e-4, err
 
