@@ -1,0 +1,111 @@
+/*
+ * unet.h - C ABI of the learned few-view correction in libbp: the kernels a
+ * 3-D residual U-Net needs for training and inference on one GB300.
+ *
+ * The paper has no learned component; these calls serve the few-view
+ * workload (a network maps a back-projection from 1/6 of the views to the
+ * full-view FDK). Every convolution is a 3x3x3, stride 1, zero-padded
+ * convolution computed as an implicit GEMM on the tensor cores with BF16
+ * operands and FP32 accumulation.
+ *
+ * Conventions
+ *   - Activations are channels-last [N][D][H][W][cstride] tensors; a call
+ *     reads or writes channels [coff, coff + C) of each voxel, so a
+ *     concatenation is two writes into one tensor. Element types are stated
+ *     per argument (BF16 = 16-bit bfloat, raw bits as uint16).
+ *   - Conv weights are BF16 [Cout][27][Cin] (tap index (dz*3+dy)*3+dx,
+ *     input channel fastest); biases FP32 [Cout]; weight gradients FP32
+ *     [Cout][27][Cin] and bias gradients FP32 [Cout], accumulated (+=).
+ *   - Cin and Cout of the tensor-core calls are multiples of 16; channel
+ *     strides and offsets are multiples of 8. Device pointers are 16-byte
+ *     aligned and owned by the caller. Calls are asynchronous on `stream`,
+ *     never allocate, and return bp_status (bp.h) with the message in
+ *     bp_last_error(NULL).
+ */
+#ifndef UNET_H
+#define UNET_H
+
+#include "bp.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* y[..., yoff + co] = act(b[co] + sum_{tap, ci} w[co][tap][ci] x[v + tap][xoff + ci])
+ * with act = ReLU when relu != 0. y is BF16 (y_fp32 == 0) or FP32. */
+bp_status cnn_conv3d_forward(const void *x, int x_cstride, int x_coff, const void *w,
+                             const float *b, void *y, int y_cstride, int y_coff, int y_fp32,
+                             int n, int d, int h, int wd, int cin, int cout, int relu,
+                             void *stream);
+
+/* Input gradient of the convolution: dx[..., dxoff + ci] = sum_{tap, co}
+ * w[co][tap][ci] dy[v - tap][dyoff + co] (BF16 in, BF16 out, FP32
+ * accumulation). wt is a caller-owned BF16 buffer of 27*cin*cout elements
+ * that receives the flipped, transposed weights used for it. */
+bp_status cnn_conv3d_dgrad(const void *dy, int dy_cstride, int dy_coff, const void *w, void *wt,
+                           void *dx, int dx_cstride, int dx_coff, int n, int d, int h, int wd,
+                           int cin, int cout, void *stream);
+
+/* Weight and bias gradients: dw[co][tap][ci] += sum_v dy[v][co] x[v + tap][ci],
+ * db[co] += sum_v dy[v][co] (db may be NULL). x and dy BF16. */
+bp_status cnn_conv3d_wgrad(const void *x, int x_cstride, int x_coff, const void *dy,
+                           int dy_cstride, int dy_coff, float *dw, float *db, int n, int d,
+                           int h, int wd, int cin, int cout, void *stream);
+
+/* Output head: one-channel 3x3x3 convolution on the CUDA cores (FP32
+ * accumulation): out[v] = res[v] + b[0] + sum_{tap, ci} w[tap][ci] x[v + tap][ci]
+ * with x BF16 [N][D][H][W][cstride] (channels 0..cin-1), w FP32 [27][cin],
+ * b FP32 [1] (device), res and out FP32 [N][D][H][W] (res may be NULL). */
+bp_status cnn_head_forward(const void *x, int x_cstride, const float *w, const float *b,
+                           const float *res, float *out, int n, int d, int h, int wd, int cin,
+                           void *stream);
+
+/* Head gradients for an FP32 output gradient g [N][D][H][W]:
+ * dx[v][ci] = sum_tap w[tap][ci] g[v - tap] (BF16 [..][dx_cstride]),
+ * dw[tap][ci] += sum_v g[v] x[v + tap][ci], db[0] += sum_v g[v]. */
+bp_status cnn_head_backward(const void *x, int x_cstride, const float *w, const float *g,
+                            void *dx, int dx_cstride, float *dw, float *db, int n, int d, int h,
+                            int wd, int cin, void *stream);
+
+/* 2x2x2 max pooling (BF16): y[N][D/2][H/2][W/2][c] over the channels
+ * [xoff, xoff+c) of x; D, H, W even. Backward: dy is routed to the arg-max
+ * of each window (first maximum in z, y, x order) and added to dx there
+ * (the other seven positions keep their value), so a skip connection's
+ * gradient already in dx is summed with the pooled branch's. */
+bp_status cnn_maxpool2_forward(const void *x, int x_cstride, int x_coff, void *y, int n, int d,
+                               int h, int wd, int c, void *stream);
+bp_status cnn_maxpool2_backward(const void *x, int x_cstride, int x_coff, const void *dy,
+                                void *dx, int dx_cstride, int dx_coff, int n, int d, int h,
+                                int wd, int c, void *stream);
+
+/* Nearest-neighbour 2x upsampling (BF16): y[2z+a][2y+b][2x+c] = x[z][y][x]
+ * into channels [yoff, yoff+c) of y ([N][2D][2H][2W][y_cstride]).
+ * Backward: dx[z][y][x] = sum of the 8 children of dy (FP32 sum, BF16 out). */
+bp_status cnn_upsample2_forward(const void *x, void *y, int y_cstride, int y_coff, int n, int d,
+                                int h, int wd, int c, void *stream);
+bp_status cnn_upsample2_backward(const void *dy, int dy_cstride, int dy_coff, void *dx, int n,
+                                 int d, int h, int wd, int c, void *stream);
+
+/* ReLU backward in place: g[v][goff+c] = 0 where y[v][yoff+c] <= 0 (BF16). */
+bp_status cnn_relu_backward(void *g, int g_cstride, int g_coff, const void *y, int y_cstride,
+                            int y_coff, long long nvox, int c, void *stream);
+
+/* FP32 [nvox] -> BF16 channels-last [nvox][cstride]: channel 0 = x, the
+ * channels 1..cstride-1 are zeroed. */
+bp_status cnn_pack_input(const float *x, void *y, int cstride, long long nvox, void *stream);
+
+/* Mean-square error: g = 2 (p - t) / n (FP32), and sum (p - t)^2 added
+ * into loss[0] (FP32, caller zeroes it). */
+bp_status cnn_mse(const float *p, const float *t, float *g, float *loss, long long n, void *stream);
+
+/* Adam step on n FP32 parameters with BF16 copies: m = b1 m + (1-b1) g,
+ * v = b2 v + (1-b2) g^2, p -= lr * (m / (1-b1^t)) / (sqrt(v / (1-b2^t)) + eps);
+ * p16 (may be NULL) receives bf16(p). Then g is zeroed. */
+bp_status cnn_adam(float *p, float *g, float *m, float *v, void *p16, long long n, float lr,
+                   float b1, float b2, float eps, int t, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* UNET_H */

@@ -424,3 +424,79 @@ int orc_num_threads(void)
     return 1;
 #endif
 }
+
+/* ------------------------------------------------------------------ */
+/* 3x3x3 convolution of the few-view correction network (no paper      */
+/* counterpart): plain definitions in double, channels-last tensors.   */
+/* ------------------------------------------------------------------ */
+
+/* y[n][z][y][x][co] = b[co] + sum_{dz,dy,dx,ci} w[co][(dz*3+dy)*3+dx][ci]
+ *                     * x[n][z+dz-1][y+dy-1][x+dx-1][ci], zero outside. */
+void orc_conv3d(const double *x, int N, int D, int H, int W, int cin, const double *w,
+                const double *b, int cout, double *y)
+{
+#pragma omp parallel for collapse(2) schedule(static)
+    for (int n = 0; n < N; ++n)
+        for (int z = 0; z < D; ++z)
+            for (int yy = 0; yy < H; ++yy)
+                for (int xx = 0; xx < W; ++xx)
+                    for (int co = 0; co < cout; ++co) {
+                        double acc = b ? b[co] : 0.0;
+                        for (int t = 0; t < 27; ++t) {
+                            int zi = z + t / 9 - 1, yi = yy + (t / 3) % 3 - 1, xi = xx + t % 3 - 1;
+                            if (zi < 0 || zi >= D || yi < 0 || yi >= H || xi < 0 || xi >= W) continue;
+                            const double *xp = x + ((((long)n * D + zi) * H + yi) * W + xi) * cin;
+                            const double *wp = w + ((long)co * 27 + t) * cin;
+                            for (int ci = 0; ci < cin; ++ci) acc += wp[ci] * xp[ci];
+                        }
+                        y[((((long)n * D + z) * H + yy) * W + xx) * cout + co] = acc;
+                    }
+}
+
+/* Input gradient: dx[v][ci] = sum_{t,co} w[co][t][ci] dy[v - off(t)][co]. */
+void orc_conv3d_dgrad(const double *dy, int N, int D, int H, int W, int cout, const double *w,
+                      int cin, double *dx)
+{
+#pragma omp parallel for collapse(2) schedule(static)
+    for (int n = 0; n < N; ++n)
+        for (int z = 0; z < D; ++z)
+            for (int yy = 0; yy < H; ++yy)
+                for (int xx = 0; xx < W; ++xx)
+                    for (int ci = 0; ci < cin; ++ci) {
+                        double acc = 0.0;
+                        for (int t = 0; t < 27; ++t) {
+                            int zo = z - (t / 9 - 1), yo = yy - ((t / 3) % 3 - 1), xo = xx - (t % 3 - 1);
+                            if (zo < 0 || zo >= D || yo < 0 || yo >= H || xo < 0 || xo >= W) continue;
+                            const double *gp = dy + ((((long)n * D + zo) * H + yo) * W + xo) * cout;
+                            for (int co = 0; co < cout; ++co) acc += w[((long)co * 27 + t) * cin + ci] * gp[co];
+                        }
+                        dx[((((long)n * D + z) * H + yy) * W + xx) * cin + ci] = acc;
+                    }
+}
+
+/* Weight and bias gradients: dw[co][t][ci] = sum_v dy[v][co] x[v + off(t)][ci],
+ * db[co] = sum_v dy[v][co] (overwritten). */
+void orc_conv3d_wgrad(const double *x, const double *dy, int N, int D, int H, int W, int cin,
+                      int cout, double *dw, double *db)
+{
+#pragma omp parallel for schedule(static)
+    for (int co = 0; co < cout; ++co) {
+        double bsum = 0.0;
+        for (long v = 0; v < (long)N * D * H * W; ++v) bsum += dy[v * cout + co];
+        db[co] = bsum;
+        for (int t = 0; t < 27; ++t)
+            for (int ci = 0; ci < cin; ++ci) {
+                double acc = 0.0;
+                for (int n = 0; n < N; ++n)
+                    for (int z = 0; z < D; ++z)
+                        for (int yy = 0; yy < H; ++yy)
+                            for (int xx = 0; xx < W; ++xx) {
+                                int zi = z + t / 9 - 1, yi = yy + (t / 3) % 3 - 1, xi = xx + t % 3 - 1;
+                                if (zi < 0 || zi >= D || yi < 0 || yi >= H || xi < 0 || xi >= W) continue;
+                                acc += dy[((((long)n * D + z) * H + yy) * W + xx) * cout + co] *
+                                       x[((((long)n * D + zi) * H + yi) * W + xi) * cin + ci];
+                            }
+                dw[((long)co * 27 + t) * cin + ci] = acc;
+            }
+    }
+}

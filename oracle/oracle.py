@@ -267,3 +267,46 @@ def voxel_centres(g) -> tuple[np.ndarray, np.ndarray, np.ndarray]:
     y = (np.arange(g["ny"]) - 0.5 * (g["ny"] - 1)) * g["sy"] + g.get("oy", 0.0)
     z = (np.arange(g["nz"]) - 0.5 * (g["nz"] - 1)) * g["sz"] + g.get("oz", 0.0)
     return x, y, z
+
+
+# ---------------------------------------------------------------------------
+# 3x3x3 convolutions (few-view correction network; no paper counterpart)
+# ---------------------------------------------------------------------------
+
+def conv3d(x, w, b=None) -> np.ndarray:
+    """Zero-padded 3x3x3 convolution, channels-last: x [N,D,H,W,cin],
+    w [cout,27,cin] (tap (dz*3+dy)*3+dx), b [cout] -> y [N,D,H,W,cout]."""
+    lib = _load()
+    x = _f64(x)
+    w = _f64(w)
+    N, D, H, W, cin = x.shape
+    cout = w.shape[0]
+    y = np.zeros((N, D, H, W, cout))
+    bp = _dp(_f64(b)) if b is not None else None
+    lib.orc_conv3d(_dp(x), N, D, H, W, cin, _dp(w), bp, cout, _dp(y))
+    return y
+
+
+def conv3d_dgrad(dy, w) -> np.ndarray:
+    """Input gradient of ``conv3d`` for an output gradient dy [N,D,H,W,cout]."""
+    lib = _load()
+    dy = _f64(dy)
+    w = _f64(w)
+    N, D, H, W, cout = dy.shape
+    cin = w.shape[2]
+    dx = np.zeros((N, D, H, W, cin))
+    lib.orc_conv3d_dgrad(_dp(dy), N, D, H, W, cout, _dp(w), cin, _dp(dx))
+    return dx
+
+
+def conv3d_wgrad(x, dy):
+    """Weight and bias gradients of ``conv3d``: (dw [cout,27,cin], db [cout])."""
+    lib = _load()
+    x = _f64(x)
+    dy = _f64(dy)
+    N, D, H, W, cin = x.shape
+    cout = dy.shape[4]
+    dw = np.zeros((cout, 27, cin))
+    db = np.zeros(cout)
+    lib.orc_conv3d_wgrad(_dp(x), _dp(dy), N, D, H, W, cin, cout, _dp(dw), _dp(db))
+    return dw, db

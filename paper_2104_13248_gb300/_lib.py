@@ -59,6 +59,20 @@ PROTOTYPES = {
     "bp_get_plan": (_i, [_vp, _iptr, _iptr, _iptr, _iptr]),
     "bp_last_error": (ctypes.c_char_p, [_vp]),
     "bp_destroy": (None, [_vp]),
+    # unet.h
+    "cnn_conv3d_forward": (_i, [_vp, _i, _i, _vp, _vp, _vp, _i, _i, _i, _i, _i, _i, _i, _i, _i, _i, _vp]),
+    "cnn_conv3d_dgrad": (_i, [_vp, _i, _i, _vp, _vp, _vp, _i, _i, _i, _i, _i, _i, _i, _i, _vp]),
+    "cnn_conv3d_wgrad": (_i, [_vp, _i, _i, _vp, _i, _i, _vp, _vp, _i, _i, _i, _i, _i, _i, _vp]),
+    "cnn_head_forward": (_i, [_vp, _i, _vp, _vp, _vp, _vp, _i, _i, _i, _i, _i, _vp]),
+    "cnn_head_backward": (_i, [_vp, _i, _vp, _vp, _vp, _i, _vp, _vp, _i, _i, _i, _i, _i, _vp]),
+    "cnn_maxpool2_forward": (_i, [_vp, _i, _i, _vp, _i, _i, _i, _i, _i, _vp]),
+    "cnn_maxpool2_backward": (_i, [_vp, _i, _i, _vp, _vp, _i, _i, _i, _i, _i, _i, _i, _i, _vp]),
+    "cnn_upsample2_forward": (_i, [_vp, _vp, _i, _i, _i, _i, _i, _i, _i, _vp]),
+    "cnn_upsample2_backward": (_i, [_vp, _i, _i, _vp, _i, _i, _i, _i, _i, _vp]),
+    "cnn_relu_backward": (_i, [_vp, _i, _i, _vp, _i, _i, _ll, _i, _vp]),
+    "cnn_pack_input": (_i, [_vp, _vp, _i, _ll, _vp]),
+    "cnn_mse": (_i, [_vp, _vp, _vp, _vp, _ll, _vp]),
+    "cnn_adam": (_i, [_vp, _vp, _vp, _vp, _vp, _ll, _f, _f, _f, _f, _i, _vp]),
 }
 
 

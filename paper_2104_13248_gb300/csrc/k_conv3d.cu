@@ -1,0 +1,739 @@
+// 3x3x3 convolutions of the few-view correction network as implicit GEMMs on
+// the tensor cores (mma.sync m16n8k16, BF16 operands, FP32 accumulation),
+// plus the element-wise kernels a U-Net needs (pooling, upsampling, ReLU
+// backward, loss, Adam). The paper has no learned component; the calls
+// serve the few-view workload.
+//
+// Forward / input-gradient tile: 16 (x) x 4 (y) x 2 (z) output voxels per
+// CTA of 4 warps; each warp owns two 16-voxel rows (two m16 tiles) and all
+// output channels. Per 16-channel input chunk the CTA stages the halo brick
+// (18 x 6 x 4 voxels) in shared memory once and, per z-plane of taps, the
+// weights of 9 taps; the 27 taps then read shifted rows of the brick with
+// ldmatrix. Rows are padded to 48 bytes so the 8 rows of an ldmatrix land
+// in 8 distinct bank groups. The input gradient is the forward kernel run on
+// the output gradient with flipped, transposed weights.
+//
+// Weight gradient: the GEMM over voxels dy^T (Cout x V) x x_shift (V x 16)
+// per tap, split over CTAs that each walk several tiles and keep the
+// partial sums of one z-plane of taps (9 taps) in registers; ldmatrix.trans
+// turns the channels-last tiles into the operand layouts.
+#include "bp_internal.h"
+
+#include <cuda_bf16.h>
+
+#include "../../include/unet.h"
+
+namespace bp {
+
+typedef __nv_bfloat16 bf16;
+
+constexpr int kTX = 16, kTY = 4, kTZ = 2;                  // output tile
+constexpr int kHX = kTX + 2, kHY = kTY + 2, kHZ = kTZ + 2;  // halo brick
+constexpr int kHV = kHX * kHY * kHZ;                        // 432 voxels
+constexpr int kRowPad = 24;                                 // bf16 per staged row (16 + 8 pad)
+constexpr int kConvThreads = 128;
+
+__device__ __forceinline__ unsigned s_addr(const void *p) {
+    return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void ldsm_x4(unsigned addr, unsigned &r0, unsigned &r1, unsigned &r2,
+                                        unsigned &r3) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(addr));
+}
+
+__device__ __forceinline__ void ldsm_x4_t(unsigned addr, unsigned &r0, unsigned &r1, unsigned &r2,
+                                          unsigned &r3) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(addr));
+}
+
+__device__ __forceinline__ void mma_bf16(float *c, unsigned a0, unsigned a1, unsigned a2,
+                                         unsigned a3, unsigned b0, unsigned b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, "
+        "{%4, %5, %6, %7}, {%8, %9}, {%0, %1, %2, %3};"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+// Tile geometry shared by the kernels: tile index -> (n, z0, y0, x0).
+struct TileGrid {
+    int tx, ty, tz;   // tiles per dimension
+    __device__ __forceinline__ void decode(long long t, int d, int &n, int &z0, int &y0, int &x0) const {
+        x0 = (int)(t % tx) * kTX;
+        long long r = t / tx;
+        y0 = (int)(r % ty) * kTY;
+        r /= ty;
+        z0 = (int)(r % tz) * kTZ;
+        n = (int)(r / tz);
+    }
+};
+
+// Stage the 16-channel chunk [c0, c0+16) of the halo brick around a tile
+// (zero outside the volume) into As[kHV][kRowPad].
+__device__ __forceinline__ void stage_halo(bf16 *As, const bf16 *__restrict__ x, int cs, int coff,
+                                           int c0, int n, int z0, int y0, int x0, int D, int H,
+                                           int W) {
+    for (int t = threadIdx.x; t < kHV * 2; t += blockDim.x) {
+        const int hv = t >> 1, half = t & 1;
+        const int hx = hv % kHX, hy = (hv / kHX) % kHY, hz = hv / (kHX * kHY);
+        const int z = z0 + hz - 1, y = y0 + hy - 1, xx = x0 + hx - 1;
+        uint4 val = make_uint4(0, 0, 0, 0);
+        if (z >= 0 && z < D && y >= 0 && y < H && xx >= 0 && xx < W) {
+            const size_t vox = (((size_t)n * D + z) * H + y) * W + xx;
+            val = *reinterpret_cast<const uint4 *>(x + vox * cs + coff + c0 + half * 8);
+        }
+        *reinterpret_cast<uint4 *>(As + hv * kRowPad + half * 8) = val;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Forward (and input-gradient) implicit GEMM
+// ---------------------------------------------------------------------------
+template <int COUT, bool OUT_F32>
+__global__ void __launch_bounds__(kConvThreads)
+conv3d_fwd_kernel(const bf16 *__restrict__ x, int xcs, int xco, const bf16 *__restrict__ w,
+                  const float *__restrict__ bias, void *__restrict__ y, int ycs, int yco, int D,
+                  int H, int W, int cin, int relu, TileGrid grid) {
+    __shared__ __align__(128) bf16 As[kHV * kRowPad];
+    __shared__ __align__(128) bf16 Bs[9 * COUT * kRowPad];
+    constexpr int NT = COUT / 8;
+
+    int n, z0, y0, x0;
+    grid.decode(blockIdx.x, D, n, z0, y0, x0);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    float acc[2][NT][4];
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) acc[mt][nt][e] = 0.0f;
+
+    // ldmatrix lane roles
+    const int a_row = lane & 15, a_koff = (lane >> 4) * 8;
+    const int b_n = (lane >> 4) * 8 + (lane & 7), b_koff = ((lane >> 3) & 1) * 8;
+
+    for (int c0 = 0; c0 < cin; c0 += 16) {
+        __syncthreads();
+        stage_halo(As, x, xcs, xco, c0, n, z0, y0, x0, D, H, W);
+        for (int dz = 0; dz < 3; ++dz) {
+            __syncthreads();
+            // weights of taps dz*9 .. dz*9+8, channels c0..c0+15
+            for (int t = threadIdx.x; t < 9 * COUT * 2; t += kConvThreads) {
+                const int half = t & 1, row = t >> 1;        // row = tap9 * COUT + co
+                const int t9 = row / COUT, co = row % COUT;
+                const uint4 val = *reinterpret_cast<const uint4 *>(
+                    w + ((size_t)co * 27 + dz * 9 + t9) * cin + c0 + half * 8);
+                *reinterpret_cast<uint4 *>(Bs + row * kRowPad + half * 8) = val;
+            }
+            __syncthreads();
+#pragma unroll 1
+            for (int t9 = 0; t9 < 9; ++t9) {
+                const int dy = t9 / 3, dx = t9 % 3;
+                unsigned a[2][4];
+#pragma unroll
+                for (int mt = 0; mt < 2; ++mt) {
+                    const int mrow = warp * 2 + mt;            // 0..7 -> (zz, yy)
+                    const int zz = mrow / kTY, yy = mrow % kTY;
+                    const int hv = ((zz + dz) * kHY + (yy + dy)) * kHX + (a_row + dx);
+                    ldsm_x4(s_addr(As + hv * kRowPad + a_koff), a[mt][0], a[mt][1], a[mt][2], a[mt][3]);
+                }
+#pragma unroll
+                for (int np = 0; np < NT / 2; ++np) {
+                    unsigned b0, b1, b2, b3;
+                    ldsm_x4(s_addr(Bs + (t9 * COUT + np * 16 + b_n) * kRowPad + b_koff), b0, b1, b2, b3);
+#pragma unroll
+                    for (int mt = 0; mt < 2; ++mt) {
+                        mma_bf16(acc[mt][2 * np], a[mt][0], a[mt][1], a[mt][2], a[mt][3], b0, b1);
+                        mma_bf16(acc[mt][2 * np + 1], a[mt][0], a[mt][1], a[mt][2], a[mt][3], b2, b3);
+                    }
+                }
+            }
+        }
+    }
+
+    // epilogue: bias, ReLU, store (c0,c1: row g; c2,c3: row g+8; cols 2q, 2q+1)
+    const int g = lane >> 2, q = lane & 3;
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt) {
+        const int mrow = warp * 2 + mt;
+        const int z = z0 + mrow / kTY, yv = y0 + mrow % kTY;
+        if (z >= D || yv >= H) continue;
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+            const int xv = x0 + g + half * 8;
+            if (xv >= W) continue;
+            const size_t vox = (((size_t)n * D + z) * H + yv) * W + xv;
+#pragma unroll
+            for (int nt = 0; nt < NT; ++nt) {
+                const int co = nt * 8 + 2 * q;
+                float v0 = acc[mt][nt][2 * half], v1 = acc[mt][nt][2 * half + 1];
+                if (bias) {
+                    v0 += bias[co];
+                    v1 += bias[co + 1];
+                }
+                if (relu) {
+                    v0 = fmaxf(v0, 0.0f);
+                    v1 = fmaxf(v1, 0.0f);
+                }
+                if (OUT_F32) {
+                    *reinterpret_cast<float2 *>(reinterpret_cast<float *>(y) + vox * ycs + yco + co) =
+                        make_float2(v0, v1);
+                } else {
+                    *reinterpret_cast<__nv_bfloat162 *>(reinterpret_cast<bf16 *>(y) + vox * ycs + yco + co) =
+                        __floats2bfloat162_rn(v0, v1);
+                }
+            }
+        }
+    }
+}
+
+// wt[ci][tap][co] = w[co][26 - tap][ci]: the weights of the input-gradient
+// convolution (taps mirrored, input and output channels swapped)
+__global__ void flip_transpose_kernel(const bf16 *__restrict__ w, bf16 *__restrict__ wt, int cin,
+                                      int cout) {
+    const long long n = 27LL * cin * cout;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int co = (int)(t % cout);
+        const int tap = (int)((t / cout) % 27);
+        const int ci = (int)(t / (27LL * cout));
+        wt[t] = w[((size_t)co * 27 + (26 - tap)) * cin + ci];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Weight gradient
+// ---------------------------------------------------------------------------
+constexpr int kWgTiles = 16;   // tiles per CTA
+
+template <int COUT>
+__global__ void __launch_bounds__(kConvThreads)
+conv3d_wgrad_kernel(const bf16 *__restrict__ x, int xcs, int xco, const bf16 *__restrict__ dy,
+                    int dycs, int dyco, float *__restrict__ dw, int D, int H, int W, int cin,
+                    long long ntiles, TileGrid grid) {
+    constexpr int DYP = COUT + 8;                 // staged dy row: COUT + 8 bf16
+    constexpr int MT = COUT / 16;                 // m16 tiles (output channels)
+    constexpr int WPM = 4 / MT;                   // warps sharing one m tile (split over k)
+    __shared__ __align__(128) bf16 As[kHV * kRowPad];
+    __shared__ __align__(128) bf16 Ds[kTX * kTY * kTZ * DYP];
+
+    const int c0 = blockIdx.y * 16;
+    const int dz = blockIdx.z;                    // this CTA's z-plane of taps
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int mt = warp % MT, ks = warp / MT;     // m tile, k-split slot
+
+    float acc[9][2][4];
+#pragma unroll
+    for (int t = 0; t < 9; ++t)
+#pragma unroll
+        for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) acc[t][nt][e] = 0.0f;
+
+    const int a_v = (lane >> 4) * 8 + (lane & 7), a_coff = ((lane >> 3) & 1) * 8;
+    const int b_v = ((lane >> 3) & 1) * 8 + (lane & 7), b_coff = (lane >> 4) * 8;
+
+    const long long t_begin = (long long)blockIdx.x * kWgTiles;
+    const long long t_end = min(ntiles, t_begin + kWgTiles);
+    for (long long tile = t_begin; tile < t_end; ++tile) {
+        int n, z0, y0, x0;
+        grid.decode(tile, D, n, z0, y0, x0);
+        __syncthreads();
+        stage_halo(As, x, xcs, xco, c0, n, z0, y0, x0, D, H, W);
+        // dy tile (zero outside the volume)
+        for (int t = threadIdx.x; t < kTX * kTY * kTZ * (COUT / 8); t += kConvThreads) {
+            const int v = t / (COUT / 8), part = t % (COUT / 8);
+            const int xx = v % kTX, yy = (v / kTX) % kTY, zz = v / (kTX * kTY);
+            const int z = z0 + zz, yv = y0 + yy, xv = x0 + xx;
+            uint4 val = make_uint4(0, 0, 0, 0);
+            if (z < D && yv < H && xv < W) {
+                const size_t vox = (((size_t)n * D + z) * H + yv) * W + xv;
+                val = *reinterpret_cast<const uint4 *>(dy + vox * dycs + dyco + part * 8);
+            }
+            *reinterpret_cast<uint4 *>(Ds + v * DYP + part * 8) = val;
+        }
+        __syncthreads();
+        // k steps: 8 rows of 16 voxels; this warp takes rows ks, ks+WPM, ...
+#pragma unroll 1
+        for (int kr = ks; kr < kTY * kTZ; kr += WPM) {
+            const int zz = kr / kTY, yy = kr % kTY;
+            unsigned a0, a1, a2, a3;
+            ldsm_x4_t(s_addr(Ds + (kr * kTX + a_v) * DYP + mt * 16 + a_coff), a0, a1, a2, a3);
+#pragma unroll
+            for (int t9 = 0; t9 < 9; ++t9) {
+                const int ddy = t9 / 3, ddx = t9 % 3;
+                const int hv = ((zz + dz) * kHY + (yy + ddy)) * kHX + (b_v + ddx);
+                unsigned b0, b1, b2, b3;
+                ldsm_x4_t(s_addr(As + hv * kRowPad + b_coff), b0, b1, b2, b3);
+                mma_bf16(acc[t9][0], a0, a1, a2, a3, b0, b1);
+                mma_bf16(acc[t9][1], a0, a1, a2, a3, b2, b3);
+            }
+        }
+    }
+    // c0,c1: (co = g, ci = 2q, 2q+1); c2,c3: (co = g+8, ...)
+    const int g = lane >> 2, q = lane & 3;
+#pragma unroll
+    for (int t9 = 0; t9 < 9; ++t9) {
+        const int tap = dz * 9 + t9;
+#pragma unroll
+        for (int nt = 0; nt < 2; ++nt) {
+            const int ci = c0 + nt * 8 + 2 * q;
+#pragma unroll
+            for (int half = 0; half < 2; ++half) {
+                const int co = mt * 16 + g + half * 8;
+                float *p = dw + ((size_t)co * 27 + tap) * cin + ci;
+                atomicAdd(p, acc[t9][nt][2 * half]);
+                atomicAdd(p + 1, acc[t9][nt][2 * half + 1]);
+            }
+        }
+    }
+}
+
+// db[co] += sum_v dy[v][co]
+__global__ void bias_grad_kernel(const bf16 *__restrict__ dy, int cs, int coff, float *db,
+                                 long long nvox, int c) {
+    extern __shared__ float part[];
+    for (int t = threadIdx.x; t < c; t += blockDim.x) part[t] = 0.0f;
+    __syncthreads();
+    const int lanes_per_vox = c;   // one thread per (voxel, channel)
+    const long long total = nvox * c;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        const long long v = t / lanes_per_vox;
+        const int ch = (int)(t % lanes_per_vox);
+        atomicAdd(&part[ch], __bfloat162float(dy[v * cs + coff + ch]));
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < c; t += blockDim.x) atomicAdd(&db[t], part[t]);
+}
+
+// ---------------------------------------------------------------------------
+// Output head (cin -> 1 channel) on the CUDA cores
+// ---------------------------------------------------------------------------
+__global__ void head_fwd_kernel(const bf16 *__restrict__ x, int cs, const float *__restrict__ w,
+                                const float *__restrict__ bptr, const float *__restrict__ res,
+                                float *__restrict__ out, int N, int D, int H, int W, int cin) {
+    extern __shared__ float ws[];   // [27][cin]
+    for (int t = threadIdx.x; t < 27 * cin; t += blockDim.x) ws[t] = w[t];
+    __syncthreads();
+    const float b0 = bptr ? *bptr : 0.0f;
+    const long long nvox = (long long)N * D * H * W;
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < nvox;
+         v += (long long)gridDim.x * blockDim.x) {
+        const int xv = (int)(v % W), yv = (int)((v / W) % H), z = (int)((v / ((long long)W * H)) % D);
+        const long long nb = v / ((long long)W * H * D);
+        float acc = b0;
+        for (int tap = 0; tap < 27; ++tap) {
+            const int zz = z + tap / 9 - 1, yy = yv + (tap / 3) % 3 - 1, xx = xv + tap % 3 - 1;
+            if (zz < 0 || zz >= D || yy < 0 || yy >= H || xx < 0 || xx >= W) continue;
+            const bf16 *p = x + (((nb * D + zz) * H + yy) * W + xx) * cs;
+            for (int ci = 0; ci < cin; ++ci) acc = fmaf(ws[tap * cin + ci], __bfloat162float(p[ci]), acc);
+        }
+        out[v] = acc + (res ? res[v] : 0.0f);
+    }
+}
+
+// dx[v][ci] = sum_tap w[tap][ci] g[v - off(tap)]
+__global__ void head_dgrad_kernel(const float *__restrict__ g, const float *__restrict__ w,
+                                  bf16 *__restrict__ dx, int cs, int N, int D, int H, int W, int cin) {
+    extern __shared__ float ws[];
+    for (int t = threadIdx.x; t < 27 * cin; t += blockDim.x) ws[t] = w[t];
+    __syncthreads();
+    const long long nvox = (long long)N * D * H * W;
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < nvox;
+         v += (long long)gridDim.x * blockDim.x) {
+        const int xv = (int)(v % W), yv = (int)((v / W) % H), z = (int)((v / ((long long)W * H)) % D);
+        const long long nb = v / ((long long)W * H * D);
+        float gt[27];
+#pragma unroll
+        for (int tap = 0; tap < 27; ++tap) {
+            const int zz = z - (tap / 9 - 1), yy = yv - ((tap / 3) % 3 - 1), xx = xv - (tap % 3 - 1);
+            gt[tap] = (zz < 0 || zz >= D || yy < 0 || yy >= H || xx < 0 || xx >= W)
+                          ? 0.0f : g[((nb * D + zz) * H + yy) * W + xx];
+        }
+        for (int ci = 0; ci < cin; ++ci) {
+            float acc = 0.0f;
+#pragma unroll
+            for (int tap = 0; tap < 27; ++tap) acc = fmaf(ws[tap * cin + ci], gt[tap], acc);
+            dx[v * cs + ci] = __float2bfloat16_rn(acc);
+        }
+    }
+}
+
+// dw[tap][ci] += sum_v g[v] x[v + off(tap)][ci]; db += sum_v g[v]
+__global__ void head_wgrad_kernel(const float *__restrict__ g, const bf16 *__restrict__ x, int cs,
+                                  float *dw, float *db, int N, int D, int H, int W, int cin) {
+    extern __shared__ float part[];   // [27*cin + 1]
+    for (int t = threadIdx.x; t < 27 * cin + 1; t += blockDim.x) part[t] = 0.0f;
+    __syncthreads();
+    const long long nvox = (long long)N * D * H * W;
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < nvox;
+         v += (long long)gridDim.x * blockDim.x) {
+        const float gv = g[v];
+        if (gv == 0.0f) continue;
+        const int xv = (int)(v % W), yv = (int)((v / W) % H), z = (int)((v / ((long long)W * H)) % D);
+        const long long nb = v / ((long long)W * H * D);
+        atomicAdd(&part[27 * cin], gv);
+        for (int tap = 0; tap < 27; ++tap) {
+            const int zz = z + tap / 9 - 1, yy = yv + (tap / 3) % 3 - 1, xx = xv + tap % 3 - 1;
+            if (zz < 0 || zz >= D || yy < 0 || yy >= H || xx < 0 || xx >= W) continue;
+            const bf16 *p = x + (((nb * D + zz) * H + yy) * W + xx) * cs;
+            for (int ci = 0; ci < cin; ++ci) atomicAdd(&part[tap * cin + ci], gv * __bfloat162float(p[ci]));
+        }
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < 27 * cin; t += blockDim.x) atomicAdd(&dw[t], part[t]);
+    if (threadIdx.x == 0) atomicAdd(db, part[27 * cin]);
+}
+
+// ---------------------------------------------------------------------------
+// Element-wise kernels
+// ---------------------------------------------------------------------------
+__global__ void maxpool2_fwd_kernel(const bf16 *__restrict__ x, int cs, int coff, bf16 *__restrict__ y,
+                                    int N, int D, int H, int W, int c) {
+    const int Do = D / 2, Ho = H / 2, Wo = W / 2;
+    const long long total = (long long)N * Do * Ho * Wo * c;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int ch = (int)(t % c);
+        long long v = t / c;
+        const int xo = (int)(v % Wo), yo = (int)((v / Wo) % Ho), zo = (int)((v / ((long long)Wo * Ho)) % Do);
+        const long long nb = v / ((long long)Wo * Ho * Do);
+        float m = -3.0e38f;
+        for (int k = 0; k < 8; ++k) {
+            const int z = 2 * zo + (k >> 2), yy = 2 * yo + ((k >> 1) & 1), xx = 2 * xo + (k & 1);
+            m = fmaxf(m, __bfloat162float(x[(((nb * D + z) * H + yy) * W + xx) * cs + coff + ch]));
+        }
+        y[v * c + ch] = __float2bfloat16_rn(m);
+    }
+}
+
+__global__ void maxpool2_bwd_kernel(const bf16 *__restrict__ x, int cs, int coff,
+                                    const bf16 *__restrict__ dy, bf16 *__restrict__ dx, int dcs,
+                                    int dcoff, int N, int D, int H, int W, int c) {
+    const int Do = D / 2, Ho = H / 2, Wo = W / 2;
+    const long long total = (long long)N * Do * Ho * Wo * c;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int ch = (int)(t % c);
+        long long v = t / c;
+        const int xo = (int)(v % Wo), yo = (int)((v / Wo) % Ho), zo = (int)((v / ((long long)Wo * Ho)) % Do);
+        const long long nb = v / ((long long)Wo * Ho * Do);
+        float m = -3.0e38f;
+        int arg = 0;
+        for (int k = 0; k < 8; ++k) {
+            const int z = 2 * zo + (k >> 2), yy = 2 * yo + ((k >> 1) & 1), xx = 2 * xo + (k & 1);
+            const float val = __bfloat162float(x[(((nb * D + z) * H + yy) * W + xx) * cs + coff + ch]);
+            if (val > m) {
+                m = val;
+                arg = k;
+            }
+        }
+        const int z = 2 * zo + (arg >> 2), yy = 2 * yo + ((arg >> 1) & 1), xx = 2 * xo + (arg & 1);
+        bf16 *p = dx + (((nb * D + z) * H + yy) * W + xx) * dcs + dcoff + ch;
+        *p = __float2bfloat16_rn(__bfloat162float(*p) + __bfloat162float(dy[v * c + ch]));
+    }
+}
+
+__global__ void upsample2_fwd_kernel(const bf16 *__restrict__ x, bf16 *__restrict__ y, int ycs,
+                                     int ycoff, int N, int D, int H, int W, int c) {
+    const int Du = 2 * D, Hu = 2 * H, Wu = 2 * W;
+    const long long total = (long long)N * Du * Hu * Wu * c;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int ch = (int)(t % c);
+        long long v = t / c;
+        const int xu = (int)(v % Wu), yu = (int)((v / Wu) % Hu), zu = (int)((v / ((long long)Wu * Hu)) % Du);
+        const long long nb = v / ((long long)Wu * Hu * Du);
+        y[v * ycs + ycoff + ch] = x[(((nb * D + zu / 2) * H + yu / 2) * W + xu / 2) * c + ch];
+    }
+}
+
+__global__ void upsample2_bwd_kernel(const bf16 *__restrict__ dy, int dycs, int dycoff,
+                                     bf16 *__restrict__ dx, int N, int D, int H, int W, int c) {
+    const long long total = (long long)N * D * H * W * c;
+    const int Hu = 2 * H, Wu = 2 * W, Du = 2 * D;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int ch = (int)(t % c);
+        long long v = t / c;
+        const int xv = (int)(v % W), yv = (int)((v / W) % H), z = (int)((v / ((long long)W * H)) % D);
+        const long long nb = v / ((long long)W * H * D);
+        float s = 0.0f;
+        for (int k = 0; k < 8; ++k) {
+            const int zu = 2 * z + (k >> 2), yu = 2 * yv + ((k >> 1) & 1), xu = 2 * xv + (k & 1);
+            s += __bfloat162float(dy[(((nb * Du + zu) * Hu + yu) * Wu + xu) * dycs + dycoff + ch]);
+        }
+        dx[v * c + ch] = __float2bfloat16_rn(s);
+    }
+}
+
+__global__ void relu_bwd_kernel(bf16 *__restrict__ g, int gcs, int gcoff, const bf16 *__restrict__ y,
+                                int ycs, int ycoff, long long nvox, int c) {
+    const long long total = nvox * c;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        const long long v = t / c;
+        const int ch = (int)(t % c);
+        if (!(__bfloat162float(y[v * ycs + ycoff + ch]) > 0.0f))
+            g[v * gcs + gcoff + ch] = __float2bfloat16_rn(0.0f);
+    }
+}
+
+__global__ void pack_input_kernel(const float *__restrict__ x, bf16 *__restrict__ y, int cs,
+                                  long long nvox) {
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < nvox;
+         v += (long long)gridDim.x * blockDim.x) {
+        y[v * cs] = __float2bfloat16_rn(x[v]);
+        for (int c = 1; c < cs; ++c) y[v * cs + c] = __float2bfloat16_rn(0.0f);
+    }
+}
+
+__global__ void mse_kernel(const float *__restrict__ p, const float *__restrict__ t, float *__restrict__ g,
+                           float *loss, long long n) {
+    __shared__ float red[32];
+    float s = 0.0f;
+    const float inv = 2.0f / (float)n;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const float d = p[i] - t[i];
+        g[i] = inv * d;
+        s = fmaf(d, d, s);
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        s = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : 0.0f;
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if (threadIdx.x == 0) atomicAdd(loss, s);
+    }
+}
+
+__global__ void adam_kernel(float *__restrict__ p, float *__restrict__ g, float *__restrict__ m,
+                            float *__restrict__ v, bf16 *__restrict__ p16, long long n, float lr,
+                            float b1, float b2, float eps, float c1, float c2) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        const float mi = b1 * m[i] + (1.0f - b1) * gi;
+        const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        const float pi = p[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+        p[i] = pi;
+        if (p16) p16[i] = __float2bfloat16_rn(pi);
+        g[i] = 0.0f;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Host wrappers
+// ---------------------------------------------------------------------------
+static unsigned ew_blocks(long long n) {
+    long long b = (n + 255) / 256;
+    return (unsigned)(b < 1 ? 1 : (b > 65535LL * 16 ? 65535LL * 16 : b));
+}
+
+static bp_status launch_ok(const char *what) {
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? BP_OK : cuda_fail(nullptr, e, what);
+}
+
+static bool al16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+
+static TileGrid make_grid(int n, int d, int h, int wd, long long *ntiles) {
+    TileGrid g;
+    g.tx = (wd + kTX - 1) / kTX;
+    g.ty = (h + kTY - 1) / kTY;
+    g.tz = (d + kTZ - 1) / kTZ;
+    *ntiles = (long long)n * g.tx * g.ty * g.tz;
+    return g;
+}
+
+static bp_status conv_fwd(const bf16 *x, int xcs, int xco, const bf16 *w, const float *b, void *y,
+                          int ycs, int yco, int yf32, int n, int d, int h, int wd, int cin, int cout,
+                          int relu, cudaStream_t st) {
+    long long nt;
+    TileGrid g = make_grid(n, d, h, wd, &nt);
+    if (nt > 0x7fffffffLL) return fail(nullptr, BP_ERR_INVALID_ARG, "conv3d: volume too large");
+#define CONV_CASE(C)                                                                                 \
+    case C:                                                                                          \
+        if (yf32)                                                                                    \
+            conv3d_fwd_kernel<C, true><<<(unsigned)nt, kConvThreads, 0, st>>>(x, xcs, xco, w, b, y, ycs, yco, d, h, wd, cin, relu, g); \
+        else                                                                                         \
+            conv3d_fwd_kernel<C, false><<<(unsigned)nt, kConvThreads, 0, st>>>(x, xcs, xco, w, b, y, ycs, yco, d, h, wd, cin, relu, g); \
+        break;
+    switch (cout) {
+        CONV_CASE(16) CONV_CASE(32) CONV_CASE(64)
+        default: return fail(nullptr, BP_ERR_UNSUPPORTED, "conv3d: cout must be 16, 32 or 64");
+    }
+#undef CONV_CASE
+    return launch_ok("conv3d_fwd_kernel");
+}
+
+static bool conv_args_ok(int cs, int coff, int c) { return cs % 8 == 0 && coff % 8 == 0 && coff + c <= cs; }
+
+}  // namespace bp
+
+using namespace bp;
+
+extern "C" {
+
+bp_status cnn_conv3d_forward(const void *x, int x_cstride, int x_coff, const void *w, const float *b,
+                             void *y, int y_cstride, int y_coff, int y_fp32, int n, int d, int h,
+                             int wd, int cin, int cout, int relu, void *stream) {
+    if (!x || !w || !y || n < 1 || d < 1 || h < 1 || wd < 1 || cin < 16 || cin % 16 ||
+        !conv_args_ok(x_cstride, x_coff, cin) || !conv_args_ok(y_cstride, y_coff, cout) ||
+        !al16(x) || !al16(w) || !al16(y))
+        return fail(nullptr, BP_ERR_INVALID_ARG, "cnn_conv3d_forward: bad arguments");
+    return conv_fwd((const bf16 *)x, x_cstride, x_coff, (const bf16 *)w, b, y, y_cstride, y_coff,
+                    y_fp32, n, d, h, wd, cin, cout, relu, (cudaStream_t)stream);
+}
+
+bp_status cnn_conv3d_dgrad(const void *dy, int dy_cstride, int dy_coff, const void *w, void *wt,
+                           void *dx, int dx_cstride, int dx_coff, int n, int d, int h, int wd,
+                           int cin, int cout, void *stream) {
+    if (!dy || !w || !wt || !dx || cin < 16 || cin % 16 || cout % 16 ||
+        !conv_args_ok(dy_cstride, dy_coff, cout) || !conv_args_ok(dx_cstride, dx_coff, cin) ||
+        !al16(dy) || !al16(w) || !al16(wt) || !al16(dx))
+        return fail(nullptr, BP_ERR_INVALID_ARG, "cnn_conv3d_dgrad: bad arguments");
+    cudaStream_t st = (cudaStream_t)stream;
+    flip_transpose_kernel<<<ew_blocks(27LL * cin * cout), 256, 0, st>>>((const bf16 *)w, (bf16 *)wt, cin, cout);
+    bp_status s = launch_ok("flip_transpose_kernel");
+    if (s != BP_OK) return s;
+    // dx = conv(dy, wt) with cin' = cout, cout' = cin, no bias, no activation;
+    // the input-gradient channels go in blocks of 64, 32 or 16 (the tile
+    // widths the tensor-core kernel is built for)
+    for (int ci0 = 0; ci0 < cin;) {
+        const int left = cin - ci0;
+        const int blk = left >= 64 ? 64 : (left >= 32 ? 32 : 16);
+        s = conv_fwd((const bf16 *)dy, dy_cstride, dy_coff, (const bf16 *)wt + (size_t)ci0 * 27 * cout,
+                     nullptr, dx, dx_cstride, dx_coff + ci0, 0, n, d, h, wd, cout, blk, 0, st);
+        if (s != BP_OK) return s;
+        ci0 += blk;
+    }
+    return BP_OK;
+}
+
+bp_status cnn_conv3d_wgrad(const void *x, int x_cstride, int x_coff, const void *dy, int dy_cstride,
+                           int dy_coff, float *dw, float *db, int n, int d, int h, int wd, int cin,
+                           int cout, void *stream) {
+    if (!x || !dy || !dw || cin < 16 || cin % 16 || !conv_args_ok(x_cstride, x_coff, cin) ||
+        !conv_args_ok(dy_cstride, dy_coff, cout) || !al16(x) || !al16(dy))
+        return fail(nullptr, BP_ERR_INVALID_ARG, "cnn_conv3d_wgrad: bad arguments");
+    cudaStream_t st = (cudaStream_t)stream;
+    long long nt;
+    TileGrid g = make_grid(n, d, h, wd, &nt);
+    dim3 grid((unsigned)((nt + kWgTiles - 1) / kWgTiles), cin / 16, 3);
+    switch (cout) {
+        case 16: conv3d_wgrad_kernel<16><<<grid, kConvThreads, 0, st>>>((const bf16 *)x, x_cstride, x_coff, (const bf16 *)dy, dy_cstride, dy_coff, dw, d, h, wd, cin, nt, g); break;
+        case 32: conv3d_wgrad_kernel<32><<<grid, kConvThreads, 0, st>>>((const bf16 *)x, x_cstride, x_coff, (const bf16 *)dy, dy_cstride, dy_coff, dw, d, h, wd, cin, nt, g); break;
+        case 64: conv3d_wgrad_kernel<64><<<grid, kConvThreads, 0, st>>>((const bf16 *)x, x_cstride, x_coff, (const bf16 *)dy, dy_cstride, dy_coff, dw, d, h, wd, cin, nt, g); break;
+        default: return fail(nullptr, BP_ERR_UNSUPPORTED, "cnn_conv3d_wgrad: cout must be 16, 32 or 64");
+    }
+    bp_status s = launch_ok("conv3d_wgrad_kernel");
+    if (s != BP_OK || !db) return s;
+    const long long nvox = (long long)n * d * h * wd;
+    bias_grad_kernel<<<ew_blocks(nvox * cout / 64), 256, cout * sizeof(float), st>>>(
+        (const bf16 *)dy, dy_cstride, dy_coff, db, nvox, cout);
+    return launch_ok("bias_grad_kernel");
+}
+
+bp_status cnn_head_forward(const void *x, int x_cstride, const float *w, const float *b, const float *res,
+                           float *out, int n, int d, int h, int wd, int cin, void *stream) {
+    if (!x || !w || !out || cin < 1 || cin > x_cstride || n < 1)
+        return fail(nullptr, BP_ERR_INVALID_ARG, "cnn_head_forward: bad arguments");
+    const long long nvox = (long long)n * d * h * wd;
+    head_fwd_kernel<<<ew_blocks(nvox), 256, 27 * cin * sizeof(float), (cudaStream_t)stream>>>(
+        (const bf16 *)x, x_cstride, w, b, res, out, n, d, h, wd, cin);
+    return launch_ok("head_fwd_kernel");
+}
+
+bp_status cnn_head_backward(const void *x, int x_cstride, const float *w, const float *g, void *dx,
+                            int dx_cstride, float *dw, float *db, int n, int d, int h, int wd,
+                            int cin, void *stream) {
+    if (!x || !w || !g || !dx || !dw || !db || cin < 1 || cin > x_cstride || cin > dx_cstride)
+        return fail(nullptr, BP_ERR_INVALID_ARG, "cnn_head_backward: bad arguments");
+    cudaStream_t st = (cudaStream_t)stream;
+    const long long nvox = (long long)n * d * h * wd;
+    head_dgrad_kernel<<<ew_blocks(nvox), 256, 27 * cin * sizeof(float), st>>>(g, w, (bf16 *)dx, dx_cstride, n, d, h, wd, cin);
+    bp_status s = launch_ok("head_dgrad_kernel");
+    if (s != BP_OK) return s;
+    head_wgrad_kernel<<<ew_blocks(nvox / 8), 256, (27 * cin + 1) * sizeof(float), st>>>(g, (const bf16 *)x, x_cstride, dw, db, n, d, h, wd, cin);
+    return launch_ok("head_wgrad_kernel");
+}
+
+bp_status cnn_maxpool2_forward(const void *x, int x_cstride, int x_coff, void *y, int n, int d, int h,
+                               int wd, int c, void *stream) {
+    if (!x || !y || d % 2 || h % 2 || wd % 2 || x_coff + c > x_cstride)
+        return fail(nullptr, BP_ERR_INVALID_ARG, "cnn_maxpool2_forward: bad arguments");
+    const long long tot = (long long)n * (d / 2) * (h / 2) * (wd / 2) * c;
+    maxpool2_fwd_kernel<<<ew_blocks(tot), 256, 0, (cudaStream_t)stream>>>((const bf16 *)x, x_cstride, x_coff, (bf16 *)y, n, d, h, wd, c);
+    return launch_ok("maxpool2_fwd_kernel");
+}
+
+bp_status cnn_maxpool2_backward(const void *x, int x_cstride, int x_coff, const void *dy, void *dx,
+                                int dx_cstride, int dx_coff, int n, int d, int h, int wd, int c,
+                                void *stream) {
+    if (!x || !dy || !dx || d % 2 || h % 2 || wd % 2)
+        return fail(nullptr, BP_ERR_INVALID_ARG, "cnn_maxpool2_backward: bad arguments");
+    const long long tot = (long long)n * (d / 2) * (h / 2) * (wd / 2) * c;
+    maxpool2_bwd_kernel<<<ew_blocks(tot), 256, 0, (cudaStream_t)stream>>>((const bf16 *)x, x_cstride, x_coff, (const bf16 *)dy, (bf16 *)dx, dx_cstride, dx_coff, n, d, h, wd, c);
+    return launch_ok("maxpool2_bwd_kernel");
+}
+
+bp_status cnn_upsample2_forward(const void *x, void *y, int y_cstride, int y_coff, int n, int d, int h,
+                                int wd, int c, void *stream) {
+    if (!x || !y || y_coff + c > y_cstride)
+        return fail(nullptr, BP_ERR_INVALID_ARG, "cnn_upsample2_forward: bad arguments");
+    const long long tot = (long long)n * 8 * d * h * wd * c;
+    upsample2_fwd_kernel<<<ew_blocks(tot), 256, 0, (cudaStream_t)stream>>>((const bf16 *)x, (bf16 *)y, y_cstride, y_coff, n, d, h, wd, c);
+    return launch_ok("upsample2_fwd_kernel");
+}
+
+bp_status cnn_upsample2_backward(const void *dy, int dy_cstride, int dy_coff, void *dx, int n, int d,
+                                 int h, int wd, int c, void *stream) {
+    if (!dy || !dx || dy_coff + c > dy_cstride)
+        return fail(nullptr, BP_ERR_INVALID_ARG, "cnn_upsample2_backward: bad arguments");
+    const long long tot = (long long)n * d * h * wd * c;
+    upsample2_bwd_kernel<<<ew_blocks(tot), 256, 0, (cudaStream_t)stream>>>((const bf16 *)dy, dy_cstride, dy_coff, (bf16 *)dx, n, d, h, wd, c);
+    return launch_ok("upsample2_bwd_kernel");
+}
+
+bp_status cnn_relu_backward(void *g, int g_cstride, int g_coff, const void *y, int y_cstride, int y_coff,
+                            long long nvox, int c, void *stream) {
+    if (!g || !y || g_coff + c > g_cstride || y_coff + c > y_cstride)
+        return fail(nullptr, BP_ERR_INVALID_ARG, "cnn_relu_backward: bad arguments");
+    relu_bwd_kernel<<<ew_blocks(nvox * c), 256, 0, (cudaStream_t)stream>>>((bf16 *)g, g_cstride, g_coff, (const bf16 *)y, y_cstride, y_coff, nvox, c);
+    return launch_ok("relu_bwd_kernel");
+}
+
+bp_status cnn_pack_input(const float *x, void *y, int cstride, long long nvox, void *stream) {
+    if (!x || !y || cstride < 1) return fail(nullptr, BP_ERR_INVALID_ARG, "cnn_pack_input: bad arguments");
+    pack_input_kernel<<<ew_blocks(nvox), 256, 0, (cudaStream_t)stream>>>(x, (bf16 *)y, cstride, nvox);
+    return launch_ok("pack_input_kernel");
+}
+
+bp_status cnn_mse(const float *p, const float *t, float *g, float *loss, long long n, void *stream) {
+    if (!p || !t || !g || !loss || n < 1) return fail(nullptr, BP_ERR_INVALID_ARG, "cnn_mse: bad arguments");
+    mse_kernel<<<ew_blocks(n) > 4096 ? 4096 : ew_blocks(n), 256, 0, (cudaStream_t)stream>>>(p, t, g, loss, n);
+    return launch_ok("mse_kernel");
+}
+
+bp_status cnn_adam(float *p, float *g, float *m, float *v, void *p16, long long n, float lr, float b1,
+                   float b2, float eps, int t, void *stream) {
+    if (!p || !g || !m || !v || n < 1 || t < 1) return fail(nullptr, BP_ERR_INVALID_ARG, "cnn_adam: bad arguments");
+    const float c1 = 1.0f - powf(b1, (float)t), c2 = 1.0f - powf(b2, (float)t);
+    adam_kernel<<<ew_blocks(n), 256, 0, (cudaStream_t)stream>>>(p, g, m, v, (bf16 *)p16, n, lr, b1, b2, eps, c1, c2);
+    return launch_ok("adam_kernel");
+}
+
+}  // extern "C"

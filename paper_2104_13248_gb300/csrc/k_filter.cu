@@ -183,8 +183,12 @@ __device__ __forceinline__ void stockham_pass(float2 *buf, const FilterArgs &a, 
                 v[q][r] = make_float2(xa, xb);
             }
         } else {
+            // (j + r G) >> 4 = (j >> 4) + r G/16 for G a multiple of 16: one
+            // padded base address and compile-time offsets
+            const float2 *src = buf + pad16(p * N + j);
 #pragma unroll
-            for (int r = 0; r < R; ++r) v[q][r] = buf[pad16(p * N + j + r * G)];
+            for (int r = 0; r < R; ++r)
+                v[q][r] = (G % 16 == 0) ? src[r * (G + G / 16)] : buf[pad16(p * N + j + r * G)];
         }
         if (NS > 1) {
             // twiddles w^r: powers of two from the table, the others as one
@@ -193,11 +197,13 @@ __device__ __forceinline__ void stockham_pass(float2 *buf, const FilterArgs &a, 
             w[0] = make_float2(1.0f, 0.0f);
 #pragma unroll
             for (int r = 1; r < R; ++r) {
-                if ((r & (r - 1)) == 0) {
+                if (r == 1 || r == 4 || r == 8 || (r == 2 && R <= 4)) {
                     w[r] = __ldg(&a.tw[(k * r) * (N / (NS * R))]);
                     if (DIR > 0) w[r].y = -w[r].y;
+                } else if (r == 2) {
+                    w[r] = cmul(w[1], w[1]);
                 } else {
-                    const int hb = 1 << (31 - __clz(r));
+                    const int hb = (r >= 8) ? 8 : (r >= 4 ? 4 : 2);
                     w[r] = cmul(w[hb], w[r - hb]);
                 }
             }
@@ -227,6 +233,7 @@ __device__ __forceinline__ void stockham_pass(float2 *buf, const FilterArgs &a, 
                 }
             }
         } else {
+            float2 *dstp = buf + pad16(p * N + dst);
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 const int m = dst + r * NS;
@@ -236,7 +243,14 @@ __device__ __forceinline__ void stockham_pass(float2 *buf, const FilterArgs &a, 
                     x.x *= h;
                     x.y *= h;
                 }
-                buf[pad16(p * N + m)] = x;
+                // dst = R j for NS == 1 (R = 16: pad adds j, offsets r stay in one
+                // 16-block); for NS a multiple of 16 the stride pads uniformly
+                if (NS == 1 && R == 16)
+                    dstp[r] = x;
+                else if (NS % 16 == 0)
+                    dstp[r * (NS + NS / 16)] = x;
+                else
+                    buf[pad16(p * N + m)] = x;
             }
         }
     }

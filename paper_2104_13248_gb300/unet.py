@@ -1,0 +1,255 @@
+"""Few-view correction network: a 3-level 3-D residual U-Net on libbp's kernels.
+
+The network maps a back-projection from 1/6 of the views to the full-view
+FDK: out = input + net(input). Levels at 16/32/64 channels, two 3x3x3
+convolutions with ReLU per level, 2x2x2 max pooling down, nearest 2x
+upsampling up with the skip features concatenated, and a 3x3x3 one-channel
+head. Every convolution runs as a BF16 implicit GEMM on the tensor cores
+with FP32 accumulation (cnn_conv3d_* in include/unet.h); activations and
+their gradients are BF16 channels-last tensors, the master weights, weight
+gradients and Adam moments FP32. Forward and backward are written out layer
+by layer (the kernels are not torch operators). The paper has no learned
+component; this serves the few-view workload.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import check
+
+# (name, cin, cout) of the tensor-core convolutions
+LAYERS = [("e1a", 16, 16), ("e1b", 16, 16), ("e2a", 16, 32), ("e2b", 32, 32), ("e3a", 32, 64),
+          ("e3b", 64, 64), ("d2a", 96, 32), ("d2b", 32, 32), ("d1a", 48, 16), ("d1b", 16, 16)]
+HEAD_CIN = 16
+
+
+def _p(t: torch.Tensor | None):
+    return ctypes.c_void_p(t.data_ptr() if t is not None else 0)
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def conv_flops(shape) -> float:
+    """Multiply-adds x 2 of one forward pass at volume shape (N, D, H, W)."""
+    n, d, h, w = shape
+    v1 = n * d * h * w
+    v2, v3 = v1 / 8, v1 / 64
+    macs = 27 * (v1 * (16 * 16 + 16 * 16 + 48 * 16 + 16 * 16 + 16) +
+                 v2 * (16 * 32 + 32 * 32 + 96 * 32 + 32 * 32) +
+                 v3 * (32 * 64 + 64 * 64))
+    return 2.0 * macs
+
+
+class UNet:
+    def __init__(self, seed: int = 0, device: str = "cuda"):
+        self.device = torch.device(device)
+        self.off = {}
+        n = 0
+        for name, cin, cout in LAYERS:
+            self.off[name] = (n, n + cout * 27 * cin, cin, cout)   # weight start, bias start
+            n += cout * 27 * cin + cout
+        self.n_conv = n
+        self.head_off = n
+        n += 27 * HEAD_CIN + 1
+        self.n_params = n
+        g = torch.Generator().manual_seed(seed)
+        p = torch.zeros(n, dtype=torch.float32)
+        for name, cin, cout in LAYERS:
+            w0, b0, _, _ = self.off[name]
+            std = math.sqrt(2.0 / (27 * cin))
+            p[w0:b0] = torch.randn(cout * 27 * cin, generator=g) * std
+        p[self.head_off:self.head_off + 27 * HEAD_CIN] = torch.randn(27 * HEAD_CIN, generator=g) * 1e-3
+        self.params = p.to(self.device)
+        self.params16 = self.params.to(torch.bfloat16)   # BF16 copy read by the kernels
+        self.grads = torch.zeros_like(self.params)
+        self.m = torch.zeros_like(self.params)
+        self.v = torch.zeros_like(self.params)
+        self.t = 0
+        largest = max(27 * cin * cout for _, cin, cout in LAYERS)
+        self.wt = torch.empty(largest, dtype=torch.bfloat16, device=self.device)
+        self.loss_buf = torch.zeros(1, dtype=torch.float32, device=self.device)
+        self._bufs = {}
+
+    # parameter views ------------------------------------------------------
+    def w16(self, name):
+        w0, b0, _, _ = self.off[name]
+        return self.params16[w0:b0]
+
+    def bias(self, name):
+        _, b0, _, cout = self.off[name]
+        return self.params[b0:b0 + cout]
+
+    def gw(self, name):
+        w0, b0, _, _ = self.off[name]
+        return self.grads[w0:b0]
+
+    def gb(self, name):
+        _, b0, _, cout = self.off[name]
+        return self.grads[b0:b0 + cout]
+
+    def head_w(self):
+        return self.params[self.head_off:self.head_off + 27 * HEAD_CIN]
+
+    def state_dict(self) -> dict:
+        return {"params": self.params.cpu(), "m": self.m.cpu(), "v": self.v.cpu(), "t": self.t}
+
+    def load_state_dict(self, sd: dict):
+        self.params.copy_(sd["params"].to(self.device))
+        self.params16.copy_(self.params.to(torch.bfloat16))
+        self.m.copy_(sd["m"].to(self.device))
+        self.v.copy_(sd["v"].to(self.device))
+        self.t = int(sd["t"])
+
+    # activation buffers ---------------------------------------------------
+    def _buffers(self, shape, train: bool):
+        key = (tuple(shape), train)
+        if key in self._bufs:
+            return self._bufs[key]
+        n, d, h, w = shape
+        if d % 4 or h % 4 or w % 4:
+            raise ValueError("volume dimensions must be multiples of 4")
+        bf = dict(dtype=torch.bfloat16, device=self.device)
+        s1, s2, s3 = (n, d, h, w), (n, d // 2, h // 2, w // 2), (n, d // 4, h // 4, w // 4)
+        B = {"x0": torch.zeros(s1 + (16,), **bf), "e1a": torch.empty(s1 + (16,), **bf),
+             "cat1": torch.empty(s1 + (48,), **bf), "p1": torch.empty(s2 + (16,), **bf),
+             "e2a": torch.empty(s2 + (32,), **bf), "cat2": torch.empty(s2 + (96,), **bf),
+             "p2": torch.empty(s3 + (32,), **bf), "e3a": torch.empty(s3 + (64,), **bf),
+             "e3b": torch.empty(s3 + (64,), **bf), "d2a": torch.empty(s2 + (32,), **bf),
+             "d2b": torch.empty(s2 + (32,), **bf), "d1a": torch.empty(s1 + (16,), **bf),
+             "d1b": torch.empty(s1 + (16,), **bf), "out": torch.empty(s1, dtype=torch.float32, device=self.device)}
+        if train:
+            B.update({"g_out": torch.empty(s1, dtype=torch.float32, device=self.device),
+                      "g_d1b": torch.empty(s1 + (16,), **bf), "g_d1a": torch.empty(s1 + (16,), **bf),
+                      "g_cat1": torch.empty(s1 + (48,), **bf), "g_d2b": torch.empty(s2 + (32,), **bf),
+                      "g_d2a": torch.empty(s2 + (32,), **bf), "g_cat2": torch.empty(s2 + (96,), **bf),
+                      "g_e3b": torch.empty(s3 + (64,), **bf), "g_e3a": torch.empty(s3 + (64,), **bf),
+                      "g_p2": torch.empty(s3 + (32,), **bf), "g_e2a": torch.empty(s2 + (32,), **bf),
+                      "g_p1": torch.empty(s2 + (16,), **bf), "g_e1a": torch.empty(s1 + (16,), **bf)})
+        self._bufs[key] = B
+        return B
+
+    # kernels ----------------------------------------------------------------
+    def _conv(self, name, x, xcs, xoff, y, ycs, yoff, dims, relu=True):
+        _, _, cin, cout = self.off[name]
+        n, d, h, w = dims
+        check(_lib.load().cnn_conv3d_forward(_p(x), xcs, xoff, _p(self.w16(name)), _p(self.bias(name)),
+                                             _p(y), ycs, yoff, 0, n, d, h, w, cin, cout, int(relu),
+                                             _stream()))
+
+    def _conv_bwd(self, name, x, xcs, xoff, g, gcs, goff, dx, dxcs, dxoff, dims):
+        _, _, cin, cout = self.off[name]
+        n, d, h, w = dims
+        lib = _lib.load()
+        check(lib.cnn_conv3d_wgrad(_p(x), xcs, xoff, _p(g), gcs, goff, _p(self.gw(name)), _p(self.gb(name)),
+                                   n, d, h, w, cin, cout, _stream()))
+        if dx is not None:
+            check(lib.cnn_conv3d_dgrad(_p(g), gcs, goff, _p(self.w16(name)), _p(self.wt), _p(dx), dxcs, dxoff,
+                                       n, d, h, w, cin, cout, _stream()))
+
+    def _relu_bwd(self, g, gcs, goff, y, ycs, yoff, nvox, c):
+        check(_lib.load().cnn_relu_backward(_p(g), gcs, goff, _p(y), ycs, yoff, nvox, c, _stream()))
+
+    def forward(self, x: torch.Tensor, train: bool = False) -> torch.Tensor:
+        """x: FP32 [N, D, H, W] (or [D, H, W]); returns x + net(x) (FP32)."""
+        squeeze = x.dim() == 3
+        if squeeze:
+            x = x.unsqueeze(0)
+        x = x.contiguous()
+        n, d, h, w = x.shape
+        B = self._buffers((n, d, h, w), train)
+        self._x = x
+        lib = _lib.load()
+        st = _stream()
+        l1, l2, l3 = (n, d, h, w), (n, d // 2, h // 2, w // 2), (n, d // 4, h // 4, w // 4)
+        check(lib.cnn_pack_input(_p(x), _p(B["x0"]), 16, n * d * h * w, st))
+        self._conv("e1a", B["x0"], 16, 0, B["e1a"], 16, 0, l1)
+        self._conv("e1b", B["e1a"], 16, 0, B["cat1"], 48, 32, l1)
+        check(lib.cnn_maxpool2_forward(_p(B["cat1"]), 48, 32, _p(B["p1"]), n, d, h, w, 16, st))
+        self._conv("e2a", B["p1"], 16, 0, B["e2a"], 32, 0, l2)
+        self._conv("e2b", B["e2a"], 32, 0, B["cat2"], 96, 64, l2)
+        check(lib.cnn_maxpool2_forward(_p(B["cat2"]), 96, 64, _p(B["p2"]), *l2, 32, st))
+        self._conv("e3a", B["p2"], 32, 0, B["e3a"], 64, 0, l3)
+        self._conv("e3b", B["e3a"], 64, 0, B["e3b"], 64, 0, l3)
+        check(lib.cnn_upsample2_forward(_p(B["e3b"]), _p(B["cat2"]), 96, 0, *l3, 64, st))
+        self._conv("d2a", B["cat2"], 96, 0, B["d2a"], 32, 0, l2)
+        self._conv("d2b", B["d2a"], 32, 0, B["d2b"], 32, 0, l2)
+        check(lib.cnn_upsample2_forward(_p(B["d2b"]), _p(B["cat1"]), 48, 0, *l2, 32, st))
+        self._conv("d1a", B["cat1"], 48, 0, B["d1a"], 16, 0, l1)
+        self._conv("d1b", B["d1a"], 16, 0, B["d1b"], 16, 0, l1)
+        hb = self.params[self.head_off + 27 * HEAD_CIN:self.head_off + 27 * HEAD_CIN + 1]
+        check(lib.cnn_head_forward(_p(B["d1b"]), 16, _p(self.head_w()), _p(hb), _p(x),
+                                   _p(B["out"]), n, d, h, w, HEAD_CIN, st))
+        out = B["out"]
+        return out[0] if squeeze else out
+
+    def backward(self, g_out: torch.Tensor):
+        """Accumulate parameter gradients for dL/d(out) = g_out (FP32, shape of out)."""
+        x = self._x
+        n, d, h, w = x.shape
+        B = self._buffers((n, d, h, w), True)
+        lib = _lib.load()
+        st = _stream()
+        l1, l2, l3 = (n, d, h, w), (n, d // 2, h // 2, w // 2), (n, d // 4, h // 4, w // 4)
+        v1, v2, v3 = n * d * h * w, n * d * h * w // 8, n * d * h * w // 64
+        hw = self.head_w()
+        gw_head = self.grads[self.head_off:self.head_off + 27 * HEAD_CIN]
+        gb_head = self.grads[self.head_off + 27 * HEAD_CIN:self.head_off + 27 * HEAD_CIN + 1]
+        check(lib.cnn_head_backward(_p(B["d1b"]), 16, _p(hw), _p(g_out.contiguous()), _p(B["g_d1b"]), 16,
+                                    _p(gw_head), _p(gb_head), n, d, h, w, HEAD_CIN, st))
+        self._relu_bwd(B["g_d1b"], 16, 0, B["d1b"], 16, 0, v1, 16)
+        self._conv_bwd("d1b", B["d1a"], 16, 0, B["g_d1b"], 16, 0, B["g_d1a"], 16, 0, l1)
+        self._relu_bwd(B["g_d1a"], 16, 0, B["d1a"], 16, 0, v1, 16)
+        self._conv_bwd("d1a", B["cat1"], 48, 0, B["g_d1a"], 16, 0, B["g_cat1"], 48, 0, l1)
+        check(lib.cnn_upsample2_backward(_p(B["g_cat1"]), 48, 0, _p(B["g_d2b"]), *l2, 32, st))
+        self._relu_bwd(B["g_d2b"], 32, 0, B["d2b"], 32, 0, v2, 32)
+        self._conv_bwd("d2b", B["d2a"], 32, 0, B["g_d2b"], 32, 0, B["g_d2a"], 32, 0, l2)
+        self._relu_bwd(B["g_d2a"], 32, 0, B["d2a"], 32, 0, v2, 32)
+        self._conv_bwd("d2a", B["cat2"], 96, 0, B["g_d2a"], 32, 0, B["g_cat2"], 96, 0, l2)
+        check(lib.cnn_upsample2_backward(_p(B["g_cat2"]), 96, 0, _p(B["g_e3b"]), *l3, 64, st))
+        self._relu_bwd(B["g_e3b"], 64, 0, B["e3b"], 64, 0, v3, 64)
+        self._conv_bwd("e3b", B["e3a"], 64, 0, B["g_e3b"], 64, 0, B["g_e3a"], 64, 0, l3)
+        self._relu_bwd(B["g_e3a"], 64, 0, B["e3a"], 64, 0, v3, 64)
+        self._conv_bwd("e3a", B["p2"], 32, 0, B["g_e3a"], 64, 0, B["g_p2"], 32, 0, l3)
+        # pooled branch's gradient added to the skip gradient of e2b (cat2[..., 64:96])
+        check(lib.cnn_maxpool2_backward(_p(B["cat2"]), 96, 64, _p(B["g_p2"]), _p(B["g_cat2"]), 96, 64,
+                                        *l2, 32, st))
+        self._relu_bwd(B["g_cat2"], 96, 64, B["cat2"], 96, 64, v2, 32)
+        self._conv_bwd("e2b", B["e2a"], 32, 0, B["g_cat2"], 96, 64, B["g_e2a"], 32, 0, l2)
+        self._relu_bwd(B["g_e2a"], 32, 0, B["e2a"], 32, 0, v2, 32)
+        self._conv_bwd("e2a", B["p1"], 16, 0, B["g_e2a"], 32, 0, B["g_p1"], 16, 0, l2)
+        check(lib.cnn_maxpool2_backward(_p(B["cat1"]), 48, 32, _p(B["g_p1"]), _p(B["g_cat1"]), 48, 32,
+                                        *l1, 16, st))
+        self._relu_bwd(B["g_cat1"], 48, 32, B["cat1"], 48, 32, v1, 16)
+        self._conv_bwd("e1b", B["e1a"], 16, 0, B["g_cat1"], 48, 32, B["g_e1a"], 16, 0, l1)
+        self._relu_bwd(B["g_e1a"], 16, 0, B["e1a"], 16, 0, v1, 16)
+        self._conv_bwd("e1a", B["x0"], 16, 0, B["g_e1a"], 16, 0, None, 0, 0, l1)
+
+    def adam_step(self, lr: float = 1e-3, b1: float = 0.9, b2: float = 0.999, eps: float = 1e-8):
+        self.t += 1
+        check(_lib.load().cnn_adam(_p(self.params), _p(self.grads), _p(self.m), _p(self.v), _p(self.params16),
+                                   self.n_params, ctypes.c_float(lr), ctypes.c_float(b1), ctypes.c_float(b2),
+                                   ctypes.c_float(eps), self.t, _stream()))
+
+    def train_step(self, x: torch.Tensor, target: torch.Tensor, lr: float = 1e-3) -> float:
+        """One forward, MSE loss, backward and Adam step; returns the loss."""
+        out = self.forward(x, train=True)
+        if x.dim() == 3:
+            out = out.unsqueeze(0)
+            target = target.unsqueeze(0)
+        B = self._buffers(tuple(out.shape), True)
+        self.loss_buf.zero_()
+        check(_lib.load().cnn_mse(_p(out), _p(target.contiguous()), _p(B["g_out"]), _p(self.loss_buf),
+                                  out.numel(), _stream()))
+        self.backward(B["g_out"])
+        self.adam_step(lr)
+        return float(self.loss_buf.item()) / out.numel()
+
+
+__all__ = ["UNet", "LAYERS", "conv_flops"]

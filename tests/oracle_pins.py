@@ -22,6 +22,9 @@ What pins what:
   fdk_sphere              FDK of a unit-density sphere in the central slices
   fdk_offcentre           FDK of an off-centre sphere lands at its true centre
   fdk_ellipsoids          FDK of the 10-ellipsoid phantom in the central slices
+  conv_vs_scipy           3x3x3 convolution vs scipy.ndimage.correlate per channel pair
+  conv_adjoints           <conv(x), dy> = <x, dgrad(dy)> and the weight gradient as the
+                          derivative of that pairing in w (linearity check)
 """
 import numpy as np
 
@@ -369,6 +372,41 @@ def fdk_ellipsoids():
         assert err.mean() < 0.06 and err.max() < 0.30, (err.mean(), err.max())
 
 
+def conv_vs_scipy():
+    ndimage = __import__("scipy.ndimage", fromlist=["correlate"])
+    rng = np.random.default_rng(12)
+    N, D, H, W, cin, cout = 2, 5, 6, 7, 3, 4
+    x = rng.normal(size=(N, D, H, W, cin))
+    w = rng.normal(size=(cout, 27, cin))
+    b = rng.normal(size=cout)
+    y = oracle.conv3d(x, w, b)
+    for n in range(N):
+        for co in range(cout):
+            ref = np.full((D, H, W), b[co])
+            for ci in range(cin):
+                ref += ndimage.correlate(x[n, ..., ci], w[co, :, ci].reshape(3, 3, 3), mode="constant", cval=0.0)
+            assert np.max(np.abs(y[n, ..., co] - ref)) < 1e-10
+
+
+def conv_adjoints():
+    rng = np.random.default_rng(13)
+    N, D, H, W, cin, cout = 1, 6, 5, 7, 5, 3
+    x = rng.normal(size=(N, D, H, W, cin))
+    w = rng.normal(size=(cout, 27, cin))
+    dy = rng.normal(size=(N, D, H, W, cout))
+    y = oracle.conv3d(x, w)
+    dx = oracle.conv3d_dgrad(dy, w)
+    assert abs(np.vdot(y, dy) - np.vdot(x, dx)) < 1e-9 * np.linalg.norm(y) * np.linalg.norm(dy)
+    dw, db = oracle.conv3d_wgrad(x, dy)
+    # <conv_w(x), dy> is linear in w with gradient dw: check on random directions
+    for seed in range(3):
+        w2 = np.random.default_rng(100 + seed).normal(size=w.shape)
+        assert abs(np.vdot(oracle.conv3d(x, w2), dy) - np.vdot(w2, dw)) < 1e-9 * np.abs(dw).sum() * 10
+    b2 = rng.normal(size=cout)
+    lhs = np.vdot(oracle.conv3d(x, 0 * w, b2), dy)
+    assert abs(lhs - np.vdot(b2, db)) < 1e-9 * max(1.0, abs(lhs))
+
+
 ALL = [matrix_vs_ray, z_invariance, bp_constant, bp_linear, bp_fp_hat_matrix, adjoint_dot,
        symmetry, filter_impulse, filter_frequency, phantom_sphere, phantom_ray_integral,
-       phantom_siddon, fdk_sphere, fdk_offcentre, fdk_ellipsoids]
+       phantom_siddon, fdk_sphere, fdk_offcentre, fdk_ellipsoids, conv_vs_scipy, conv_adjoints]

@@ -1,0 +1,218 @@
+"""Tensor-core convolution kernels vs the FP64 oracle (inputs pre-rounded to
+BF16 so both sides see the same values; FP32 outputs within 1e-4 of the
+maximum, BF16 outputs within BF16 rounding), the element-wise kernels vs
+numpy, and the learned few-view correction end to end on a small scan."""
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2104_13248_gb300 import _lib, inputs, learned
+from paper_2104_13248_gb300.unet import UNet
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def P(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def S():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def bf16_round(a):
+    return torch.from_numpy(np.asarray(a, np.float32)).to(torch.bfloat16).float().numpy().astype(np.float64)
+
+
+def rel(a, b):
+    return float(np.abs(np.asarray(a, np.float64) - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+SHAPES = [(1, 8, 8, 16, 16, 16), (2, 6, 9, 13, 32, 64), (1, 12, 10, 9, 48, 16), (1, 4, 4, 20, 96, 32),
+          (1, 16, 16, 16, 64, 64)]
+
+
+@pytest.mark.parametrize("shape", SHAPES, ids=lambda s: "n%d_%dx%dx%d_ci%d_co%d" % s)
+def test_conv_forward_dgrad_wgrad(shape):
+    n, d, h, w, cin, cout = shape
+    rng = np.random.default_rng(sum(shape))
+    x = bf16_round(rng.normal(size=(n, d, h, w, cin)))
+    wt = bf16_round(rng.normal(size=(cout, 27, cin)) * 0.1)
+    b = rng.normal(size=cout).astype(np.float32)
+    dy = bf16_round(rng.normal(size=(n, d, h, w, cout)))
+    xd = torch.from_numpy(x.astype(np.float32)).cuda().to(torch.bfloat16)
+    wd = torch.from_numpy(wt.astype(np.float32)).cuda().to(torch.bfloat16)
+    bd = torch.from_numpy(b).cuda()
+    dyd = torch.from_numpy(dy.astype(np.float32)).cuda().to(torch.bfloat16)
+    lib = _lib.load()
+    # forward, FP32 output, bias, no ReLU
+    y32 = torch.empty((n, d, h, w, cout), dtype=torch.float32, device="cuda")
+    _lib.check(lib.cnn_conv3d_forward(P(xd), cin, 0, P(wd), P(bd), P(y32), cout, 0, 1, n, d, h, w, cin, cout, 0, S()))
+    ref = oracle.conv3d(x, wt, b)
+    assert rel(y32.cpu().numpy(), ref) <= 1e-4
+    # forward, BF16 output with ReLU, written into a channel slice of a wider tensor
+    ybig = torch.zeros((n, d, h, w, cout + 16), dtype=torch.bfloat16, device="cuda")
+    _lib.check(lib.cnn_conv3d_forward(P(xd), cin, 0, P(wd), P(bd), P(ybig), cout + 16, 16, 0, n, d, h, w, cin,
+                                      cout, 1, S()))
+    yb = ybig.float().cpu().numpy()
+    assert rel(yb[..., 16:], np.maximum(ref, 0)) <= 8e-3
+    assert np.all(yb[..., :16] == 0)
+    # input gradient (BF16 out)
+    dx = torch.empty((n, d, h, w, cin), dtype=torch.bfloat16, device="cuda")
+    scratch = torch.empty(27 * cin * cout, dtype=torch.bfloat16, device="cuda")
+    _lib.check(lib.cnn_conv3d_dgrad(P(dyd), cout, 0, P(wd), P(scratch), P(dx), cin, 0, n, d, h, w, cin, cout, S()))
+    dref = oracle.conv3d_dgrad(dy, wt)
+    assert rel(dx.float().cpu().numpy(), dref) <= 8e-3
+    # the same input gradient at FP32 through the forward kernel and the flipped weights
+    if cin in (16, 32, 64):
+        dx32 = torch.empty((n, d, h, w, cin), dtype=torch.float32, device="cuda")
+        _lib.check(lib.cnn_conv3d_forward(P(dyd), cout, 0, P(scratch), None, P(dx32), cin, 0, 1, n, d, h, w, cout,
+                                          cin, 0, S()))
+        assert rel(dx32.cpu().numpy(), dref) <= 1e-4
+    # weight and bias gradients (FP32, accumulated onto the initial values)
+    dw = torch.full((cout, 27, cin), 0.5, dtype=torch.float32, device="cuda")
+    db = torch.full((cout,), -0.25, dtype=torch.float32, device="cuda")
+    _lib.check(lib.cnn_conv3d_wgrad(P(xd), cin, 0, P(dyd), cout, 0, P(dw), P(db), n, d, h, w, cin, cout, S()))
+    wref, bref = oracle.conv3d_wgrad(x, dy)
+    assert rel(dw.cpu().numpy() - 0.5, wref) <= 1e-4
+    assert rel(db.cpu().numpy() + 0.25, bref) <= 1e-4
+
+
+def test_pool_upsample_relu():
+    rng = np.random.default_rng(5)
+    n, d, h, w, c = 2, 6, 4, 8, 16
+    x = bf16_round(rng.normal(size=(n, d, h, w, c + 16)))
+    xd = torch.from_numpy(x.astype(np.float32)).cuda().to(torch.bfloat16)
+    lib = _lib.load()
+    y = torch.empty((n, d // 2, h // 2, w // 2, c), dtype=torch.bfloat16, device="cuda")
+    _lib.check(lib.cnn_maxpool2_forward(P(xd), c + 16, 16, P(y), n, d, h, w, c, S()))
+    xs = x[..., 16:].reshape(n, d // 2, 2, h // 2, 2, w // 2, 2, c)
+    ref = xs.max(axis=(2, 4, 6))
+    assert np.array_equal(y.float().cpu().numpy(), ref)
+    # backward adds dy at the first arg-max of each window
+    dy = bf16_round(rng.normal(size=ref.shape))
+    dyd = torch.from_numpy(dy.astype(np.float32)).cuda().to(torch.bfloat16)
+    dx = torch.zeros((n, d, h, w, c + 16), dtype=torch.bfloat16, device="cuda")
+    _lib.check(lib.cnn_maxpool2_backward(P(xd), c + 16, 16, P(dyd), P(dx), c + 16, 16, n, d, h, w, c, S()))
+    got = dx.float().cpu().numpy()[..., 16:].reshape(xs.shape)
+    flat = xs.transpose(0, 1, 3, 5, 7, 2, 4, 6).reshape(n, d // 2, h // 2, w // 2, c, 8)
+    arg = flat.argmax(axis=-1)
+    exp = np.zeros_like(flat)
+    np.put_along_axis(exp, arg[..., None], dy[..., None], axis=-1)
+    exp = exp.reshape(n, d // 2, h // 2, w // 2, c, 2, 2, 2).transpose(0, 1, 5, 2, 6, 3, 7, 4)
+    assert np.array_equal(got, exp)
+    # upsample forward into a channel slice, backward sums the 8 children
+    up = torch.zeros((n, d * 2, h * 2, w * 2, c + 8), dtype=torch.bfloat16, device="cuda")
+    src = xd[..., 16:].contiguous()
+    _lib.check(lib.cnn_upsample2_forward(P(src), P(up), c + 8, 8, n, d, h, w, c, S()))
+    u = up.float().cpu().numpy()[..., 8:]
+    assert np.array_equal(u, x[..., 16:].repeat(2, 1).repeat(2, 2).repeat(2, 3))
+    gsum = torch.empty((n, d, h, w, c), dtype=torch.bfloat16, device="cuda")
+    _lib.check(lib.cnn_upsample2_backward(P(up), c + 8, 8, P(gsum), n, d, h, w, c, S()))
+    assert rel(gsum.float().cpu().numpy(), 8 * x[..., 16:]) <= 4e-3
+    # ReLU backward masks where y <= 0
+    g = torch.ones((n, d, h, w, c), dtype=torch.bfloat16, device="cuda")
+    _lib.check(lib.cnn_relu_backward(P(g), c, 0, P(xd), c + 16, 16, n * d * h * w, c, S()))
+    assert np.array_equal(g.float().cpu().numpy(), (x[..., 16:] > 0).astype(np.float32))
+
+
+def _torch_reference(net, x, flat):
+    """The same network in plain PyTorch FP32 on the CPU, parameters taken
+    from the flat vector ``flat`` (laid out like net.params)."""
+    import torch.nn.functional as F
+
+    def conv(name, t):
+        w0, b0, cin, cout = net.off[name]
+        wt = flat[w0:b0].reshape(cout, 3, 3, 3, cin).permute(0, 4, 1, 2, 3)
+        return F.relu(F.conv3d(t, wt, flat[b0:b0 + cout], padding=1))
+
+    t = x[None, None]
+    e1 = conv("e1b", conv("e1a", t))
+    e2 = conv("e2b", conv("e2a", F.max_pool3d(e1, 2)))
+    e3 = conv("e3b", conv("e3a", F.max_pool3d(e2, 2)))
+    d2 = conv("d2b", conv("d2a", torch.cat([F.interpolate(e3, scale_factor=2), e2], 1)))
+    d1 = conv("d1b", conv("d1a", torch.cat([F.interpolate(d2, scale_factor=2), e1], 1)))
+    h0 = net.head_off
+    hw = flat[h0:h0 + 27 * 16].reshape(1, 3, 3, 3, 16).permute(0, 4, 1, 2, 3)
+    return (F.conv3d(d1, hw, flat[h0 + 27 * 16:h0 + 27 * 16 + 1], padding=1) + t)[0, 0]
+
+
+def test_unet_forward_backward_against_plain_pytorch():
+    """Forward output and every layer's weight gradient vs autograd on a plain
+    FP32 PyTorch copy of the network (weights rounded to BF16 like the
+    kernels read them). The kernels keep activations and their gradients in
+    BF16, so the comparison allows BF16-level differences: outputs within
+    2e-2 of the maximum, gradients with cosine similarity above 0.99."""
+    net = UNet(seed=3)
+    with torch.no_grad():
+        net.params[net.head_off:net.head_off + 27 * 16] = torch.randn(27 * 16, device="cuda") * 0.05
+    x = torch.from_numpy(inputs.uniform_array(8, (16, 16, 24), 0, 1).astype(np.float32))
+    tgt = torch.from_numpy(inputs.uniform_array(9, (16, 16, 24), 0, 1).astype(np.float32))
+    out = net.forward(x.cuda(), train=True).cpu()
+    flat = net.params.cpu().clone()
+    flat[:net.n_conv] = net.params16[:net.n_conv].float().cpu()
+    for name, (_, b0, _, cout) in net.off.items():   # biases stay FP32 in the kernels
+        flat[b0:b0 + cout] = net.params[b0:b0 + cout].cpu()
+    flat.requires_grad_(True)
+    ref = _torch_reference(net, x, flat)
+    assert (out - ref).abs().max().item() <= 2e-2 * ref.abs().max().item()
+    g = (2 * (out - tgt) / out.numel()).contiguous()
+    net.backward(g.cuda())
+    loss = ((ref - tgt) ** 2).mean()
+    loss.backward()
+    gref = flat.grad
+    for name, cin, cout in [(k, v[2], v[3]) for k, v in net.off.items()]:
+        w0, b0, _, _ = net.off[name]
+        a, b = net.grads[w0:b0].cpu().double(), gref[w0:b0].double()
+        cos = float((a @ b) / (a.norm() * b.norm()))
+        assert cos > 0.99, (name, cos)
+        assert abs(a.norm() / b.norm() - 1) < 0.05, (name, float(a.norm() / b.norm()))
+    h0 = net.head_off
+    a, b = net.grads[h0:h0 + 27 * 16].cpu().double(), gref[h0:h0 + 27 * 16].double()
+    assert float((a @ b) / (a.norm() * b.norm())) > 0.999
+
+
+def test_training_reduces_loss_and_checkpoint_resume(tmp_path):
+    net = UNet(seed=1)
+    x = torch.from_numpy(inputs.uniform_array(1, (2, 16, 16, 16), 0, 1).astype(np.float32)).cuda()
+    t = (x * 0.5 + 0.1).contiguous()
+    losses = [net.train_step(x, t, lr=3e-3) for _ in range(60)]
+    assert np.mean(losses[-5:]) < 0.3 * np.mean(losses[:5])
+    # checkpoint / resume: the continued trajectory is identical
+    path = tmp_path / "ck.pt"
+    torch.save(net.state_dict(), path)
+    cont = [net.train_step(x, t, lr=3e-3) for _ in range(3)]
+    net2 = UNet(seed=99)
+    net2.load_state_dict(torch.load(path))
+    cont2 = [net2.train_step(x, t, lr=3e-3) for _ in range(3)]
+    np.testing.assert_allclose(cont, cont2, rtol=2e-3)
+
+
+def test_learned_few_view_gain_small():
+    """A small version of the few-view workload: 128^3 volumes, 90 -> 15 views.
+    The trained network must cut the few-view RMSE (vs the full-view FDK) on
+    held-out seeds well below the plain few-view FDK's."""
+    g = inputs.scaled_geom(inputs.preset("c5_learned")["geom"], np=90, nu=256, nv=256, du=0.8, dv=0.8,
+                           nx=64, ny=64, nz=64, sx=1.0, sy=1.0, sz=1.0)
+    maker = learned.PairMaker(g, stride=6, n_ell=20, axes=(3.0, 25.0))
+    rng = np.random.default_rng(0)
+    xs, ts = learned.make_training_set(maker, range(2000, 2016), 32, 4, rng)
+    net = UNet(seed=0)
+    learned.train(net, xs, ts, steps=400, lr=2e-3, batch=2)
+    mask = learned.fov_mask(g)
+    r_few, r_net = learned.evaluate(net, maker, range(9000, 9004), mask)
+    print(f"few-view RMSE {r_few:.4f}, with network {r_net:.4f}")
+    assert r_net < 0.85 * r_few
+    # fallback: without a network the full-view path is used
+    api_vol = learned.reconstruct(maker, maker.raw, None)
+    assert api_vol.shape == (g["nz"], g["ny"], g["nx"])
+    maker.close()

@@ -42,6 +42,11 @@ MUTANTS = [
     ("phantom_rotation_transposed",
      "pb[a] = (R[0 * 3 + a] * p[0] + R[1 * 3 + a] * p[1] + R[2 * 3 + a] * p[2]) / E[3 + a];\n                    db[a] = (R[0 * 3 + a] * dir[0] + R[1 * 3 + a] * dir[1] + R[2 * 3 + a] * dir[2]) / E[3 + a];",
      "pb[a] = (R[a * 3 + 0] * p[0] + R[a * 3 + 1] * p[1] + R[a * 3 + 2] * p[2]) / E[3 + a];\n                    db[a] = (R[a * 3 + 0] * dir[0] + R[a * 3 + 1] * dir[1] + R[a * 3 + 2] * dir[2]) / E[3 + a];"),
+    ("conv_tap_sign", "int zi = z + t / 9 - 1, yi = yy + (t / 3) % 3 - 1, xi = xx + t % 3 - 1;\n                            if (zi < 0 || zi >= D || yi < 0 || yi >= H || xi < 0 || xi >= W) continue;\n                            const double *xp",
+     "int zi = z - t / 9 + 1, yi = yy + (t / 3) % 3 - 1, xi = xx + t % 3 - 1;\n                            if (zi < 0 || zi >= D || yi < 0 || yi >= H || xi < 0 || xi >= W) continue;\n                            const double *xp"),
+    ("conv_no_bias", "double acc = b ? b[co] : 0.0;", "double acc = 0.0;"),
+    ("conv_dgrad_transposed_w", "acc += w[((long)co * 27 + t) * cin + ci] * gp[co];", "acc += w[((long)co * 27 + (26 - t)) * cin + ci] * gp[co];"),
+    ("conv_wgrad_bias_sum", "for (long v = 0; v < (long)N * D * H * W; ++v) bsum += dy[v * cout + co];", "for (long v = 1; v < (long)N * D * H * W; ++v) bsum += dy[v * cout + co];"),
     ("phantom_chord_half", "if (disc > 0.0) sum += E[15] * sqrt(disc) / A * L;", "if (disc > 0.0) sum += E[15] * sqrt(disc) / (2.0 * A) * L;"),
 ]
 
