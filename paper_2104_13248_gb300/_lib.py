@@ -66,7 +66,7 @@ PROTOTYPES = {
     "cnn_head_forward": (_i, [_vp, _i, _vp, _vp, _vp, _vp, _i, _i, _i, _i, _i, _vp]),
     "cnn_head_backward": (_i, [_vp, _i, _vp, _vp, _vp, _i, _vp, _vp, _i, _i, _i, _i, _i, _vp]),
     "cnn_maxpool2_forward": (_i, [_vp, _i, _i, _vp, _i, _i, _i, _i, _i, _vp]),
-    "cnn_maxpool2_backward": (_i, [_vp, _i, _i, _vp, _vp, _i, _i, _i, _i, _i, _i, _i, _i, _vp]),
+    "cnn_maxpool2_backward": (_i, [_vp, _i, _i, _vp, _vp, _i, _i, _i, _i, _i, _i, _i, _vp]),
     "cnn_upsample2_forward": (_i, [_vp, _vp, _i, _i, _i, _i, _i, _i, _i, _vp]),
     "cnn_upsample2_backward": (_i, [_vp, _i, _i, _vp, _i, _i, _i, _i, _i, _vp]),
     "cnn_relu_backward": (_i, [_vp, _i, _i, _vp, _i, _i, _ll, _i, _vp]),
