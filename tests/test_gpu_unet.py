@@ -136,7 +136,8 @@ def _torch_reference(net, x, flat):
         return F.relu(F.conv3d(t, wt, flat[b0:b0 + cout], padding=1))
 
     t = x[None, None]
-    e1 = conv("e1b", conv("e1a", t))
+    t16 = torch.cat([t, torch.zeros((1, 15) + tuple(x.shape))], 1)   # input channel padded to 16
+    e1 = conv("e1b", conv("e1a", t16))
     e2 = conv("e2b", conv("e2a", F.max_pool3d(e1, 2)))
     e3 = conv("e3b", conv("e3a", F.max_pool3d(e2, 2)))
     d2 = conv("d2b", conv("d2a", torch.cat([F.interpolate(e3, scale_factor=2), e2], 1)))
