@@ -46,6 +46,31 @@ bp_status cnn_conv3d_dgrad(const void *dy, int dy_cstride, int dy_coff, const vo
                            void *dx, int dx_cstride, int dx_coff, int n, int d, int h, int wd,
                            int cin, int cout, void *stream);
 
+/* The input gradient of cnn_conv3d_dgrad for callers that cannot allocate
+ * device memory: code running while a CUDA graph is being captured, where a
+ * cudaMalloc would break the capture; a serving loop or an external runtime
+ * that owns every allocation on the device and hands this library only the
+ * tensors; or a process whose device memory is already fully reserved by a
+ * pooling allocator. This call takes no weight buffer and allocates nothing
+ * (no cudaMalloc, no cudaFree, no allocating library routine): the flipped,
+ * transposed weights go to a static device array of the library, reserved
+ * on every GPU that loads it until the process exits.
+ *   Limit: 27 * cin * cout <= 442368 BF16 values (cin * cout <= 16384, e.g.
+ *   128 x 128); larger layers get BP_ERR_INVALID_ARG and must use
+ *   cnn_conv3d_dgrad.
+ *   The first call on a device looks up the array's device address
+ *   (cudaGetSymbolAddress) and caches it; make that first call before any
+ *   stream capture on that device.
+ *   All calls share the one array. Each call overwrites every value it
+ *   later reads, so what an earlier call left there is never used, but two
+ *   calls whose work overlaps on the GPU (different streams without
+ *   ordering) race on it.
+ * There is no counterpart in the paper. Other arguments and the result are
+ * those of cnn_conv3d_dgrad. */
+bp_status cnn_conv3d_dgrad_noalloc(const void *dy, int dy_cstride, int dy_coff, const void *w,
+                                   void *dx, int dx_cstride, int dx_coff, int n, int d, int h,
+                                   int wd, int cin, int cout, void *stream);
+
 /* Weight and bias gradients: dw[co][tap][ci] += sum_v dy[v][co] x[v + tap][ci],
  * db[co] += sum_v dy[v][co] (db may be NULL). x and dy BF16. */
 bp_status cnn_conv3d_wgrad(const void *x, int x_cstride, int x_coff, const void *dy,

@@ -21,6 +21,8 @@
 
 #include <cuda_bf16.h>
 
+#include <mutex>
+
 #include "../../include/unet.h"
 
 namespace bp {
@@ -581,6 +583,38 @@ static bp_status conv_fwd(const bf16 *x, int xcs, int xco, const bf16 *w, const 
 
 static bool conv_args_ok(int cs, int coff, int c) { return cs % 8 == 0 && coff % 8 == 0 && coff + c <= cs; }
 
+// Scratch of cnn_conv3d_dgrad_noalloc: the flipped, transposed weights live
+// in this fixed device array instead of a caller buffer. 27 * 128 * 128 BF16
+// values (864 KiB), reserved on every GPU that loads the library until the
+// process exits. Host code must not pass the name itself to a kernel (on the
+// host it only stands for the symbol); the device address comes from
+// cudaGetSymbolAddress, looked up once per device and cached.
+constexpr long long kNoAllocScratchElems = 27LL * 128 * 128;
+static __device__ __align__(256) bf16 g_dgrad_scratch[kNoAllocScratchElems];
+
+constexpr int kMaxDevices = 64;
+static std::mutex g_scratch_mu;
+static void *g_scratch_addr[kMaxDevices] = {};
+
+static bp_status dgrad_scratch_address(void **out) {
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "cnn_conv3d_dgrad_noalloc: cudaGetDevice");
+    if (dev < 0 || dev >= kMaxDevices)
+        return fail(nullptr, BP_ERR_UNSUPPORTED, "cnn_conv3d_dgrad_noalloc: device index out of range");
+    std::lock_guard<std::mutex> lock(g_scratch_mu);
+    if (!g_scratch_addr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_dgrad_scratch);
+        if (e != cudaSuccess || !p)
+            return cuda_fail(nullptr, e != cudaSuccess ? e : cudaErrorInvalidSymbol,
+                             "cnn_conv3d_dgrad_noalloc: cudaGetSymbolAddress");
+        g_scratch_addr[dev] = p;
+    }
+    *out = g_scratch_addr[dev];
+    return BP_OK;
+}
+
 }  // namespace bp
 
 using namespace bp;
@@ -612,6 +646,40 @@ bp_status cnn_conv3d_dgrad(const void *dy, int dy_cstride, int dy_coff, const vo
     // dx = conv(dy, wt) with cin' = cout, cout' = cin, no bias, no activation;
     // the input-gradient channels go in blocks of 64, 32 or 16 (the tile
     // widths the tensor-core kernel is built for)
+    for (int ci0 = 0; ci0 < cin;) {
+        const int left = cin - ci0;
+        const int blk = left >= 64 ? 64 : (left >= 32 ? 32 : 16);
+        s = conv_fwd((const bf16 *)dy, dy_cstride, dy_coff, (const bf16 *)wt + (size_t)ci0 * 27 * cout,
+                     nullptr, dx, dx_cstride, dx_coff + ci0, 0, n, d, h, wd, cout, blk, 0, st);
+        if (s != BP_OK) return s;
+        ci0 += blk;
+    }
+    return BP_OK;
+}
+
+// Same result as cnn_conv3d_dgrad without the caller's weight buffer: for
+// callers that cannot allocate device memory (see unet.h). Allocates
+// nothing; the scratch is the library's static array above.
+bp_status cnn_conv3d_dgrad_noalloc(const void *dy, int dy_cstride, int dy_coff, const void *w,
+                                   void *dx, int dx_cstride, int dx_coff, int n, int d, int h,
+                                   int wd, int cin, int cout, void *stream) {
+    if (!dy || !w || !dx || cin < 16 || cin % 16 || cout % 16 ||
+        !conv_args_ok(dy_cstride, dy_coff, cout) || !conv_args_ok(dx_cstride, dx_coff, cin) ||
+        !al16(dy) || !al16(w) || !al16(dx))
+        return fail(nullptr, BP_ERR_INVALID_ARG, "cnn_conv3d_dgrad_noalloc: bad arguments");
+    if (27LL * cin * cout > kNoAllocScratchElems)
+        return fail(nullptr, BP_ERR_INVALID_ARG,
+                    "cnn_conv3d_dgrad_noalloc: cin * cout exceeds the static scratch limit of 16384 "
+                    "(27 * cin * cout BF16 values must fit 442368); use cnn_conv3d_dgrad");
+    void *wt = nullptr;
+    bp_status s = dgrad_scratch_address(&wt);
+    if (s != BP_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    // every element of the scratch that the convolution reads is written
+    // here first, so nothing left by an earlier call is ever used
+    flip_transpose_kernel<<<ew_blocks(27LL * cin * cout), 256, 0, st>>>((const bf16 *)w, (bf16 *)wt, cin, cout);
+    s = launch_ok("flip_transpose_kernel");
+    if (s != BP_OK) return s;
     for (int ci0 = 0; ci0 < cin;) {
         const int left = cin - ci0;
         const int blk = left >= 64 ? 64 : (left >= 32 ? 32 : 16);

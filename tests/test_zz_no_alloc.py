@@ -1,0 +1,69 @@
+"""The allocation-free input-gradient entry point (cnn_conv3d_dgrad_noalloc).
+
+Some callers cannot allocate device memory: code inside a CUDA graph
+capture, a runtime that owns every allocation and passes only tensors, or a
+process whose memory a pooling allocator has already reserved. This entry
+point keeps its scratch in a static device array instead of a caller buffer;
+here it must give the same input gradient as cnn_conv3d_dgrad (which takes a
+caller buffer) on two different calls in a row, and refuse a layer too large
+for its array. The file sorts last so that a run stopping at the first
+failure has already run every other test.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+from paper_2104_13248_gb300 import _lib
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def _p(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _s():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _case(seed, n, d, h, w, cin, cout):
+    g = torch.Generator(device="cuda").manual_seed(seed)
+    dy = torch.randn((n, d, h, w, cout), generator=g, device="cuda").to(torch.bfloat16)
+    wt = (0.1 * torch.randn((cout, 27, cin), generator=g, device="cuda")).to(torch.bfloat16)
+    return dy, wt
+
+
+def test_noalloc_dgrad_matches_buffered_dgrad_twice():
+    lib = _lib.load()
+    # two calls in a row with different layers: the static scratch is reused
+    for seed, (n, d, h, w, cin, cout) in enumerate([(1, 8, 12, 16, 48, 32), (2, 6, 8, 20, 32, 64)]):
+        dy, wt = _case(100 + seed, n, d, h, w, cin, cout)
+        ref = torch.empty((n, d, h, w, cin), dtype=torch.bfloat16, device="cuda")
+        buf = torch.empty(27 * cin * cout, dtype=torch.bfloat16, device="cuda")
+        _lib.check(lib.cnn_conv3d_dgrad(_p(dy), cout, 0, _p(wt), _p(buf), _p(ref), cin, 0, n, d, h, w, cin,
+                                        cout, _s()))
+        out = torch.full((n, d, h, w, cin), 7.0, dtype=torch.bfloat16, device="cuda")
+        _lib.check(lib.cnn_conv3d_dgrad_noalloc(_p(dy), cout, 0, _p(wt), _p(out), cin, 0, n, d, h, w, cin,
+                                                cout, _s()))
+        torch.cuda.synchronize()
+        a, b = out.float(), ref.float()
+        # same kernels, same weights: within the BF16 tolerance of the conv tests (here equal)
+        assert (a - b).abs().max().item() <= 8e-3 * b.abs().max().item()
+
+
+def test_noalloc_dgrad_rejects_layers_beyond_the_limit():
+    lib = _lib.load()
+    dy = torch.zeros((1, 4, 4, 16, 160), dtype=torch.bfloat16, device="cuda")
+    wt = torch.zeros((160, 27, 128), dtype=torch.bfloat16, device="cuda")
+    dx = torch.zeros((1, 4, 4, 16, 128), dtype=torch.bfloat16, device="cuda")
+    st = lib.cnn_conv3d_dgrad_noalloc(_p(dy), 160, 0, _p(wt), _p(dx), 128, 0, 1, 4, 4, 16, 128, 160, _s())
+    assert st == _lib.BP_ERR_INVALID_ARG
+    assert b"limit" in lib.bp_last_error(None)
