@@ -44,6 +44,15 @@ def parse_args(argv=None):
     return ap.parse_args(argv)
 
 
+def backprojector_source_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("paper_2104_13248_gb300/csrc/k_backproject.cu", "paper_2104_13248_gb300/csrc/geom_dev.cuh"):
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -266,9 +275,12 @@ def run_ours(args):
     achieved = U / (bp_ms_max * 1e-3) / 1e9
     traffic = None
     tp = os.path.join(ROOT, "profiles", "bp_zcol_tma_c3_traffic.json")
-    if os.path.exists(tp):
+    if os.path.exists(tp) and args.workload == "c3_paper" and not args.views:
         try:
-            traffic = json.load(open(tp)).get("dram_bytes_per_launch")
+            rec = json.load(open(tp))
+            # counters only count while the kernel source is the one they were taken on
+            if rec.get("source_sha256_16") == backprojector_source_hash():
+                traffic = rec.get("dram_bytes_per_launch")
         except Exception:
             traffic = None
 
