@@ -39,6 +39,9 @@ def parse_args(argv=None):
     ap.add_argument("--tk", type=int, default=0, help="voxels per thread along z (32/64; 0 = plan)")
     ap.add_argument("--ctas", type=int, default=2, help="CTAs per SM the TK=32 back-projector targets")
     ap.add_argument("--views", type=int, default=0, help="override the number of views (profiling runs)")
+    ap.add_argument("--op", choices=["fdk", "fp", "ls"], default="fdk",
+                    help="fdk: filter + back-projection (the benchmark); fp: matched forward projection "
+                         "of the workload's volume(s); ls: least-squares iterations (differentiable workload)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args(argv)
@@ -183,6 +186,55 @@ def run_reference(args):
                              "sample": sample},
             "e2e": {"value": val, "unit": "GUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def run_op(args):
+    """Secondary measurements (forward projector, least squares) in the same JSON form."""
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2104_13248_gb300 import api, autograd, inputs
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    p = inputs.preset(args.workload)
+    g = p["geom"]
+    if args.views:
+        g = inputs.scaled_geom(g, np=args.views)
+    batch = p.get("batch", 1)
+    ctx = api.bp_create(g)
+    U = float(g["nx"]) * g["ny"] * g["nz"] * g["np"] * batch
+    raws = torch.stack([api.bp_phantom_project(ctx, inputs.random_ellipsoids(p["seed"] + b, p["n_ell"], p["axes"], g))
+                        for b in range(batch)])
+    gen = torch.Generator(device="cuda").manual_seed(0)
+    x = torch.rand((batch,) + ctx.vol_shape(), device="cuda", generator=gen)
+    proj = torch.empty_like(raws)
+    if args.op == "fp":
+        def step():
+            api.fp_project(ctx, x, proj=proj)
+        upd, unit_desc = U, "forward-projection"
+    else:
+        L = autograd.lipschitz(ctx, iters=5)
+
+        def step():
+            autograd.least_squares(ctx, raws, iters=1, x0=x, L=L)
+        upd, unit_desc = 2 * U, "least-squares iteration (one forward + one back-projection)"
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(args.steps):
+        step()
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / args.steps
+    api.bp_device_status(ctx)
+    print(json.dumps({"metric": f"{args.op}_gups", "value": upd / (ms * 1e-3) / 1e9, "unit": "GUPS",
+                      "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+                      "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+                      "config": {"workload": args.workload, "batch": batch, "step": unit_desc}}), flush=True)
+    ctx.close()
 
 
 def run_ours(args):
@@ -357,6 +409,8 @@ def main(argv=None):
     args = parse_args(argv)
     if args.impl == "reference":
         run_reference(args)
+    elif args.op != "fdk":
+        run_op(args)
     else:
         run_ours(args)
 
