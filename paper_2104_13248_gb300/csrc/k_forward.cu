@@ -12,6 +12,13 @@
 namespace bp {
 
 constexpr int kFpTX = 32, kFpTY = 8, kFpTK = 32;
+
+// Shared-memory reduction without a return value (red.shared.add.f32): the
+// plain atomicAdd on a float in shared memory can come out as a
+// compare-and-swap loop.
+__device__ __forceinline__ void red_add_shared(float *p, float v) {
+    asm volatile("red.shared.add.f32 [%0], %1;" ::"r"(smem_addr(p)), "f"(v) : "memory");
+}
 constexpr int kFpThreads = kFpTX * kFpTY;
 
 template <int TK>
@@ -87,10 +94,10 @@ fp_zcol(const float *__restrict__ vol, const double *__restrict__ P, int nviews,
                         float val = wt * x[kk];
                         float a1 = fv * val, a0 = val - a1;   // (1-fv) val, fv val
                         float *p = base + row * bu;
-                        atomicAdd(p, gu * a0);
-                        atomicAdd(p + 1, fu * a0);
-                        atomicAdd(p + bu, gu * a1);
-                        atomicAdd(p + bu + 1, fu * a1);
+                        red_add_shared(p, gu * a0);
+                        red_add_shared(p + 1, fu * a0);
+                        red_add_shared(p + bu, gu * a1);
+                        red_add_shared(p + bu + 1, fu * a1);
                     }
                 }
             }
