@@ -21,14 +21,23 @@ __device__ __forceinline__ void red_add_shared(float *p, float v) {
 }
 constexpr int kFpThreads = kFpTX * kFpTY;
 
+// Per (column, view) quantities shared by the 32 lanes that scatter the
+// column's voxels (computed once per view by the thread owning the column).
+struct FpCol {
+    float v0, dv, wt, fu;
+    int cu, ok;
+};
+
 template <int TK>
 __global__ void __launch_bounds__(kFpThreads)
 fp_zcol(const float *__restrict__ vol, const double *__restrict__ P, int nviews, int nu, int nv,
         int nx, int ny, int nz, int bu, int bv, float scale, float *__restrict__ proj,
         unsigned *err) {
+    static_assert(TK == 32, "one lane per voxel of a 32-voxel column chunk");
     extern __shared__ __align__(16) unsigned char smem[];
     ViewRec *recs = reinterpret_cast<ViewRec *>(smem);
-    float *box = reinterpret_cast<float *>(smem + kRecChunk * sizeof(ViewRec));
+    FpCol *cols = reinterpret_cast<FpCol *>(smem + kRecChunk * sizeof(ViewRec));
+    float *box = reinterpret_cast<float *>(smem + kRecChunk * sizeof(ViewRec) + kFpThreads * sizeof(FpCol));
     const int nbox = bu * bv;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -37,18 +46,28 @@ fp_zcol(const float *__restrict__ vol, const double *__restrict__ P, int nviews,
     const int k0 = blockIdx.y * TK;
     const int b = blockIdx.z;
     const int ex = min(kFpTX, nx - i0), ey = min(kFpTY, ny - j0), ez = min(TK, nz - k0);
+    // column owned by this thread for the per-view setup (8 x 4 patch per warp)
     const int wx = warp % (kFpTX / 8), wy = warp / (kFpTX / 8);
     const int di = wx * 8 + (lane & 7), dj = wy * 4 + (lane >> 3);
     const bool col_ok = di < ex && dj < ey;
     const float fdi = (float)di, fdj = (float)dj;
 
-    float x[TK];
+    // Scatter mapping: warp w handles the 32 columns of the same patch, one
+    // at a time; lane l holds voxel k0 + l of each of them. Within one
+    // scatter instruction the lanes of a column then hit 32 different
+    // detector rows (the v step per voxel is >= 1 pixel here), so the
+    // shared-memory adds do not contend inside the warp.
+    float x[32];
     {
-        size_t plane = (size_t)nx * ny;
-        size_t base = ((size_t)b * nz + k0) * plane + (size_t)(j0 + dj) * nx + (i0 + di);
+        const size_t plane = (size_t)nx * ny;
+        const bool kin = lane < ez;
 #pragma unroll
-        for (int kk = 0; kk < TK; ++kk)
-            x[kk] = (col_ok && kk < ez) ? scale * vol[base + (size_t)kk * plane] : 0.0f;
+        for (int c = 0; c < 32; ++c) {
+            const int cdi = wx * 8 + (c & 7), cdj = wy * 4 + (c >> 3);
+            const bool ok = kin && cdi < ex && cdj < ey;
+            x[c] = ok ? scale * vol[((size_t)b * nz + k0 + lane) * plane + (size_t)(j0 + cdj) * nx + (i0 + cdi)]
+                      : 0.0f;
+        }
     }
     float *pb = proj + (size_t)b * nviews * nu * nv;
 
@@ -64,41 +83,50 @@ fp_zcol(const float *__restrict__ vol, const double *__restrict__ P, int nviews,
         for (int n = 0; n < cn; ++n) {
             __syncthreads();   // previous flush done (and records ready)
             for (int t = tid; t < nbox; t += kFpThreads) box[t] = 0.0f;
-            __syncthreads();
             const ViewRec r = recs[n];
-            if (col_ok) {
-                float W = fmaf(r.Wj, fdj, fmaf(r.Wi, fdi, r.W0));
-                float inv = __frcp_rn(W);
-                float uL = fmaf(r.Nuj, fdj, fmaf(r.Nui, fdi, r.Nu0)) * inv;
-                float v0 = fmaf(r.Nvj, fdj, fmaf(r.Nvi, fdi, r.Nv0)) * inv;
-                float dv = r.Nvk * inv;
-                float wt = inv * inv;
-                float tu = __fadd_rd(uL, kMagic);
-                int cu = __float_as_int(tu) - kMagicBits;
-                float fu = uL - (tu - kMagic);
-                float vlast = fmaf((float)(ez - 1), dv, v0);
-                int rfirst = __float_as_int(__fadd_rd(v0, kMagic)) - kMagicBits;
-                int rlast = __float_as_int(__fadd_rd(vlast, kMagic)) - kMagicBits;
-                if (cu < 0 || cu > bu - 2 || min(rfirst, rlast) < 0 || max(rfirst, rlast) > bv - 2 || !(uL == uL)) {
-                    atomicOr(err, DEV_ERR_FOOTPRINT);
-                } else {
-                    float *base = box + cu;
-                    const float gu = 1.0f - fu;
+            {
+                FpCol c;
+                c.ok = 0;
+                if (col_ok) {
+                    float W = fmaf(r.Wj, fdj, fmaf(r.Wi, fdi, r.W0));
+                    float inv = __frcp_rn(W);
+                    float uL = fmaf(r.Nuj, fdj, fmaf(r.Nui, fdi, r.Nu0)) * inv;
+                    c.v0 = fmaf(r.Nvj, fdj, fmaf(r.Nvi, fdi, r.Nv0)) * inv;
+                    c.dv = r.Nvk * inv;
+                    c.wt = inv * inv;
+                    float tu = __fadd_rd(uL, kMagic);
+                    c.cu = __float_as_int(tu) - kMagicBits;
+                    c.fu = uL - (tu - kMagic);
+                    float vlast = fmaf((float)(ez - 1), c.dv, c.v0);
+                    int rfirst = __float_as_int(__fadd_rd(c.v0, kMagic)) - kMagicBits;
+                    int rlast = __float_as_int(__fadd_rd(vlast, kMagic)) - kMagicBits;
+                    if (c.cu < 0 || c.cu > bu - 2 || min(rfirst, rlast) < 0 ||
+                        max(rfirst, rlast) > bv - 2 || !(uL == uL))
+                        atomicOr(err, DEV_ERR_FOOTPRINT);
+                    else
+                        c.ok = 1;
+                }
+                cols[tid] = c;
+            }
+            __syncthreads();
+            const float fl = (float)lane;
 #pragma unroll
-                    for (int kk = 0; kk < TK; ++kk) {
-                        if (kk >= ez) break;
-                        float v = fmaf((float)kk, dv, v0);
-                        float tv = __fadd_rd(v, kMagic);
-                        float fv = v - (tv - kMagic);
-                        int row = __float_as_int(tv) - kMagicBits;
-                        float val = wt * x[kk];
-                        float a1 = fv * val, a0 = val - a1;   // (1-fv) val, fv val
-                        float *p = base + row * bu;
-                        red_add_shared(p, gu * a0);
-                        red_add_shared(p + 1, fu * a0);
-                        red_add_shared(p + bu, gu * a1);
-                        red_add_shared(p + bu + 1, fu * a1);
-                    }
+            for (int c = 0; c < 32; ++c) {
+                const FpCol cc = cols[warp * 32 + ((c >> 3) << 3) + (c & 7)];
+                if (!cc.ok) continue;   // uniform across the warp
+                float v = fmaf(fl, cc.dv, cc.v0);
+                float tv = __fadd_rd(v, kMagic);
+                float fv = v - (tv - kMagic);
+                int row = __float_as_int(tv) - kMagicBits;
+                float val = cc.wt * x[c];
+                float a1 = fv * val, a0 = val - a1;   // (1-fv) val, fv val
+                if (lane < ez && val != 0.0f) {
+                    float *p = box + row * bu + cc.cu;
+                    const float gu = 1.0f - cc.fu;
+                    red_add_shared(p, gu * a0);
+                    red_add_shared(p + 1, cc.fu * a0);
+                    red_add_shared(p + bu, gu * a1);
+                    red_add_shared(p + bu + 1, cc.fu * a1);
                 }
             }
             __syncthreads();
@@ -178,7 +206,8 @@ bp_status launch_forward(bp_ctx *ctx, const float *vol, float *proj, int batch, 
     // FP tiles are 32 x 8 x 32, the same shape the plan's TK=32 box covers;
     // with TK=64 plans the box is at least as large, so it still covers.
     const int bu = ctx->plan.bu, bv = ctx->plan.bv;
-    const int smem = kRecChunk * (int)sizeof(ViewRec) + bu * bv * (int)sizeof(float);
+    const int smem = kRecChunk * (int)sizeof(ViewRec) + kFpThreads * (int)sizeof(FpCol) +
+                     bu * bv * (int)sizeof(float);
     e = cudaFuncSetAttribute(fp_zcol<kFpTK>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "fp_zcol attribute");
     dim3 grid(((ctx->nx + kFpTX - 1) / kFpTX) * ((ctx->ny + kFpTY - 1) / kFpTY),
