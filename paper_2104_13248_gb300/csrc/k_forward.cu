@@ -38,7 +38,10 @@ fp_zcol(const float *__restrict__ vol, const double *__restrict__ P, int nviews,
     ViewRec *recs = reinterpret_cast<ViewRec *>(smem);
     FpCol *cols = reinterpret_cast<FpCol *>(smem + kRecChunk * sizeof(ViewRec));
     float *box = reinterpret_cast<float *>(smem + kRecChunk * sizeof(ViewRec) + kFpThreads * sizeof(FpCol));
-    const int nbox = bu * bv;
+    // odd row pitch: the 32 lanes of a column walk down ~32-64 rows at one
+    // column, which an odd pitch spreads over all 32 banks
+    const int pitch = bu | 1;
+    const int nbox = pitch * bv;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int ntx = (nx + kFpTX - 1) / kFpTX;
@@ -121,21 +124,21 @@ fp_zcol(const float *__restrict__ vol, const double *__restrict__ P, int nviews,
                 float val = cc.wt * x[c];
                 float a1 = fv * val, a0 = val - a1;   // (1-fv) val, fv val
                 if (lane < ez && val != 0.0f) {
-                    float *p = box + row * bu + cc.cu;
+                    float *p = box + row * pitch + cc.cu;
                     const float gu = 1.0f - cc.fu;
                     red_add_shared(p, gu * a0);
                     red_add_shared(p + 1, cc.fu * a0);
-                    red_add_shared(p + bu, gu * a1);
-                    red_add_shared(p + bu + 1, cc.fu * a1);
+                    red_add_shared(p + pitch, gu * a1);
+                    red_add_shared(p + pitch + 1, cc.fu * a1);
                 }
             }
             __syncthreads();
             // flush the box into the projection (pixels inside the detector only)
             float *img = pb + (size_t)(cb + n) * nu * nv;
-            for (int t = tid; t < nbox; t += kFpThreads) {
+            for (int t = tid; t < bu * bv; t += kFpThreads) {
                 int rr = t / bu, cc = t - rr * bu;
                 int r_ = r.v_box + rr, c_ = r.u_box + cc;
-                float val = box[t];
+                float val = box[rr * pitch + cc];
                 if (val != 0.0f && r_ >= 0 && r_ < nv && c_ >= 0 && c_ < nu)
                     atomicAdd(img + (size_t)r_ * nu + c_, val);
             }
@@ -207,7 +210,7 @@ bp_status launch_forward(bp_ctx *ctx, const float *vol, float *proj, int batch, 
     // with TK=64 plans the box is at least as large, so it still covers.
     const int bu = ctx->plan.bu, bv = ctx->plan.bv;
     const int smem = kRecChunk * (int)sizeof(ViewRec) + kFpThreads * (int)sizeof(FpCol) +
-                     bu * bv * (int)sizeof(float);
+                     (bu | 1) * bv * (int)sizeof(float);
     e = cudaFuncSetAttribute(fp_zcol<kFpTK>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "fp_zcol attribute");
     dim3 grid(((ctx->nx + kFpTX - 1) / kFpTX) * ((ctx->ny + kFpTY - 1) / kFpTY),
