@@ -157,6 +157,19 @@ static void make_plan(bp_ctx *ctx) {
     auto fits = [&](int bu, int es) { return bu > 0 && base + 4 * ((bu * pl.bv * es + 127) / 128 * 128) <= 227 * 1024; };
     if (pl.bv > 256 || !fits(pl.bu, 4)) pl.bu = -1;
     if (pl.bv > 256 || !fits(pl.bu16, 2)) pl.bu16 = -1;
+    // forward projector: per-warp boxes of an 8 x 4 column patch, 32 voxels deep
+    // (+1 column and row of slack for the FP32 corner rounding)
+    int wbu, wbv;
+    max_footprint(ctx, 8, 4, 32, 1, &wbu, &wbv);
+    wbu += 1;
+    wbv += 1;
+    const int fp_smem = 256 * 48 + 256 * 24 + 8 * (wbu | 1) * wbv * 4;
+    if (pl.bu > 0 && fp_smem <= 227 * 1024) {
+        pl.fp_wbu = wbu;
+        pl.fp_wbv = wbv;
+    } else {
+        pl.fp_wbu = pl.fp_wbv = -1;
+    }
 }
 
 // Ramp filter tables: real spectrum of the circularly embedded Ram-Lak

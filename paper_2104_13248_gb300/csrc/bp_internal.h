@@ -52,6 +52,7 @@ struct Plan {
     int bu16;                // box width for FP16 (multiple of 8)
     int stages;              // pipeline depth (views in flight)
     int ctas;                // CTAs per SM the TK=32 kernel's register budget targets (2 or 3)
+    int fp_wbu, fp_wbv;      // forward projector: per-warp box (8 x 4 columns x 32 voxels), -1 if unusable
 };
 
 }  // namespace bp

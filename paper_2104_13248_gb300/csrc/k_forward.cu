@@ -31,17 +31,18 @@ struct FpCol {
 template <int TK>
 __global__ void __launch_bounds__(kFpThreads)
 fp_zcol(const float *__restrict__ vol, const double *__restrict__ P, int nviews, int nu, int nv,
-        int nx, int ny, int nz, int bu, int bv, float scale, float *__restrict__ proj,
-        unsigned *err) {
+        int nx, int ny, int nz, int bu, int bv, int wbu, int wbv, float scale,
+        float *__restrict__ proj, unsigned *err) {
     static_assert(TK == 32, "one lane per voxel of a 32-voxel column chunk");
     extern __shared__ __align__(16) unsigned char smem[];
     ViewRec *recs = reinterpret_cast<ViewRec *>(smem);
     FpCol *cols = reinterpret_cast<FpCol *>(smem + kRecChunk * sizeof(ViewRec));
-    float *box = reinterpret_cast<float *>(smem + kRecChunk * sizeof(ViewRec) + kFpThreads * sizeof(FpCol));
-    // odd row pitch: the 32 lanes of a column walk down ~32-64 rows at one
-    // column, which an odd pitch spreads over all 32 banks
-    const int pitch = bu | 1;
-    const int nbox = pitch * bv;
+    // one private box per warp, odd row pitch: the lanes of a column walk
+    // down the rows at one column, which an odd pitch spreads over the banks
+    const int wpitch = wbu | 1;
+    const int wbox_n = wpitch * wbv;
+    float *wbox = reinterpret_cast<float *>(smem + kRecChunk * sizeof(ViewRec) + kFpThreads * sizeof(FpCol)) +
+                  (threadIdx.x >> 5) * wbox_n;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int ntx = (nx + kFpTX - 1) / kFpTX;
@@ -55,11 +56,11 @@ fp_zcol(const float *__restrict__ vol, const double *__restrict__ P, int nviews,
     const bool col_ok = di < ex && dj < ey;
     const float fdi = (float)di, fdj = (float)dj;
 
-    // Scatter mapping: warp w handles the 32 columns of the same patch, one
-    // at a time; lane l holds voxel k0 + l of each of them. Within one
-    // scatter instruction the lanes of a column then hit 32 different
-    // detector rows (the v step per voxel is >= 1 pixel here), so the
-    // shared-memory adds do not contend inside the warp.
+    // Scatter mapping: warp w handles the 32 columns of its patch one at a
+    // time; lane l holds voxel k0 + l of each of them. The v step per voxel
+    // is at least one pixel (checked per column), so within one scatter
+    // instruction the lanes of a column write 32 different rows of the
+    // warp's own box: plain read-add-write, no atomics.
     float x[32];
     {
         const size_t plane = (size_t)nx * ny;
@@ -84,63 +85,88 @@ fp_zcol(const float *__restrict__ vol, const double *__restrict__ P, int nviews,
             recs[n] = r;
         }
         for (int n = 0; n < cn; ++n) {
-            __syncthreads();   // previous flush done (and records ready)
-            for (int t = tid; t < nbox; t += kFpThreads) box[t] = 0.0f;
+            __syncthreads();   // records ready; previous view's column setup consumed
             const ViewRec r = recs[n];
-            {
-                FpCol c;
-                c.ok = 0;
-                if (col_ok) {
-                    float W = fmaf(r.Wj, fdj, fmaf(r.Wi, fdi, r.W0));
-                    float inv = __frcp_rn(W);
-                    float uL = fmaf(r.Nuj, fdj, fmaf(r.Nui, fdi, r.Nu0)) * inv;
-                    c.v0 = fmaf(r.Nvj, fdj, fmaf(r.Nvi, fdi, r.Nv0)) * inv;
-                    c.dv = r.Nvk * inv;
-                    c.wt = inv * inv;
-                    float tu = __fadd_rd(uL, kMagic);
-                    c.cu = __float_as_int(tu) - kMagicBits;
-                    c.fu = uL - (tu - kMagic);
-                    float vlast = fmaf((float)(ez - 1), c.dv, c.v0);
-                    int rfirst = __float_as_int(__fadd_rd(c.v0, kMagic)) - kMagicBits;
-                    int rlast = __float_as_int(__fadd_rd(vlast, kMagic)) - kMagicBits;
-                    if (c.cu < 0 || c.cu > bu - 2 || min(rfirst, rlast) < 0 ||
-                        max(rfirst, rlast) > bv - 2 || !(uL == uL))
-                        atomicOr(err, DEV_ERR_FOOTPRINT);
-                    else
-                        c.ok = 1;
+            FpCol c;
+            c.ok = 0;
+            float umin = 3e38f, umax = -3e38f, vmin = 3e38f, vmax = -3e38f;
+            if (col_ok) {
+                float W = fmaf(r.Wj, fdj, fmaf(r.Wi, fdi, r.W0));
+                float inv = __frcp_rn(W);
+                float uL = fmaf(r.Nuj, fdj, fmaf(r.Nui, fdi, r.Nu0)) * inv;
+                c.v0 = fmaf(r.Nvj, fdj, fmaf(r.Nvi, fdi, r.Nv0)) * inv;
+                c.dv = r.Nvk * inv;
+                c.wt = inv * inv;
+                float tu = __fadd_rd(uL, kMagic);
+                c.cu = __float_as_int(tu) - kMagicBits;
+                c.fu = uL - (tu - kMagic);
+                float vlast = fmaf((float)(ez - 1), c.dv, c.v0);
+                if (uL == uL && c.v0 == c.v0) {
+                    c.ok = 1;
+                    umin = umax = uL;
+                    vmin = fminf(c.v0, vlast);
+                    vmax = fmaxf(c.v0, vlast);
                 }
-                cols[tid] = c;
             }
-            __syncthreads();
-            const float fl = (float)lane;
+            // the warp's box: floor of the smallest column / row its lanes touch
+            for (int o = 16; o > 0; o >>= 1) {
+                umin = fminf(umin, __shfl_xor_sync(0xffffffffu, umin, o));
+                umax = fmaxf(umax, __shfl_xor_sync(0xffffffffu, umax, o));
+                vmin = fminf(vmin, __shfl_xor_sync(0xffffffffu, vmin, o));
+                vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
+            }
+            const bool any = umin <= umax;
+            const int uo = any ? __float_as_int(__fadd_rd(umin, kMagic)) - kMagicBits : 0;
+            const int vo = any ? __float_as_int(__fadd_rd(vmin, kMagic)) - kMagicBits : 0;
+            const bool fits = any && (__float_as_int(__fadd_rd(umax, kMagic)) - kMagicBits) + 1 - uo <= wbu - 1 &&
+                              (__float_as_int(__fadd_rd(vmax, kMagic)) - kMagicBits) + 1 - vo <= wbv - 1;
+            if (any && !fits && lane == 0) atomicOr(err, DEV_ERR_FOOTPRINT);
+            if (c.ok) {
+                c.cu -= uo;   // column relative to the warp box
+                if (!(c.dv >= 1.0f)) {
+                    c.ok = 0;   // rows of consecutive voxels could coincide
+                    atomicOr(err, DEV_ERR_FOOTPRINT);
+                }
+            }
+            cols[tid] = c;
+            for (int t = lane; t < wbox_n; t += 32) wbox[t] = 0.0f;
+            __syncwarp();
+            if (any && fits) {
+                const float fl = (float)lane;
 #pragma unroll
-            for (int c = 0; c < 32; ++c) {
-                const FpCol cc = cols[warp * 32 + ((c >> 3) << 3) + (c & 7)];
-                if (!cc.ok) continue;   // uniform across the warp
-                float v = fmaf(fl, cc.dv, cc.v0);
-                float tv = __fadd_rd(v, kMagic);
-                float fv = v - (tv - kMagic);
-                int row = __float_as_int(tv) - kMagicBits;
-                float val = cc.wt * x[c];
-                float a1 = fv * val, a0 = val - a1;   // (1-fv) val, fv val
-                if (lane < ez && val != 0.0f) {
-                    float *p = box + row * pitch + cc.cu;
+                for (int cix = 0; cix < 32; ++cix) {
+                    const FpCol cc = cols[warp * 32 + cix];
+                    if (!cc.ok) continue;   // uniform across the warp
+                    float v = fmaf(fl, cc.dv, cc.v0);
+                    float tv = __fadd_rd(v, kMagic);
+                    float fv = v - (tv - kMagic);
+                    int row = __float_as_int(tv) - kMagicBits - vo;
+                    float val = cc.wt * x[cix];
+                    float a1 = fv * val, a0 = val - a1;   // (1-fv) val, fv val
+                    const bool act = lane < ez && val != 0.0f;
+                    float *p = wbox + row * wpitch + cc.cu;
                     const float gu = 1.0f - cc.fu;
-                    red_add_shared(p, gu * a0);
-                    red_add_shared(p + 1, cc.fu * a0);
-                    red_add_shared(p + pitch, gu * a1);
-                    red_add_shared(p + pitch + 1, cc.fu * a1);
+                    // four phases: within each, the lanes' addresses differ
+                    if (act) p[0] += gu * a0;
+                    __syncwarp();
+                    if (act) p[1] += cc.fu * a0;
+                    __syncwarp();
+                    if (act) p[wpitch] += gu * a1;
+                    __syncwarp();
+                    if (act) p[wpitch + 1] += cc.fu * a1;
+                    __syncwarp();
                 }
-            }
-            __syncthreads();
-            // flush the box into the projection (pixels inside the detector only)
-            float *img = pb + (size_t)(cb + n) * nu * nv;
-            for (int t = tid; t < bu * bv; t += kFpThreads) {
-                int rr = t / bu, cc = t - rr * bu;
-                int r_ = r.v_box + rr, c_ = r.u_box + cc;
-                float val = box[rr * pitch + cc];
-                if (val != 0.0f && r_ >= 0 && r_ < nv && c_ >= 0 && c_ < nu)
-                    atomicAdd(img + (size_t)r_ * nu + c_, val);
+                // flush the warp's box into the projection (inside the detector only)
+                float *img = pb + (size_t)(cb + n) * nu * nv;
+                const int rows_used = min(wbv, (__float_as_int(__fadd_rd(vmax, kMagic)) - kMagicBits) + 2 - vo);
+                const int cols_used = min(wbu, (__float_as_int(__fadd_rd(umax, kMagic)) - kMagicBits) + 2 - uo);
+                for (int t = lane; t < rows_used * cols_used; t += 32) {
+                    const int rr = t / cols_used, ccol = t - rr * cols_used;
+                    const float val = wbox[rr * wpitch + ccol];
+                    const int r_ = r.v_box + vo + rr, c_ = r.u_box + uo + ccol;
+                    if (val != 0.0f && r_ >= 0 && r_ < nv && c_ >= 0 && c_ < nu)
+                        atomicAdd(img + (size_t)r_ * nu + c_, val);
+                }
             }
         }
     }
@@ -198,7 +224,7 @@ bp_status launch_forward(bp_ctx *ctx, const float *vol, float *proj, int batch, 
     size_t bytes = sizeof(float) * (size_t)batch * ctx->n_views * ctx->nu * ctx->nv;
     cudaError_t e = cudaMemsetAsync(proj, 0, bytes, st);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "fp_project: clear");
-    if (!ctx->zinv || ctx->plan.bu <= 0) {
+    if (!ctx->zinv || ctx->plan.bu <= 0 || ctx->plan.fp_wbu <= 0) {
         // general matrices, or a footprint too large for the shared box
         dim3 grid(((ctx->nx + 7) / 8) * ((ctx->ny + 7) / 8) * ((ctx->nz + 3) / 4), 1, batch);
         fp_voxel_gen<<<grid, 256, 0, st>>>(vol, ctx->d_P, ctx->n_views, ctx->nu, ctx->nv, ctx->nx,
@@ -209,15 +235,16 @@ bp_status launch_forward(bp_ctx *ctx, const float *vol, float *proj, int batch, 
     // FP tiles are 32 x 8 x 32, the same shape the plan's TK=32 box covers;
     // with TK=64 plans the box is at least as large, so it still covers.
     const int bu = ctx->plan.bu, bv = ctx->plan.bv;
+    const int wbu = ctx->plan.fp_wbu, wbv = ctx->plan.fp_wbv;
     const int smem = kRecChunk * (int)sizeof(ViewRec) + kFpThreads * (int)sizeof(FpCol) +
-                     (bu | 1) * bv * (int)sizeof(float);
+                     (kFpThreads / 32) * (wbu | 1) * wbv * (int)sizeof(float);
     e = cudaFuncSetAttribute(fp_zcol<kFpTK>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "fp_zcol attribute");
     dim3 grid(((ctx->nx + kFpTX - 1) / kFpTX) * ((ctx->ny + kFpTY - 1) / kFpTY),
               (ctx->nz + kFpTK - 1) / kFpTK, batch);
     fp_zcol<kFpTK><<<grid, kFpThreads, smem, st>>>(vol, ctx->d_P, ctx->n_views, ctx->nu, ctx->nv,
-                                                  ctx->nx, ctx->ny, ctx->nz, bu, bv, scale, proj,
-                                                  ctx->d_err);
+                                                  ctx->nx, ctx->ny, ctx->nz, bu, bv, wbu, wbv, scale,
+                                                  proj, ctx->d_err);
     e = cudaGetLastError();
     return e == cudaSuccess ? BP_OK : cuda_fail(ctx, e, "fp_zcol launch");
 }
