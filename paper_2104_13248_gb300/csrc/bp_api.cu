@@ -163,7 +163,7 @@ static void make_plan(bp_ctx *ctx) {
     max_footprint(ctx, 8, 4, 32, 1, &wbu, &wbv);
     wbu += 1;
     wbv += 1;
-    const int fp_smem = 256 * 48 + 256 * 24 + 8 * (wbu | 1) * wbv * 4;
+    const int fp_smem = 256 * 48 + 256 * 32 + 8 * (wbu | 1) * wbv * 4;
     if (pl.bu > 0 && fp_smem <= 227 * 1024) {
         pl.fp_wbu = wbu;
         pl.fp_wbv = wbv;

@@ -23,9 +23,9 @@ constexpr int kFpThreads = kFpTX * kFpTY;
 
 // Per (column, view) quantities shared by the 32 lanes that scatter the
 // column's voxels (computed once per view by the thread owning the column).
-struct FpCol {
+struct __align__(16) FpCol {
     float v0, dv, wt, fu;
-    int cu, ok;
+    int cu, ok, pad0, pad1;
 };
 
 template <int TK>
@@ -89,6 +89,7 @@ fp_zcol(const float *__restrict__ vol, const double *__restrict__ P, int nviews,
             const ViewRec r = recs[n];
             FpCol c;
             c.ok = 0;
+            c.pad0 = c.pad1 = 0;
             float umin = 3e38f, umax = -3e38f, vmin = 3e38f, vmax = -3e38f;
             if (col_ok) {
                 float W = fmaf(r.Wj, fdj, fmaf(r.Wi, fdi, r.W0));
@@ -160,12 +161,15 @@ fp_zcol(const float *__restrict__ vol, const double *__restrict__ P, int nviews,
                 float *img = pb + (size_t)(cb + n) * nu * nv;
                 const int rows_used = min(wbv, (__float_as_int(__fadd_rd(vmax, kMagic)) - kMagicBits) + 2 - vo);
                 const int cols_used = min(wbu, (__float_as_int(__fadd_rd(umax, kMagic)) - kMagicBits) + 2 - uo);
-                for (int t = lane; t < rows_used * cols_used; t += 32) {
-                    const int rr = t / cols_used, ccol = t - rr * cols_used;
-                    const float val = wbox[rr * wpitch + ccol];
-                    const int r_ = r.v_box + vo + rr, c_ = r.u_box + uo + ccol;
-                    if (val != 0.0f && r_ >= 0 && r_ < nv && c_ >= 0 && c_ < nu)
-                        atomicAdd(img + (size_t)r_ * nu + c_, val);
+                for (int rr = 0; rr < rows_used; ++rr) {
+                    const int r_ = r.v_box + vo + rr;
+                    if (r_ < 0 || r_ >= nv) continue;   // uniform across the warp
+                    float *dst = img + (size_t)r_ * nu;
+                    for (int ccol = lane; ccol < cols_used; ccol += 32) {
+                        const float val = wbox[rr * wpitch + ccol];
+                        const int c_ = r.u_box + uo + ccol;
+                        if (val != 0.0f && c_ >= 0 && c_ < nu) atomicAdd(dst + c_, val);
+                    }
                 }
             }
         }
