@@ -161,15 +161,13 @@ fp_zcol(const float *__restrict__ vol, const double *__restrict__ P, int nviews,
                 float *img = pb + (size_t)(cb + n) * nu * nv;
                 const int rows_used = min(wbv, (__float_as_int(__fadd_rd(vmax, kMagic)) - kMagicBits) + 2 - vo);
                 const int cols_used = min(wbu, (__float_as_int(__fadd_rd(umax, kMagic)) - kMagicBits) + 2 - uo);
-                for (int rr = 0; rr < rows_used; ++rr) {
-                    const int r_ = r.v_box + vo + rr;
-                    if (r_ < 0 || r_ >= nv) continue;   // uniform across the warp
-                    float *dst = img + (size_t)r_ * nu;
-                    for (int ccol = lane; ccol < cols_used; ccol += 32) {
-                        const float val = wbox[rr * wpitch + ccol];
-                        const int c_ = r.u_box + uo + ccol;
-                        if (val != 0.0f && c_ >= 0 && c_ < nu) atomicAdd(dst + c_, val);
-                    }
+                // flattened over the used rows x columns so every lane has work
+                for (int t = lane; t < rows_used * cols_used; t += 32) {
+                    const int rr = t / cols_used, ccol = t - rr * cols_used;
+                    const float val = wbox[rr * wpitch + ccol];
+                    const int r_ = r.v_box + vo + rr, c_ = r.u_box + uo + ccol;
+                    if (val != 0.0f && r_ >= 0 && r_ < nv && c_ >= 0 && c_ < nu)
+                        atomicAdd(img + (size_t)r_ * nu + c_, val);
                 }
             }
         }
