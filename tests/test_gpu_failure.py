@@ -1,0 +1,57 @@
+"""Failure detection on the GPU without a fault: a bounded wait that runs out.
+
+The staging producer of the back-projector is told to skip one view's load
+(bp_test_drop_view), so no copy ever completes that view's barrier. Every
+wait in the kernel has a time limit: the consumers give up on the missing
+view, the producer gives up on the slot they never release, both record
+DEV_ERR_TIMEOUT in the context's device word and the CTA returns after the
+copies it did issue have landed. The host then reads BP_ERR_TIMEOUT from
+bp_device_status, and the same context (and CUDA context) keeps working: the
+next call without the hook reproduces the result of a clean call bit for bit.
+
+The problem is one wave of CTAs (64^3 voxels, 90 views) and the limit is
+50 ms, so the failing launch ends in about a tenth of a second.
+"""
+import math
+
+import pytest
+import torch
+
+from paper_2104_13248_gb300 import _lib, api, inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def test_dropped_view_times_out_and_context_survives():
+    g = inputs.preset("c1_small")["geom"]
+    q = torch.from_numpy(inputs.uniform_array(11, (g["np"], g["nv"], g["nu"]), -1.0, 1.0)).float().cuda()
+    scale = math.pi / g["np"]
+    with api.bp_create(g) as ctx:
+        plan = api.bp_get_plan(ctx)
+        if plan["bu32"] < 0:
+            pytest.skip("the staged (TMA) kernel is not used for this geometry")
+        ref = api.bp_backproject(ctx, q, scale=scale)
+        api.bp_device_status(ctx)
+
+        api.bp_set_timeout(ctx, 0.05)
+        api.bp_test_drop_view(ctx, 7)
+        vol = torch.zeros(ctx.vol_shape(), device="cuda")
+        api.bp_backproject(ctx, q, vol=vol, scale=scale)
+        with pytest.raises(_lib.BPError) as e:
+            api.bp_device_status(ctx)
+        assert e.value.status == _lib.BP_ERR_TIMEOUT
+
+        # the word was cleared by the read, the hook is off: a clean call again
+        api.bp_test_drop_view(ctx, -1)
+        api.bp_device_status(ctx)
+        again = api.bp_backproject(ctx, q, scale=scale)
+        api.bp_device_status(ctx)
+        assert torch.equal(again, ref)
+        # other kernels on the same CUDA context are unaffected
+        assert torch.isfinite(api.bp_filter(ctx, q)).all()
