@@ -4,6 +4,7 @@
 // footprints of the CTA tiles, and every call validates its arguments
 // before launching.
 #include "bp_internal.h"
+#include "filter_quad.h"
 
 #include <algorithm>
 #include <atomic>
@@ -176,8 +177,13 @@ static void make_plan(bp_ctx *ctx) {
 // kernel (times dp and 1/N, natural order) and the N FFT twiddles.
 static bp_status make_filter_tables(bp_ctx *ctx) {
     const bp_geometry &g = ctx->g;
-    int n = 1, lg = 0;
-    while (n < 2 * g.nu - 1 || n < 16) { n <<= 1; ++lg; }
+    int n = quad_fft_size(g.nu), lg = 0;
+    ctx->fft_quad = n > 0;
+    if (!ctx->fft_quad) {
+        n = 1;
+        while (n < 2 * g.nu - 1 || n < 16) n <<= 1;
+    }
+    while ((1 << lg) < n) ++lg;
     ctx->fft_n = n;
     ctx->fft_log2 = lg;
     const double dp = g.du * g.sid / g.sdd;
@@ -193,6 +199,24 @@ static bp_status make_filter_tables(bp_ctx *ctx) {
         double acc = h[0];
         for (int m = 1; m < g.nu; m += 2) acc += 2.0 * h[m] * std::cos(2.0 * M_PI * (double)((long long)k * m % n) / n);
         Hf[k] = (float)(acc * dp / n);
+    }
+    if (ctx->fft_quad) {
+        // four-row kernel: spectrum and twiddle angles duplicated for its two lanes
+        std::vector<float> H2(2 * (size_t)n), tw4(4 * (size_t)n);
+        for (int k = 0; k < n; ++k) {
+            H2[2 * k] = H2[2 * k + 1] = Hf[k];
+            const float c = (float)std::cos(2.0 * M_PI * k / n), sn = (float)std::sin(2.0 * M_PI * k / n);
+            tw4[4 * k] = tw4[4 * k + 1] = c;
+            tw4[4 * k + 2] = tw4[4 * k + 3] = sn;
+        }
+        cudaError_t e = dev_alloc(&ctx->d_H2, sizeof(float) * 2 * n);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "filter spectrum");
+        e = dev_alloc(&ctx->d_tw4, sizeof(float) * 4 * n);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "filter twiddles");
+        e = cudaMemcpy(ctx->d_H2, H2.data(), sizeof(float) * 2 * n, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(ctx->d_tw4, tw4.data(), sizeof(float) * 4 * n, cudaMemcpyHostToDevice);
+        return e == cudaSuccess ? BP_OK : cuda_fail(ctx, e, "filter tables upload");
     }
     for (int k = 0; k < n; ++k) {
         tw[2 * k] = (float)std::cos(2.0 * M_PI * k / n);
@@ -459,6 +483,8 @@ void bp_destroy(bp_ctx *ctx) {
     cudaFree(ctx->d_err);
     cudaFree(ctx->d_H);
     cudaFree(ctx->d_tw);
+    cudaFree(ctx->d_H2);
+    cudaFree(ctx->d_tw4);
     cudaFree(ctx->d_phcoef);
     delete ctx;
 }

@@ -1,7 +1,9 @@
 // FDK pre-filter (the paper assumes filtered projections, Section 2.1.2):
 // cosine weight, then the linear convolution of every detector row with the
 // discrete Ram-Lak kernel, done as a zero-padded FFT convolution in shared
-// memory. Two real rows travel as the real and imaginary parts of one
+// memory. Rows of up to 5120 pixels go to the four-row kernel of
+// filter_quad.cuh; this file holds the dispatch and, for longer rows
+// (N = 16384), a two-row kernel with one float2 per point. Two real rows travel as the real and imaginary parts of one
 // complex FFT: the kernel's spectrum is real and even, so the product keeps
 // the two rows apart.
 //
@@ -15,7 +17,10 @@
 // the last forward pass multiplies by the spectrum of the kernel (which
 // carries dp and the 1/N of the inverse); the last inverse pass writes the
 // first nu samples of each row to global memory.
+#include <cstdint>
+
 #include "bp_internal.h"
+#include "filter_quad.h"
 
 namespace bp {
 
@@ -326,19 +331,59 @@ static cudaError_t launch_lg(int lg, const FilterArgs &a, unsigned nblk, int sme
         return cudaGetLastError();                                                              \
     }
     switch (lg) {
-        BP_FILTER_CASE(4) BP_FILTER_CASE(5) BP_FILTER_CASE(6) BP_FILTER_CASE(7)
-        BP_FILTER_CASE(8) BP_FILTER_CASE(9) BP_FILTER_CASE(10) BP_FILTER_CASE(11)
-        BP_FILTER_CASE(12) BP_FILTER_CASE(13) BP_FILTER_CASE(14)
+        BP_FILTER_CASE(14)
         default: return cudaErrorInvalidValue;
     }
 #undef BP_FILTER_CASE
+}
+
+int quad_fft_size(int nu) {
+    static const int sizes[] = {32, 64, 128, 256, 512, 1024, 1280, 2048, 2560, 4096, 5120, 8192, 10240};
+    for (int n : sizes)
+        if (n >= 2 * nu - 1) return n;
+    return 0;
 }
 
 bp_status launch_filter(bp_ctx *ctx, const float *proj, void *out, bp_dtype out_t,
                         long long n_views_total, cudaStream_t st) {
     const bp_geometry &g = ctx->g;
     const int N = ctx->fft_n;
-    if (ctx->fft_log2 < 4 || ctx->fft_log2 > 14)
+    if (ctx->fft_quad) {
+        QArgs q;
+        q.in = proj;
+        q.out = out;
+        q.nrows = n_views_total * ctx->nv;
+        q.nu = ctx->nu;
+        q.nv = ctx->nv;
+        q.out_f16 = out_t == BP_F16;
+        q.in_vec = (ctx->nu % 4 == 0) && (reinterpret_cast<uintptr_t>(proj) % 16 == 0);
+        q.H2 = reinterpret_cast<const float2 *>(ctx->d_H2);
+        q.tw4 = reinterpret_cast<const ulonglong2 *>(ctx->d_tw4);
+        q.sdd = (float)g.sdd;
+        q.du = (float)g.du;
+        q.dv = (float)g.dv;
+        q.cu = (float)(0.5 * (g.nu - 1) + g.u_off_px);
+        q.cv = (float)(0.5 * (g.nv - 1) + g.v_off_px);
+        cudaError_t e;
+        switch (N) {
+            case 32: e = launch_quad<32>(q, st); break;
+            case 64: e = launch_quad<64>(q, st); break;
+            case 128: e = launch_quad<128>(q, st); break;
+            case 256: e = launch_quad<256>(q, st); break;
+            case 512: e = launch_quad<512>(q, st); break;
+            case 1024: e = launch_quad<1024>(q, st); break;
+            case 1280: e = launch_quad<1280>(q, st); break;
+            case 2048: e = launch_quad<2048>(q, st); break;
+            case 2560: e = launch_quad<2560>(q, st); break;
+            case 4096: e = launch_quad<4096>(q, st); break;
+            case 5120: e = launch_quad<5120>(q, st); break;
+            case 8192: e = launch_quad<8192>(q, st); break;
+            case 10240: e = launch_quad<10240>(q, st); break;
+            default: return fail(ctx, BP_ERR_UNSUPPORTED, "bp_filter: no transform of this size");
+        }
+        return e == cudaSuccess ? BP_OK : cuda_fail(ctx, e, "ramp_filter_quad launch");
+    }
+    if (ctx->fft_log2 != 14)
         return fail(ctx, BP_ERR_UNSUPPORTED, "bp_filter: detector rows longer than 8192 pixels");
     FilterArgs a;
     a.in = proj;

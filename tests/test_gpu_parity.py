@@ -62,16 +62,20 @@ def test_filter_c1(c1):
     assert rel(out16.astype(np.float64), ref) <= 1e-3
 
 
-@pytest.mark.parametrize("nu", [20, 33, 100, 300, 512, 1248, 2100])
+@pytest.mark.parametrize("nu", [8, 20, 33, 100, 300, 512, 600, 700, 1248, 1900, 2100, 3000, 4600, 5200])
 def test_filter_sizes(nu):
-    """Every FFT size class: N = 64 .. 8192 (radix-16 passes plus 2/4/8)."""
+    """Every transform size: N = 32 .. 8192 and 1280 .. 10240 (the four-row
+    kernel, radices 16 and 2/4/5/8/10) and N = 16384 (the two-row kernel);
+    21 rows, so the last four-row group is ragged."""
     g = dict(sid=800.0, sdd=1300.0, np=3, angles=None, nu=nu, nv=7, du=0.45, dv=0.5, u_off=1.2,
              v_off=-0.8, nx=8, ny=8, nz=8, sx=1.0, sy=1.0, sz=1.0, ox=0, oy=0, oz=0)
     raw = inputs.uniform_array(40 + nu, (g["np"], g["nv"], g["nu"]), 0.0, 2.0).astype(np.float32)
     ref = oracle.ramp_filter(g, raw)
     with api.bp_create(g) as ctx:
         out = api.bp_filter(ctx, torch.from_numpy(raw).cuda()).cpu().numpy()
+        out16 = api.bp_filter(ctx, torch.from_numpy(raw).cuda(), out_dtype=torch.float16).cpu().numpy()
     assert rel(out, ref) <= 2e-5
+    assert rel(out16.astype(np.float64), ref) <= 1e-3
 
 
 def test_host_pipeline_matches_device_fdk(c1):
