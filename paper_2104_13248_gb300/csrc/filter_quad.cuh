@@ -21,7 +21,8 @@
 //
 // Shared memory: one float4 (re pair, im pair) per point, position
 // m + m/16 within the quad's block, which keeps the 16-byte accesses of
-// every pass free of bank conflicts.
+// every pass free of bank conflicts. The raw rows are first staged at the
+// start of the same buffer with cp.async.
 #pragma once
 
 #include <cuda_fp16.h>
@@ -337,12 +338,14 @@ struct QCfg {
     static constexpr int SP = N / 2;                                   // staged row pitch (floats) >= nu
     static constexpr int BUF_BYTES = QPC * QS * 16;
     static constexpr int STAGE_BYTES = QPC * 4 * SP * 4;
-    // raw rows of the next quad are copied to shared memory while the current
-    // one is transformed, when both fit in one CTA's shared memory
-    static constexpr bool STAGED = BUF_BYTES + STAGE_BYTES <= 227 * 1024;
-    static constexpr int SMEM = BUF_BYTES + (STAGED ? STAGE_BYTES : 0);
-    // resident CTAs the register budget targets (about 128 registers a thread)
-    static constexpr int MINB = (65536 / (NT * 128)) > 1 ? 65536 / (NT * 128) : 1;
+    // raw rows are copied to the start of the transform buffer first (the
+    // first pass reads them all before it writes)
+    static constexpr bool STAGED = STAGE_BYTES <= 227 * 1024;
+    static constexpr int SMEM = BUF_BYTES > STAGE_BYTES ? BUF_BYTES : STAGE_BYTES;
+    // resident CTAs the register budget targets (about 100 registers a thread:
+    // four CTAs of 160 threads for N = 2560; a few spills cost less than the
+    // latency a fourth CTA hides)
+    static constexpr int MINB = (65536 / (NT * 100)) > 1 ? 65536 / (NT * 100) : 1;
 };
 
 __device__ __forceinline__ unsigned smem_u32(const void *p) {
@@ -469,7 +472,7 @@ __device__ __forceinline__ void qpass(ulonglong2 *buf, const float *stage, const
             Dft<R, -DIR>::run(v[q]);
         }
     }
-    if constexpr (MODE != 1) __syncthreads();   // every read of the pass precedes every write
+    if constexpr (MODE != 1 || QCfg<N>::STAGED) __syncthreads();   // every read of the pass precedes every write
 #pragma unroll
     for (int q = 0; q < GPT; ++q) {
         const int g = q * NT + tid;
@@ -523,15 +526,15 @@ __device__ __forceinline__ void inverse_passes(ulonglong2 *buf, const float *sta
 }
 
 // One unit (QPC quads) per CTA. When the rows are staged, the CTA first
-// copies its raw rows to shared memory with cp.async, so every load of the
-// unit is in flight at once without holding registers. (A persistent loop
+// copies its raw rows into its shared memory with cp.async, so every load of
+// the unit is in flight at once without holding registers. (A persistent loop
 // that prefetched the next unit spilled: the compiler kept the transform's
 // loop-invariant constants live across iterations.)
 template <int N>
 __global__ void __launch_bounds__(QCfg<N>::NT, QCfg<N>::MINB) ramp_filter_quad(QArgs a) {
     extern __shared__ ulonglong2 qbuf[];
     using Cfg = QCfg<N>;
-    float *stage = reinterpret_cast<float *>(reinterpret_cast<unsigned char *>(qbuf) + Cfg::BUF_BYTES);
+    float *stage = reinterpret_cast<float *>(qbuf);   // aliases the transform buffer
     const long long row0 = (long long)blockIdx.x * 4LL * Cfg::QPC;
     if constexpr (Cfg::STAGED) {
         stage_rows<N>(stage, a, row0);
