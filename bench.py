@@ -42,6 +42,12 @@ def parse_args(argv=None):
     ap.add_argument("--op", choices=["fdk", "fp", "ls"], default="fdk",
                     help="fdk: filter + back-projection (the benchmark); fp: matched forward projection "
                          "of the workload's volume(s); ls: least-squares iterations (differentiable workload)")
+    ap.add_argument("--grid", nargs="*", default=None,
+                    help="time back-projection alone on the paper's problems P1..P10 (all when empty); "
+                         "one JSON line per problem")
+    ap.add_argument("--depth-sweep", nargs="*", type=int, default=None,
+                    help="time the back-projection of the workload at these pipeline depths "
+                         "(views in flight, default 1 2 3 4 6 8); one JSON line per depth")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args(argv)
@@ -237,6 +243,121 @@ def run_op(args):
     ctx.close()
 
 
+def run_grid(args):
+    """The paper's problem grid: back-projection alone (no filter), per problem
+    the device-resident time and the time including the host-to-device copy of
+    the projections from pinned memory (the volume stays on the device), the
+    two ways the paper reports its CPU and GPU results."""
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2104_13248_gb300 import api, inputs
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    labels = args.grid or list(inputs.PROBLEMS)
+    stream = torch.cuda.current_stream()
+    for label in labels:
+        g = inputs.paper_problem(label, views=args.views or 512)
+        ctx = api.bp_create(g)
+        gen = torch.Generator(device="cuda").manual_seed(5)
+        q = torch.rand(ctx.proj_shape(), device="cuda", generator=gen)
+        vol = torch.empty(ctx.vol_shape(), device="cuda")
+        host = torch.empty(q.shape, dtype=torch.float32, pin_memory=True)
+        host.copy_(q)
+        scale = math.pi / g["np"]
+        U = float(g["nx"]) * g["ny"] * g["nz"] * g["np"]
+
+        def timed(fn):
+            for _ in range(args.warmup):
+                fn()
+            torch.cuda.synchronize()
+            ms = []
+            for _ in range(args.steps):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                fn()
+                b.record(stream)
+                b.synchronize()
+                ms.append(a.elapsed_time(b))
+            return statistics.median(ms)
+
+        ms_dev = timed(lambda: api.bp_backproject(ctx, q, vol=vol, scale=scale))
+
+        def with_h2d():
+            q.copy_(host, non_blocking=True)
+            api.bp_backproject(ctx, q, vol=vol, scale=scale)
+
+        ms_h2d = timed(with_h2d)
+        api.bp_device_status(ctx)
+        print(json.dumps({
+            "metric": "bp_gups", "problem": label, "value": U / (ms_dev * 1e-3) / 1e9, "unit": "GUPS",
+            "ms": ms_dev, "with_h2d": {"value": U / (ms_h2d * 1e-3) / 1e9, "ms": ms_h2d,
+                                       "h2d_bytes": host.numel() * 4},
+            "steps": args.steps, "warmup": args.warmup, "dtype": "f32", "data": "synthetic (uniform)",
+            "config": {"detector": f"{g['nu']}x{g['nv']}", "views": g["np"],
+                       "volume": f"{g['nx']}^3", "volume_gb": U / g["np"] * 4 / 1e9,
+                       "plan": api.bp_get_plan(ctx)}}), flush=True)
+        del q, vol, host
+        ctx.close()
+        torch.cuda.empty_cache()
+
+
+def run_depth_sweep(args):
+    """Back-projection alone at several staging depths (views in flight), FP32
+    and FP16 storage: the GPU analogue of the paper's view-batch experiment
+    (Section 4.3), where the batch is the number of views prefetched ahead of
+    the voxel updates."""
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2104_13248_gb300 import _lib, api, inputs
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    g = inputs.preset(args.workload)["geom"]
+    if args.views:
+        g = inputs.scaled_geom(g, np=args.views)
+    ctx = api.bp_create(g)
+    gen = torch.Generator(device="cuda").manual_seed(5)
+    q32 = torch.rand(ctx.proj_shape(), device="cuda", generator=gen)
+    q16 = q32.half()
+    vol = torch.empty(ctx.vol_shape(), device="cuda")
+    scale = math.pi / g["np"]
+    U = float(g["nx"]) * g["ny"] * g["nz"] * g["np"]
+    stream = torch.cuda.current_stream()
+
+    def timed(q):
+        for _ in range(args.warmup):
+            api.bp_backproject(ctx, q, vol=vol, scale=scale)
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(args.steps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            api.bp_backproject(ctx, q, vol=vol, scale=scale)
+            b.record(stream)
+            b.synchronize()
+            ms.append(a.elapsed_time(b))
+        return statistics.median(ms)
+
+    for depth in (args.depth_sweep or [1, 2, 3, 4, 6, 8]):
+        try:
+            api.bp_set_pipeline_depth(ctx, depth)
+        except _lib.BPError as e:
+            print(json.dumps({"metric": "bp_gups", "workload": args.workload, "stages": depth,
+                              "skipped": str(e)}), flush=True)
+            continue
+        ms32, ms16 = timed(q32), timed(q16)
+        api.bp_device_status(ctx)
+        print(json.dumps({"metric": "bp_gups", "workload": args.workload, "stages": depth,
+                          "value": U / (ms32 * 1e-3) / 1e9, "unit": "GUPS", "ms": ms32,
+                          "fp16_storage": {"value": U / (ms16 * 1e-3) / 1e9, "ms": ms16},
+                          "steps": args.steps, "warmup": args.warmup, "plan": api.bp_get_plan(ctx)}),
+              flush=True)
+    ctx.close()
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -409,6 +530,10 @@ def main(argv=None):
     args = parse_args(argv)
     if args.impl == "reference":
         run_reference(args)
+    elif args.grid is not None:
+        run_grid(args)
+    elif args.depth_sweep is not None:
+        run_depth_sweep(args)
     elif args.op != "fdk":
         run_op(args)
     else:

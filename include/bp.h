@@ -179,19 +179,29 @@ bp_status bp_device_status(bp_ctx *ctx, void *stream);
  *                      (32 or 64) and, for 32, the CTAs per SM the kernel's
  *                      register budget targets (2 or 3); re-derives the
  *                      staged box sizes.
+ *   bp_set_pipeline_depth
+ *                      views the staging producer of the back-projector keeps
+ *                      in flight (1..8, default 4; BP_ERR_INVALID_ARG when the
+ *                      boxes of that many views exceed shared memory). When
+ *                      the default does not fit, the plan lowers it (to 2 at
+ *                      least) before falling back to direct global loads. The
+ *                      GPU counterpart of the paper's view batching and
+ *                      prefetching depth (Section 3.1.3, Algorithm 2).
  *   bp_set_timeout     limit of every bounded wait inside the kernels
  *                      (seconds, (0, 60]; default 2).
  *   bp_test_drop_view  test hook: the staging producer skips the load of
  *                      this view (-1 = off), so the consumers' bounded wait
  *                      runs out and bp_device_status reports BP_ERR_TIMEOUT.
- *   bp_get_plan        the launch plan: voxels per thread along z and the
- *                      staged box (FP32 width, FP16 width, rows); a width of
- *                      -1 means that element type uses direct global loads.
+ *   bp_get_plan        the launch plan: voxels per thread along z, the
+ *                      staged box (FP32 width, FP16 width, rows; a width of
+ *                      -1 means that element type uses direct global loads)
+ *                      and the pipeline depth in use. Any pointer may be NULL.
  */
 bp_status bp_set_tuning(bp_ctx *ctx, int tk, int ctas_per_sm);
+bp_status bp_set_pipeline_depth(bp_ctx *ctx, int stages);
 bp_status bp_set_timeout(bp_ctx *ctx, double seconds);
 bp_status bp_test_drop_view(bp_ctx *ctx, int view);
-bp_status bp_get_plan(const bp_ctx *ctx, int *tk, int *bu32, int *bu16, int *bv);
+bp_status bp_get_plan(const bp_ctx *ctx, int *tk, int *bu32, int *bu16, int *bv, int *stages);
 
 /* Message of the last failed call on ctx (never NULL; "" after success).
  * With ctx == NULL: the last failure of bp_create* in this thread. */

@@ -136,14 +136,19 @@ def bp_get_matrices(ctx: Context) -> np.ndarray:
 
 
 def bp_get_plan(ctx: Context) -> dict:
-    v = [ctypes.c_int() for _ in range(4)]
+    v = [ctypes.c_int() for _ in range(5)]
     check(_lib.load().bp_get_plan(ctx.handle, *[ctypes.byref(x) for x in v]), ctx.handle)
-    return dict(tk=v[0].value, bu32=v[1].value, bu16=v[2].value, bv=v[3].value)
+    return dict(tk=v[0].value, bu32=v[1].value, bu16=v[2].value, bv=v[3].value, stages=v[4].value)
 
 
 def bp_set_tuning(ctx: Context, tk: int = 32, ctas_per_sm: int = 2) -> None:
     """Back-projector variant: voxels per thread along z and target CTAs per SM."""
     check(_lib.load().bp_set_tuning(ctx.handle, int(tk), int(ctas_per_sm)), ctx.handle)
+
+
+def bp_set_pipeline_depth(ctx: Context, stages: int) -> None:
+    """Views the back-projector's staging producer keeps in flight (1..8)."""
+    check(_lib.load().bp_set_pipeline_depth(ctx.handle, int(stages)), ctx.handle)
 
 
 def bp_set_timeout(ctx: Context, seconds: float) -> None:
@@ -302,5 +307,5 @@ def fdk(ctx: Context, proj: torch.Tensor, out_dtype: torch.dtype = torch.float32
 
 __all__ = ["Context", "BPError", "HostPipeline", "bp_filter_views", "bp_create", "bp_create_from_matrices", "bp_destroy", "bp_filter",
            "bp_backproject", "bp_backproject_views", "fp_project", "bp_phantom_project",
-           "bp_get_matrices", "bp_get_plan", "bp_set_tuning", "bp_set_timeout",
+           "bp_get_matrices", "bp_get_plan", "bp_set_tuning", "bp_set_pipeline_depth", "bp_set_timeout",
            "bp_test_drop_view", "bp_device_status", "fdk"]

@@ -134,11 +134,18 @@ void max_footprint(const bp_ctx *ctx, int tx, int ty, int tk, int align, int *bu
     *bv = *std::max_element(mv.begin(), mv.end());
 }
 
+// Shared memory of the staged back-projector: view records, 2 x 8 barrier
+// slots, then one box per stage (each rounded up to 128 bytes).
+static int tma_smem_bytes(int bu, int bv, int elem_bytes, int stages) {
+    const int base = (256 * 48 + 2 * 8 * 8 + 127) / 128 * 128;
+    return base + stages * ((bu * bv * elem_bytes + 127) / 128 * 128);
+}
+
 static void make_plan(bp_ctx *ctx) {
     Plan &pl = ctx->plan;
     pl.tx = 32;
     pl.ty = 8;
-    pl.stages = 4;
+    if (ctx->stages_req < 1 || ctx->stages_req > 8) ctx->stages_req = 4;
     if (pl.tk != 64) pl.tk = 32;
     if (pl.ctas != 3) pl.ctas = 2;
     if (!ctx->zinv) {
@@ -152,12 +159,13 @@ static void make_plan(bp_ctx *ctx) {
     pl.bu = plan_box_width(bu32, 4);
     pl.bu16 = plan_box_width(bu16, 2);
     pl.bv = std::max(bv32, bv16);
-    // shared memory budget of the TMA kernel (records + barriers + 4 stages)
-    const int rec = 256 * 48 + 2 * 4 * 8;
-    const int base = (rec + 127) / 128 * 128;
-    auto fits = [&](int bu, int es) { return bu > 0 && base + 4 * ((bu * pl.bv * es + 127) / 128 * 128) <= 227 * 1024; };
-    if (pl.bv > 256 || !fits(pl.bu, 4)) pl.bu = -1;
-    if (pl.bv > 256 || !fits(pl.bu16, 2)) pl.bu16 = -1;
+    // shared memory budget of the TMA kernel (records + barriers + the stages):
+    // the requested depth, lowered (to 2 at least) until the FP32 boxes fit
+    auto fits = [&](int bu, int es, int st) { return bu > 0 && tma_smem_bytes(bu, pl.bv, es, st) <= 227 * 1024; };
+    pl.stages = ctx->stages_req;
+    while (pl.stages > 2 && !fits(pl.bu, 4, pl.stages)) --pl.stages;
+    if (pl.bv > 256 || !fits(pl.bu, 4, pl.stages)) pl.bu = -1;
+    if (pl.bv > 256 || !fits(pl.bu16, 2, pl.stages)) pl.bu16 = -1;
     // forward projector: per-warp boxes of an 8 x 4 column patch, 32 voxels deep
     // (+1 column and row of slack for the FP32 corner rounding)
     int wbu, wbv;
@@ -450,6 +458,19 @@ bp_status bp_set_tuning(bp_ctx *ctx, int tk, int ctas_per_sm) {
     return BP_OK;
 }
 
+bp_status bp_set_pipeline_depth(bp_ctx *ctx, int stages) {
+    if (!ctx) return fail(nullptr, BP_ERR_INVALID_ARG, "bp_set_pipeline_depth: NULL context");
+    if (stages < 1 || stages > 8)
+        return fail(ctx, BP_ERR_INVALID_ARG, "bp_set_pipeline_depth: stages must be in [1, 8]");
+    const Plan &pl = ctx->plan;
+    if ((pl.bu > 0 && tma_smem_bytes(pl.bu, pl.bv, 4, stages) > 227 * 1024) ||
+        (pl.bu16 > 0 && tma_smem_bytes(pl.bu16, pl.bv, 2, stages) > 227 * 1024))
+        return fail(ctx, BP_ERR_INVALID_ARG, "bp_set_pipeline_depth: the staged boxes do not fit in shared memory");
+    ctx->stages_req = stages;
+    make_plan(ctx);
+    return BP_OK;
+}
+
 bp_status bp_set_timeout(bp_ctx *ctx, double seconds) {
     if (!ctx) return fail(nullptr, BP_ERR_INVALID_ARG, "bp_set_timeout: NULL context");
     if (!(seconds > 0.0 && seconds <= 60.0)) return fail(ctx, BP_ERR_INVALID_ARG, "bp_set_timeout: (0, 60] seconds");
@@ -463,12 +484,13 @@ bp_status bp_test_drop_view(bp_ctx *ctx, int view) {
     return BP_OK;
 }
 
-bp_status bp_get_plan(const bp_ctx *ctx, int *tk, int *bu32, int *bu16, int *bv) {
+bp_status bp_get_plan(const bp_ctx *ctx, int *tk, int *bu32, int *bu16, int *bv, int *stages) {
     if (!ctx) return fail(nullptr, BP_ERR_INVALID_ARG, "bp_get_plan: NULL context");
     if (tk) *tk = ctx->plan.tk;
     if (bu32) *bu32 = ctx->plan.bu;
     if (bu16) *bu16 = ctx->plan.bu16;
     if (bv) *bv = ctx->plan.bv;
+    if (stages) *stages = ctx->plan.stages;
     return BP_OK;
 }
 

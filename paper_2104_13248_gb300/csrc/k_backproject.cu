@@ -24,7 +24,7 @@ namespace bp {
 
 constexpr int kTX = 32;      // tile columns along x (4 warps x 8)
 constexpr int kTY = 8;       // tile columns along y (2 warps x 4)
-constexpr int kStages = 4;   // views in flight
+constexpr int kMaxStages = 8;   // barrier slots; the views in flight (plan.stages) are <= this
 constexpr int kConsumers = kTX * kTY;
 constexpr int kConsumerWarps = kConsumers / 32;
 constexpr int kThreads = kConsumers + 32;   // + producer warp
@@ -38,7 +38,7 @@ __host__ __device__ constexpr int stage_bytes(int bu, int bv) {
 
 constexpr int kRecBytes = kRecChunk * (int)sizeof(ViewRec);
 constexpr int kBarOffset = kRecBytes;
-constexpr int kStageOffset = align_up(kRecBytes + 2 * kStages * 8, 128);
+constexpr int kStageOffset = align_up(kRecBytes + 2 * kMaxStages * 8, 128);
 
 // Thread -> column within the CTA tile: each warp owns an 8 x 4 patch.
 __device__ __forceinline__ void consumer_column(int warp, int lane, int *di, int *dj) {
@@ -179,11 +179,11 @@ __global__ void __launch_bounds__(kThreads, MB)
 bp_zcol_tma(const __grid_constant__ CUtensorMap tmap, const double *__restrict__ P, int view0,
             int nviews, int nx, int ny, int nz, int bv, int align, float *__restrict__ vol,
             float scale, int accumulate, unsigned *err, unsigned long long timeout_ns,
-            int drop_view) {
+            int drop_view, int nst) {
     extern __shared__ __align__(128) unsigned char smem[];
     ViewRec *recs = reinterpret_cast<ViewRec *>(smem);
     unsigned long long *full = reinterpret_cast<unsigned long long *>(smem + kBarOffset);
-    unsigned long long *empty = full + kStages;
+    unsigned long long *empty = full + kMaxStages;
     unsigned char *stages = smem + kStageOffset;
     const int sbytes = stage_bytes<T>(BU, bv);
     const unsigned box_bytes = (unsigned)(BU * bv * sizeof(T));
@@ -201,7 +201,7 @@ bp_zcol_tma(const __grid_constant__ CUtensorMap tmap, const double *__restrict__
     const float fdi = (float)di, fdj = (float)dj;
 
     if (tid == 0) {
-        for (int s = 0; s < kStages; ++s) {
+        for (int s = 0; s < nst; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], kConsumerWarps);
         }
@@ -219,10 +219,13 @@ bp_zcol_tma(const __grid_constant__ CUtensorMap tmap, const double *__restrict__
 #pragma unroll
     for (int kk = 0; kk < (kPairs ? 1 : TK); ++kk) acc[kk] = 0.0f;
 
-    __shared__ unsigned arms[kStages];   // producer: armings of each full barrier
-    if (tid < kStages) arms[tid] = 0;
+    __shared__ unsigned arms[kMaxStages];   // producer: armings of each full barrier
+    if (tid < kMaxStages) arms[tid] = 0;
     bool alive = true;
-    unsigned g0 = 0;                     // pipeline iterations before this chunk
+    // pipeline position of the current view g: slot g % nst, phase (g / nst) & 1,
+    // advanced per view (no division)
+    int slot = 0;
+    unsigned phase = 0, g = 0;
     for (int cb = 0; cb < nviews; cb += kRecChunk) {
         const int cn = min(kRecChunk, nviews - cb);
         __syncthreads();
@@ -234,28 +237,28 @@ bp_zcol_tma(const __grid_constant__ CUtensorMap tmap, const double *__restrict__
         if (warp == kConsumerWarps) {
             // ---- producer: one elected lane issues the TMA loads ----
             if (lane == 0 && alive) {
-                for (int n = 0; n < cn; ++n) {
-                    unsigned g = g0 + n;
-                    int slot = g % kStages;
-                    if (g >= kStages &&
-                        !mbar_wait_bounded(&empty[slot], ((g / kStages) - 1) & 1, timeout_ns)) {
+                for (int n = 0; n < cn; ++n, ++g) {
+                    if (g >= (unsigned)nst && !mbar_wait_bounded(&empty[slot], phase ^ 1u, timeout_ns)) {
                         atomicOr(err, DEV_ERR_TIMEOUT);
                         alive = false;
                         break;
                     }
-                    if (view0 + cb + n == drop_view) continue;   // test hook
-                    mbar_arrive_expect_tx(&full[slot], box_bytes);
-                    tma_load_4d(stages + slot * sbytes, &tmap, recs[n].u_box, recs[n].v_box,
-                                cb + n, b, &full[slot]);
-                    ++arms[slot];
+                    if (view0 + cb + n != drop_view) {   // test hook: skip this view's load
+                        mbar_arrive_expect_tx(&full[slot], box_bytes);
+                        tma_load_4d(stages + slot * sbytes, &tmap, recs[n].u_box, recs[n].v_box,
+                                    cb + n, b, &full[slot]);
+                        ++arms[slot];
+                    }
+                    if (++slot == nst) {
+                        slot = 0;
+                        phase ^= 1u;
+                    }
                 }
             }
         } else {
             // ---- consumers ----
             for (int n = 0; n < cn && alive; ++n) {
-                unsigned g = g0 + n;
-                int slot = g % kStages;
-                if (!mbar_wait_bounded(&full[slot], (g / kStages) & 1, timeout_ns)) {
+                if (!mbar_wait_bounded(&full[slot], phase, timeout_ns)) {
                     if (lane == 0) atomicOr(err, DEV_ERR_TIMEOUT);
                     alive = false;
                     break;
@@ -283,13 +286,16 @@ bp_zcol_tma(const __grid_constant__ CUtensorMap tmap, const double *__restrict__
                 }
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&empty[slot]);
+                if (++slot == nst) {
+                    slot = 0;
+                    phase ^= 1u;
+                }
             }
         }
-        g0 += cn;
     }
     if (warp == kConsumerWarps && lane == 0) {
         // drain: every issued load must have landed before the CTA exits
-        for (int s = 0; s < kStages; ++s)
+        for (int s = 0; s < nst; ++s)
             if (arms[s] > 0 && !mbar_wait_bounded(&full[s], (arms[s] - 1) & 1, timeout_ns))
                 atomicOr(err, DEV_ERR_TIMEOUT);
     }
@@ -478,7 +484,8 @@ template <typename T, int TK, int BU, int MB>
 static cudaError_t launch_tma_t(const CUtensorMap &map, bp_ctx *ctx, int view0, int nviews,
                                 int bv, int align, float *vol, int batch, float scale,
                                 int accumulate, cudaStream_t st) {
-    const int smem = kStageOffset + kStages * stage_bytes<T>(BU, bv);
+    const int nst = ctx->plan.stages;
+    const int smem = kStageOffset + nst * stage_bytes<T>(BU, bv);
     auto kern = bp_zcol_tma<T, TK, BU, MB>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
@@ -486,7 +493,7 @@ static cudaError_t launch_tma_t(const CUtensorMap &map, bp_ctx *ctx, int view0, 
               batch);
     kern<<<grid, kThreads, smem, st>>>(map, ctx->d_P, view0, nviews, ctx->nx, ctx->ny, ctx->nz, bv,
                                        align, vol, scale, accumulate, ctx->d_err, ctx->timeout_ns,
-                                       ctx->test_drop_view);
+                                       ctx->test_drop_view, nst);
     return cudaGetLastError();
 }
 

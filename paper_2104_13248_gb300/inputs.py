@@ -94,6 +94,25 @@ PRESETS = {
 }
 
 
+# The paper's problem grid (Section 4, table of problem sizes): square
+# detectors of 256, 512 or 1024 pixels, 512 views over 360 deg, volumes of
+# 256^3, 512^3, 1024^3 and 1300^3. The paper gives no geometry for them; these
+# keep the source distances of the workloads above, a 204.8 mm detector and a
+# 128 mm volume (the footprint of the 512^2 / 256^3 workload).
+PROBLEMS = {
+    "P1": (256, 256), "P2": (256, 512), "P3": (256, 1024),
+    "P4": (512, 256), "P5": (512, 512), "P6": (512, 1024),
+    "P7": (1024, 256), "P8": (1024, 512), "P9": (1024, 1024),
+    "P10": (1024, 1300),
+}
+
+
+def paper_problem(label: str, views: int = 512) -> dict:
+    """Geometry of problem ``label`` (detector n x n, volume m^3, 512 views)."""
+    n, m = PROBLEMS[label]
+    return _geom(views, n, n, 204.8 / n, 204.8 / n, m, 128.0 / m)
+
+
 def preset(name: str) -> dict:
     p = PRESETS[name]
     out = dict(p)

@@ -77,6 +77,7 @@ def test_null_arguments(lib):
     assert lib.bp_backproject(None, None, 0, None, 1, 1.0, 0, None) == _lib.BP_ERR_INVALID_ARG
     assert lib.fp_project(None, None, None, 1, 1.0, None) == _lib.BP_ERR_INVALID_ARG
     assert lib.bp_get_matrices(None, None) == _lib.BP_ERR_INVALID_ARG
+    assert lib.bp_set_pipeline_depth(None, 4) == _lib.BP_ERR_INVALID_ARG
     lib.bp_destroy(None)   # NULL-safe
 
 
