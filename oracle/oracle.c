@@ -415,6 +415,94 @@ void orc_siddon(double sid, double sdd, int np, const double *angles, int nu,
 }
 
 /* Number of OpenMP threads the routines above use (1 without OpenMP). */
+/* ------------------------------------------------------------------ */
+/* Iterative reconstruction on the projector pair (Section 1 names     */
+/* MLEM and SART as the methods that call back-projection repeatedly)   */
+/* ------------------------------------------------------------------ */
+
+/* Views of subset t (of nsub): s = t, t + nsub, t + 2 nsub, ... Their
+ * matrices and projections are gathered into compact arrays. */
+static int subset_views(int np, int nsub, int t, const double *P, const double *proj,
+                        long plane, double *Pt, double *pt)
+{
+    int n = 0;
+    for (int s = t; s < np; s += nsub, ++n) {
+        memcpy(Pt + 12 * n, P + 12 * s, 12 * sizeof(double));
+        if (proj) memcpy(pt + plane * n, proj + plane * s, plane * sizeof(double));
+    }
+    return n;
+}
+
+/* MLEM (Shepp and Vardi) with ordered subsets of views (Hudson and Larkin;
+ * nsub = 1 is plain MLEM). A is the voxel-driven forward projector with
+ * scale 1, A^T the back-projector. Per subset t:
+ *   y = A_t x;  r_i = p_i / y_i where y_i > eps, else 0;
+ *   x_j <- x_j (A_t^T r)_j / (A_t^T 1)_j where (A_t^T 1)_j > eps, else x_j.
+ * iters passes over all subsets; x holds the start value on entry. */
+void orc_mlem(const double *P, int np, const double *proj, int nu, int nv, int nx,
+              int ny, int nz, int nsub, int iters, double eps, double *x)
+{
+    const long plane = (long)nu * nv, nvox = (long)nx * ny * nz;
+    const int nmax = (np + nsub - 1) / nsub;
+    double *Pt = malloc(sizeof(double) * 12 * nmax);
+    double *pt = malloc(sizeof(double) * plane * nmax);
+    double *y = malloc(sizeof(double) * plane * nmax);
+    double *ones = malloc(sizeof(double) * plane * nmax);
+    double *b = malloc(sizeof(double) * nvox);
+    double *sens = malloc(sizeof(double) * nvox);
+    for (long i = 0; i < plane * nmax; ++i) ones[i] = 1.0;
+    for (int it = 0; it < iters; ++it) {
+        for (int t = 0; t < nsub; ++t) {
+            const int n = subset_views(np, nsub, t, P, proj, plane, Pt, pt);
+            orc_backproject(Pt, n, ones, nu, nv, nx, ny, nz, 1.0, sens);
+            orc_forward_project(Pt, n, x, nx, ny, nz, 1.0, nu, nv, y);
+            for (long i = 0; i < plane * n; ++i) y[i] = (y[i] > eps) ? pt[i] / y[i] : 0.0;
+            orc_backproject(Pt, n, y, nu, nv, nx, ny, nz, 1.0, b);
+            for (long j = 0; j < nvox; ++j)
+                if (sens[j] > eps) x[j] = x[j] * b[j] / sens[j];
+        }
+    }
+    free(Pt); free(pt); free(y); free(ones); free(b); free(sens);
+}
+
+/* SART (Andersen and Kak) in block form over the same view subsets (nsub = 1
+ * is the simultaneous version, SIRT). Per subset t:
+ *   y = A_t x;  r_i = (p_i - y_i) / (A_t 1)_i where (A_t 1)_i > eps, else 0;
+ *   x_j <- x_j + lambda (A_t^T r)_j / (A_t^T 1)_j where (A_t^T 1)_j > eps;
+ *   then x_j <- max(x_j, 0) when nonneg. */
+void orc_sart(const double *P, int np, const double *proj, int nu, int nv, int nx,
+              int ny, int nz, int nsub, int iters, double lambda, int nonneg,
+              double eps, double *x)
+{
+    const long plane = (long)nu * nv, nvox = (long)nx * ny * nz;
+    const int nmax = (np + nsub - 1) / nsub;
+    double *Pt = malloc(sizeof(double) * 12 * nmax);
+    double *pt = malloc(sizeof(double) * plane * nmax);
+    double *y = malloc(sizeof(double) * plane * nmax);
+    double *ray = malloc(sizeof(double) * plane * nmax);
+    double *ones_p = malloc(sizeof(double) * plane * nmax);
+    double *ones_v = malloc(sizeof(double) * nvox);
+    double *b = malloc(sizeof(double) * nvox);
+    double *sens = malloc(sizeof(double) * nvox);
+    for (long i = 0; i < plane * nmax; ++i) ones_p[i] = 1.0;
+    for (long j = 0; j < nvox; ++j) ones_v[j] = 1.0;
+    for (int it = 0; it < iters; ++it) {
+        for (int t = 0; t < nsub; ++t) {
+            const int n = subset_views(np, nsub, t, P, proj, plane, Pt, pt);
+            orc_backproject(Pt, n, ones_p, nu, nv, nx, ny, nz, 1.0, sens);
+            orc_forward_project(Pt, n, ones_v, nx, ny, nz, 1.0, nu, nv, ray);
+            orc_forward_project(Pt, n, x, nx, ny, nz, 1.0, nu, nv, y);
+            for (long i = 0; i < plane * n; ++i) y[i] = (ray[i] > eps) ? (pt[i] - y[i]) / ray[i] : 0.0;
+            orc_backproject(Pt, n, y, nu, nv, nx, ny, nz, 1.0, b);
+            for (long j = 0; j < nvox; ++j) {
+                if (sens[j] > eps) x[j] += lambda * b[j] / sens[j];
+                if (nonneg && x[j] < 0.0) x[j] = 0.0;
+            }
+        }
+    }
+    free(Pt); free(pt); free(y); free(ray); free(ones_p); free(ones_v); free(b); free(sens);
+}
+
 int orc_num_threads(void)
 {
 #ifdef _OPENMP

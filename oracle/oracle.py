@@ -177,6 +177,35 @@ def forward_project(P, vol, nu, nv, scale=1.0) -> np.ndarray:
     return proj
 
 
+def mlem(P, proj, nx, ny, nz, iters, subsets=1, x0=None, eps=1e-9) -> np.ndarray:
+    """MLEM / ordered-subset EM on the projector pair (scale 1); see orc_mlem."""
+    lib = _load()
+    P = _f64(P)
+    q = _f64(proj)
+    n_views, nv, nu = q.shape
+    x = np.ones((nz, ny, nx)) if x0 is None else np.array(x0, dtype=np.float64, copy=True)
+    x = np.ascontiguousarray(x)
+    lib.orc_mlem(_dp(P), ctypes.c_int(n_views), _dp(q), ctypes.c_int(nu), ctypes.c_int(nv),
+                 ctypes.c_int(nx), ctypes.c_int(ny), ctypes.c_int(nz), ctypes.c_int(subsets),
+                 ctypes.c_int(iters), ctypes.c_double(eps), _dp(x))
+    return x
+
+
+def sart(P, proj, nx, ny, nz, iters, subsets=1, lam=1.0, nonneg=False, x0=None, eps=1e-9) -> np.ndarray:
+    """Block SART over view subsets (SIRT for one subset); see orc_sart."""
+    lib = _load()
+    P = _f64(P)
+    q = _f64(proj)
+    n_views, nv, nu = q.shape
+    x = np.zeros((nz, ny, nx)) if x0 is None else np.array(x0, dtype=np.float64, copy=True)
+    x = np.ascontiguousarray(x)
+    lib.orc_sart(_dp(P), ctypes.c_int(n_views), _dp(q), ctypes.c_int(nu), ctypes.c_int(nv),
+                 ctypes.c_int(nx), ctypes.c_int(ny), ctypes.c_int(nz), ctypes.c_int(subsets),
+                 ctypes.c_int(iters), ctypes.c_double(lam), ctypes.c_int(1 if nonneg else 0),
+                 ctypes.c_double(eps), _dp(x))
+    return x
+
+
 def ramp_filter(g, proj) -> np.ndarray:
     """Cosine weight + Ram-Lak, direct linear convolution along u (double)."""
     lib = _load()

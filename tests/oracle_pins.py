@@ -25,6 +25,11 @@ What pins what:
   conv_vs_scipy           3x3x3 convolution vs scipy.ndimage.correlate per channel pair
   conv_adjoints           <conv(x), dy> = <x, dgrad(dy)> and the weight gradient as the
                           derivative of that pairing in w (linearity check)
+  mlem_counts             EM count preservation: sum (A^T 1) x+ = sum of p over rays with Ax > 0
+  mlem_likelihood         EM never decreases the Poisson log-likelihood
+  iter_fixed_points       the true volume is a fixed point of MLEM and SART on consistent data
+  sart_constant_step      one SART or MLEM step maps a constant start to a constant volume's value
+  iter_convergence        MLEM, OS-EM, SIRT and SART reach the true volume of a full-rank system
 """
 import numpy as np
 
@@ -407,6 +412,84 @@ def conv_adjoints():
     assert abs(lhs - np.vdot(b2, db)) < 1e-9 * max(1.0, abs(lhs))
 
 
+def _iter_system():
+    """A small system with full column rank (60 voxels, 8 views of 12 x 10
+    pixels, the whole volume in view): consistent data from a positive volume."""
+    g = dict(sid=300.0, sdd=450.0, np=8, angles=np.linspace(0.1, 2 * np.pi, 8, endpoint=False), nu=12,
+             nv=10, du=1.5, dv=1.5, u_off=0.3, v_off=-0.2, nx=5, ny=4, nz=3, sx=2.0, sy=2.0, sz=2.0,
+             ox=0.2, oy=-0.1, oz=0.1)
+    P = oracle.matrices(g)
+    rng = np.random.default_rng(3)
+    xt = rng.uniform(0.5, 1.5, size=(g["nz"], g["ny"], g["nx"]))
+    p = oracle.forward_project(P, xt, g["nu"], g["nv"], 1.0)
+    return g, P, xt, p, rng
+
+
+def mlem_counts():
+    # EM preserves counts: after x+ = x A^T(p / Ax) / A^T 1, sum_j (A^T 1)_j x+_j
+    # = sum of p over the rays with Ax > 0 (a property of the update, any x > 0)
+    g, P, xt, p, rng = _iter_system()
+    pn = p * (1 + 0.2 * rng.uniform(-1, 1, size=p.shape))
+    x0 = rng.uniform(0.2, 2.0, size=xt.shape)
+    x1 = oracle.mlem(P, pn, g["nx"], g["ny"], g["nz"], iters=1, x0=x0)
+    sens = oracle.backproject(P, np.ones_like(p), g["nx"], g["ny"], g["nz"], 1.0)
+    y0 = oracle.forward_project(P, x0, g["nu"], g["nv"], 1.0)
+    lhs, rhs = (sens * x1).sum(), pn[y0 > 1e-9].sum()
+    assert abs(lhs - rhs) <= 1e-12 * rhs, (lhs, rhs)
+    assert (x1 >= 0).all()
+
+
+def mlem_likelihood():
+    # EM never decreases the Poisson log-likelihood sum_i p_i log y_i - y_i
+    g, P, xt, p, rng = _iter_system()
+    pn = p * (1 + 0.3 * rng.uniform(-1, 1, size=p.shape))
+    x = np.ones_like(xt)
+    prev = -np.inf
+    for _ in range(8):
+        x = oracle.mlem(P, pn, g["nx"], g["ny"], g["nz"], iters=1, x0=x)
+        y = oracle.forward_project(P, x, g["nu"], g["nv"], 1.0)
+        m = y > 0
+        ll = (pn[m] * np.log(y[m]) - y[m]).sum() - y[~m].sum()
+        assert ll >= prev - 1e-9 * abs(ll), (ll, prev)
+        prev = ll
+
+
+def iter_fixed_points():
+    # consistent data: the true volume is a fixed point of MLEM and SART
+    g, P, xt, p, _ = _iter_system()
+    for nsub in (1, 3):
+        xm = oracle.mlem(P, p, g["nx"], g["ny"], g["nz"], iters=1, subsets=nsub, x0=xt)
+        xs = oracle.sart(P, p, g["nx"], g["ny"], g["nz"], iters=1, subsets=nsub, x0=xt)
+        assert np.abs(xm - xt).max() <= 1e-13 and np.abs(xs - xt).max() <= 1e-13
+
+
+def sart_constant_step():
+    # both normalisations together map constants to constants: for p = A (c' 1)
+    # every normalised residual (p_i - (A c 1)_i) / (A 1)_i equals c' - c, so one
+    # step with lambda = 1 from c 1 lands on c' 1 exactly (every subset step too)
+    g, P, xt, _, _ = _iter_system()
+    one = np.ones_like(xt)
+    p = oracle.forward_project(P, 2.5 * one, g["nu"], g["nv"], 1.0)
+    for nsub in (1, 3):
+        x = oracle.sart(P, p, g["nx"], g["ny"], g["nz"], iters=1, subsets=nsub, x0=0.7 * one)
+        assert np.abs(x - 2.5).max() <= 1e-12, nsub
+        x = oracle.mlem(P, p, g["nx"], g["ny"], g["nz"], iters=1, subsets=nsub, x0=0.7 * one)
+        assert np.abs(x - 2.5).max() <= 1e-12, nsub
+
+
+def iter_convergence():
+    # consistent data and full column rank: both methods reach the true volume
+    g, P, xt, p, _ = _iter_system()
+    n = (g["nx"], g["ny"], g["nz"])
+    assert np.abs(oracle.mlem(P, p, *n, iters=1000) - xt).max() <= 1e-10
+    assert np.abs(oracle.mlem(P, p, *n, iters=300, subsets=4) - xt).max() <= 1e-10
+    assert np.abs(oracle.sart(P, p, *n, iters=1000) - xt).max() <= 1e-10
+    assert np.abs(oracle.sart(P, p, *n, iters=300, subsets=4, nonneg=True) - xt).max() <= 1e-10
+    # and not in one step (the pins above would not see a no-op update)
+    assert np.abs(oracle.sart(P, p, *n, iters=1) - xt).max() > 1e-2
+
+
 ALL = [matrix_vs_ray, z_invariance, bp_constant, bp_linear, bp_fp_hat_matrix, adjoint_dot,
        symmetry, filter_impulse, filter_frequency, phantom_sphere, phantom_ray_integral,
-       phantom_siddon, fdk_sphere, fdk_offcentre, fdk_ellipsoids, conv_vs_scipy, conv_adjoints]
+       phantom_siddon, fdk_sphere, fdk_offcentre, fdk_ellipsoids, conv_vs_scipy, conv_adjoints,
+       mlem_counts, mlem_likelihood, iter_fixed_points, sart_constant_step, iter_convergence]

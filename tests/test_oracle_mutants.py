@@ -48,6 +48,10 @@ MUTANTS = [
     ("conv_dgrad_transposed_w", "acc += w[((long)co * 27 + t) * cin + ci] * gp[co];", "acc += w[((long)co * 27 + (26 - t)) * cin + ci] * gp[co];"),
     ("conv_wgrad_bias_sum", "for (long v = 0; v < (long)N * D * H * W; ++v) bsum += dy[v * cout + co];", "for (long v = 1; v < (long)N * D * H * W; ++v) bsum += dy[v * cout + co];"),
     ("phantom_chord_half", "if (disc > 0.0) sum += E[15] * sqrt(disc) / A * L;", "if (disc > 0.0) sum += E[15] * sqrt(disc) / (2.0 * A) * L;"),
+    ("mlem_no_sensitivity", "if (sens[j] > eps) x[j] = x[j] * b[j] / sens[j];", "if (sens[j] > eps) x[j] = x[j] * b[j];"),
+    ("mlem_ratio_inverted", "y[i] = (y[i] > eps) ? pt[i] / y[i] : 0.0;", "y[i] = (y[i] > eps) ? y[i] / pt[i] : 0.0;"),
+    ("sart_no_ray_norm", "(pt[i] - y[i]) / ray[i] : 0.0;", "(pt[i] - y[i]) : 0.0;"),
+    ("sart_sign", "if (sens[j] > eps) x[j] += lambda * b[j] / sens[j];", "if (sens[j] > eps) x[j] -= lambda * b[j] / sens[j];"),
 ]
 
 
