@@ -39,7 +39,8 @@ def parse_args(argv=None):
     ap.add_argument("--tk", type=int, default=0, help="voxels per thread along z (32/64; 0 = plan)")
     ap.add_argument("--ctas", type=int, default=2, help="CTAs per SM the TK=32 back-projector targets")
     ap.add_argument("--views", type=int, default=0, help="override the number of views (profiling runs)")
-    ap.add_argument("--op", choices=["fdk", "fp", "ls"], default="fdk",
+    ap.add_argument("--subsets", type=int, default=0, help="view subsets of --op mlem / sart (0 = 1 / 10)")
+    ap.add_argument("--op", choices=["fdk", "fp", "ls", "mlem", "sart"], default="fdk",
                     help="fdk: filter + back-projection (the benchmark); fp: matched forward projection "
                          "of the workload's volume(s); ls: least-squares iterations (differentiable workload)")
     ap.add_argument("--grid", nargs="*", default=None,
@@ -215,10 +216,26 @@ def run_op(args):
     gen = torch.Generator(device="cuda").manual_seed(0)
     x = torch.rand((batch,) + ctx.vol_shape(), device="cuda", generator=gen)
     proj = torch.empty_like(raws)
+    sub = None
     if args.op == "fp":
         def step():
             api.fp_project(ctx, x, proj=proj)
         upd, unit_desc = U, "forward-projection"
+    elif args.op in ("mlem", "sart"):
+        from paper_2104_13248_gb300 import iterative
+        nsub = args.subsets or (1 if args.op == "mlem" else 10)
+        sub = iterative.Subsets(ctx, nsub, need_rays=args.op == "sart")
+        state = {"x": x[0].clone()}
+
+        def step():
+            if args.op == "mlem":
+                state["x"] = iterative.mlem(ctx, raws[0], iters=1, x0=state["x"], sub=sub)
+            else:
+                state["x"] = iterative.sart(ctx, raws[0], iters=1, x0=state["x"], sub=sub, nonneg=True)
+        U = U / batch
+        upd = 2 * U
+        unit_desc = (f"one {args.op.upper()} pass over {nsub} view subset(s): a forward and a back-projection "
+                     f"of every view plus the element-wise steps (batch 1)")
     else:
         L = autograd.lipschitz(ctx, iters=5)
 
@@ -239,7 +256,10 @@ def run_op(args):
     print(json.dumps({"metric": f"{args.op}_gups", "value": upd / (ms * 1e-3) / 1e9, "unit": "GUPS",
                       "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
                       "higher_is_better": True, "dtype": "f32", "data": "synthetic",
-                      "config": {"workload": args.workload, "batch": batch, "step": unit_desc}}), flush=True)
+                      "config": {"workload": args.workload, "batch": 1 if sub else batch, "step": unit_desc}}),
+          flush=True)
+    if sub is not None:
+        sub.close()
     ctx.close()
 
 

@@ -1,4 +1,4 @@
-"""ctypes binding of libbp.so (declarations of include/bp.h).
+"""ctypes binding of libbp.so (declarations of include/bp.h, unet.h and iter.h).
 
 Argument marshalling only: every computation runs in the CUDA library. The
 library is loaded from paper_2104_13248_gb300/_build/libbp.so; a missing or
@@ -75,6 +75,12 @@ PROTOTYPES = {
     "cnn_pack_input": (_i, [_vp, _vp, _i, _ll, _vp]),
     "cnn_mse": (_i, [_vp, _vp, _vp, _vp, _ll, _vp]),
     "cnn_adam": (_i, [_vp, _vp, _vp, _vp, _vp, _ll, _f, _f, _f, _f, _i, _vp]),
+    # include/iter.h
+    "it_fill": (_i, [_vp, _ll, _f, _vp]),
+    "it_ratio": (_i, [_vp, _vp, _vp, _ll, _f, _vp]),
+    "it_residual": (_i, [_vp, _vp, _vp, _vp, _ll, _f, _vp]),
+    "it_mlem_update": (_i, [_vp, _vp, _vp, _ll, _f, _vp]),
+    "it_sart_update": (_i, [_vp, _vp, _vp, _ll, _f, _i, _f, _vp]),
 }
 
 

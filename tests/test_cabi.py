@@ -78,6 +78,12 @@ def test_null_arguments(lib):
     assert lib.fp_project(None, None, None, 1, 1.0, None) == _lib.BP_ERR_INVALID_ARG
     assert lib.bp_get_matrices(None, None) == _lib.BP_ERR_INVALID_ARG
     assert lib.bp_set_pipeline_depth(None, 4) == _lib.BP_ERR_INVALID_ARG
+    assert lib.it_fill(None, 5, 1.0, None) == _lib.BP_ERR_INVALID_ARG
+    assert lib.it_ratio(None, None, None, -1, 0.0, None) == _lib.BP_ERR_INVALID_ARG
+    assert lib.it_residual(None, None, None, None, 3, 0.0, None) == _lib.BP_ERR_INVALID_ARG
+    assert lib.it_mlem_update(None, None, None, 2, 0.0, None) == _lib.BP_ERR_INVALID_ARG
+    assert lib.it_sart_update(None, None, None, 2, 1.0, 0, 0.0, None) == _lib.BP_ERR_INVALID_ARG
+    assert lib.it_fill(None, 0, 1.0, None) == _lib.BP_OK   # empty: nothing to do, no launch
     lib.bp_destroy(None)   # NULL-safe
 
 
