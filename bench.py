@@ -49,6 +49,8 @@ def parse_args(argv=None):
     ap.add_argument("--depth-sweep", nargs="*", type=int, default=None,
                     help="time the back-projection of the workload at these pipeline depths "
                          "(views in flight, default 1 2 3 4 6 8); one JSON line per depth")
+    ap.add_argument("--no-sym", action="store_true",
+                    help="FP32 back-projection without the mid-plane symmetry (Section 3.1.2)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args(argv)
@@ -280,6 +282,8 @@ def run_grid(args):
     for label in labels:
         g = inputs.paper_problem(label, views=args.views or 512)
         ctx = api.bp_create(g)
+        if args.no_sym:
+            api.bp_set_symmetry(ctx, False)
         gen = torch.Generator(device="cuda").manual_seed(5)
         q = torch.rand(ctx.proj_shape(), device="cuda", generator=gen)
         vol = torch.empty(ctx.vol_shape(), device="cuda")
@@ -413,6 +417,8 @@ def run_ours(args):
     ctx = api.bp_create(g)
     if args.tk or args.ctas != 2:
         api.bp_set_tuning(ctx, args.tk or 32, args.ctas)
+    if args.no_sym:
+        api.bp_set_symmetry(ctx, False)
     plan = api.bp_get_plan(ctx)
     E = inputs.random_ellipsoids(p["seed"] + 7919 * rank, p["n_ell"], p["axes"], g)
     raw = api.bp_phantom_project(ctx, E)
@@ -467,7 +473,7 @@ def run_ours(args):
     peak_gups = n_sm * UPD_PER_CLK_SM * sm_mhz * 1e6 / 1e9
     achieved = U / (bp_ms_max * 1e-3) / 1e9
     traffic = None
-    tp = os.path.join(ROOT, "profiles", "bp_zcol_tma_c3_traffic.json")
+    tp = os.path.join(ROOT, "profiles", "bp_c3_traffic.json")
     if os.path.exists(tp) and args.workload == "c3_paper" and not args.views:
         try:
             rec = json.load(open(tp))

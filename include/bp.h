@@ -187,6 +187,15 @@ bp_status bp_device_status(bp_ctx *ctx, void *stream);
  *                      least) before falling back to direct global loads. The
  *                      GPU counterpart of the paper's view batching and
  *                      prefetching depth (Section 3.1.3, Algorithm 2).
+ *   bp_set_symmetry    FP32 back-projection with the mid-plane symmetry of
+ *                      Section 3.1.2 / Algorithm 1: a thread owns voxels k
+ *                      and nz-1-k and computes v, its floor and fraction
+ *                      once for both. 1 (default): used whenever
+ *                      v(nz-1-k) = nv-1-v(k) holds for the context's matrices
+ *                      (v_off = 0, volume centred on the central plane) and
+ *                      the boxes fit shared memory; asking for it explicitly
+ *                      on other matrices returns BP_ERR_UNSUPPORTED (and
+ *                      leaves it off). 0: always the plain z-column kernel.
  *   bp_set_timeout     limit of every bounded wait inside the kernels
  *                      (seconds, (0, 60]; default 2).
  *   bp_test_drop_view  test hook: the staging producer skips the load of
@@ -194,14 +203,17 @@ bp_status bp_device_status(bp_ctx *ctx, void *stream);
  *                      runs out and bp_device_status reports BP_ERR_TIMEOUT.
  *   bp_get_plan        the launch plan: voxels per thread along z, the
  *                      staged box (FP32 width, FP16 width, rows; a width of
- *                      -1 means that element type uses direct global loads)
- *                      and the pipeline depth in use. Any pointer may be NULL.
+ *                      -1 means that element type uses direct global loads),
+ *                      the pipeline depth in use and whether FP32 calls use
+ *                      the mid-plane symmetry. Any pointer may be NULL.
  */
 bp_status bp_set_tuning(bp_ctx *ctx, int tk, int ctas_per_sm);
 bp_status bp_set_pipeline_depth(bp_ctx *ctx, int stages);
+bp_status bp_set_symmetry(bp_ctx *ctx, int enable);
 bp_status bp_set_timeout(bp_ctx *ctx, double seconds);
 bp_status bp_test_drop_view(bp_ctx *ctx, int view);
-bp_status bp_get_plan(const bp_ctx *ctx, int *tk, int *bu32, int *bu16, int *bv, int *stages);
+bp_status bp_get_plan(const bp_ctx *ctx, int *tk, int *bu32, int *bu16, int *bv, int *stages,
+                      int *symmetric);
 
 /* Message of the last failed call on ctx (never NULL; "" after success).
  * With ctx == NULL: the last failure of bp_create* in this thread. */

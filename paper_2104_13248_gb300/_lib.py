@@ -55,9 +55,10 @@ PROTOTYPES = {
     "bp_device_status": (_i, [_vp, _vp]),
     "bp_set_tuning": (_i, [_vp, _i, _i]),
     "bp_set_pipeline_depth": (_i, [_vp, _i]),
+    "bp_set_symmetry": (_i, [_vp, _i]),
     "bp_set_timeout": (_i, [_vp, _d]),
     "bp_test_drop_view": (_i, [_vp, _i]),
-    "bp_get_plan": (_i, [_vp, _iptr, _iptr, _iptr, _iptr, _iptr]),
+    "bp_get_plan": (_i, [_vp, _iptr, _iptr, _iptr, _iptr, _iptr, _iptr]),
     "bp_last_error": (ctypes.c_char_p, [_vp]),
     "bp_destroy": (None, [_vp]),
     # unet.h

@@ -136,9 +136,10 @@ def bp_get_matrices(ctx: Context) -> np.ndarray:
 
 
 def bp_get_plan(ctx: Context) -> dict:
-    v = [ctypes.c_int() for _ in range(5)]
+    v = [ctypes.c_int() for _ in range(6)]
     check(_lib.load().bp_get_plan(ctx.handle, *[ctypes.byref(x) for x in v]), ctx.handle)
-    return dict(tk=v[0].value, bu32=v[1].value, bu16=v[2].value, bv=v[3].value, stages=v[4].value)
+    return dict(tk=v[0].value, bu32=v[1].value, bu16=v[2].value, bv=v[3].value, stages=v[4].value,
+                symmetric=bool(v[5].value))
 
 
 def bp_set_tuning(ctx: Context, tk: int = 32, ctas_per_sm: int = 2) -> None:
@@ -149,6 +150,13 @@ def bp_set_tuning(ctx: Context, tk: int = 32, ctas_per_sm: int = 2) -> None:
 def bp_set_pipeline_depth(ctx: Context, stages: int) -> None:
     """Views the back-projector's staging producer keeps in flight (1..8)."""
     check(_lib.load().bp_set_pipeline_depth(ctx.handle, int(stages)), ctx.handle)
+
+
+def bp_set_symmetry(ctx: Context, enable: bool = True) -> None:
+    """Allow (default) or forbid the mid-plane symmetry of FP32 back-projection;
+    enabling raises BPError when the geometry is not mirror-symmetric about
+    the central slice."""
+    check(_lib.load().bp_set_symmetry(ctx.handle, 1 if enable else 0), ctx.handle)
 
 
 def bp_set_timeout(ctx: Context, seconds: float) -> None:
@@ -307,5 +315,5 @@ def fdk(ctx: Context, proj: torch.Tensor, out_dtype: torch.dtype = torch.float32
 
 __all__ = ["Context", "BPError", "HostPipeline", "bp_filter_views", "bp_create", "bp_create_from_matrices", "bp_destroy", "bp_filter",
            "bp_backproject", "bp_backproject_views", "fp_project", "bp_phantom_project",
-           "bp_get_matrices", "bp_get_plan", "bp_set_tuning", "bp_set_pipeline_depth", "bp_set_timeout",
+           "bp_get_matrices", "bp_get_plan", "bp_set_tuning", "bp_set_pipeline_depth", "bp_set_symmetry", "bp_set_timeout",
            "bp_test_drop_view", "bp_device_status", "fdk"]

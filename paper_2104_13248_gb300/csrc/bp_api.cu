@@ -141,6 +141,22 @@ static int tma_smem_bytes(int bu, int bv, int elem_bytes, int stages) {
     return base + stages * ((bu * bv * elem_bytes + 127) / 128 * 128);
 }
 
+// Mid-plane symmetry of the matrices (Section 3.1.2): v(i, j, nz-1-k) =
+// nv-1 - v(i, j, k) for every voxel and view. With u and w independent of k
+// this holds iff 2 P[1][0] = (nv-1) P[2][0], 2 P[1][1] = (nv-1) P[2][1] and
+// 2 P[1][3] + (nz-1) P[1][2] = (nv-1) P[2][3]; checked to 1e-10 relative.
+static bool mirror_symmetric(const bp_ctx *ctx) {
+    if (!ctx->zinv) return false;
+    const double a = ctx->nv - 1.0, c = ctx->nz - 1.0;
+    auto close = [](double x, double y) { return std::fabs(x - y) <= 1e-10 * (std::fabs(x) + std::fabs(y) + 1e-300); };
+    for (int s = 0; s < ctx->n_views; ++s) {
+        const double *p = &ctx->P[12 * (size_t)s];
+        if (!close(2.0 * p[4], a * p[8]) || !close(2.0 * p[5], a * p[9]) || !close(2.0 * p[7] + c * p[6], a * p[11]))
+            return false;
+    }
+    return true;
+}
+
 static void make_plan(bp_ctx *ctx) {
     Plan &pl = ctx->plan;
     pl.tx = 32;
@@ -166,6 +182,17 @@ static void make_plan(bp_ctx *ctx) {
     while (pl.stages > 2 && !fits(pl.bu, 4, pl.stages)) --pl.stages;
     if (pl.bv > 256 || !fits(pl.bu, 4, pl.stages)) pl.bu = -1;
     if (pl.bv > 256 || !fits(pl.bu16, 2, pl.stages)) pl.bu16 = -1;
+    // mid-plane symmetry: boxes of 16-voxel half columns, two per stage
+    pl.sym_bu = pl.sym_bv = -1;
+    if (ctx->sym_enable && pl.bu > 0 && mirror_symmetric(ctx)) {
+        int sbu, sbv;
+        max_footprint(ctx, pl.tx, pl.ty, 16, 4, &sbu, &sbv);
+        sbu = plan_box_width(sbu, 4);
+        if (sbu > 0 && sbv <= 256 && tma_smem_bytes(sbu, sbv, 4, 2 * pl.stages) <= 227 * 1024) {
+            pl.sym_bu = sbu;
+            pl.sym_bv = sbv;
+        }
+    }
     // forward projector: per-warp boxes of an 8 x 4 column patch, 32 voxels deep
     // (+1 column and row of slack for the FP32 corner rounding)
     int wbu, wbv;
@@ -471,6 +498,20 @@ bp_status bp_set_pipeline_depth(bp_ctx *ctx, int stages) {
     return BP_OK;
 }
 
+bp_status bp_set_symmetry(bp_ctx *ctx, int enable) {
+    if (!ctx) return fail(nullptr, BP_ERR_INVALID_ARG, "bp_set_symmetry: NULL context");
+    ctx->sym_enable = enable != 0;
+    make_plan(ctx);
+    if (enable && ctx->plan.sym_bu <= 0) {
+        ctx->sym_enable = 0;
+        make_plan(ctx);
+        return fail(ctx, BP_ERR_UNSUPPORTED,
+                    "bp_set_symmetry: the matrices are not mirror-symmetric about the central slice, "
+                    "or the staged boxes do not fit");
+    }
+    return BP_OK;
+}
+
 bp_status bp_set_timeout(bp_ctx *ctx, double seconds) {
     if (!ctx) return fail(nullptr, BP_ERR_INVALID_ARG, "bp_set_timeout: NULL context");
     if (!(seconds > 0.0 && seconds <= 60.0)) return fail(ctx, BP_ERR_INVALID_ARG, "bp_set_timeout: (0, 60] seconds");
@@ -484,13 +525,15 @@ bp_status bp_test_drop_view(bp_ctx *ctx, int view) {
     return BP_OK;
 }
 
-bp_status bp_get_plan(const bp_ctx *ctx, int *tk, int *bu32, int *bu16, int *bv, int *stages) {
+bp_status bp_get_plan(const bp_ctx *ctx, int *tk, int *bu32, int *bu16, int *bv, int *stages,
+                      int *symmetric) {
     if (!ctx) return fail(nullptr, BP_ERR_INVALID_ARG, "bp_get_plan: NULL context");
     if (tk) *tk = ctx->plan.tk;
     if (bu32) *bu32 = ctx->plan.bu;
     if (bu16) *bu16 = ctx->plan.bu16;
     if (bv) *bv = ctx->plan.bv;
     if (stages) *stages = ctx->plan.stages;
+    if (symmetric) *symmetric = ctx->plan.sym_bu > 0;
     return BP_OK;
 }
 

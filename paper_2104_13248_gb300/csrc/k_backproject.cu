@@ -174,6 +174,95 @@ __device__ __forceinline__ void store_column(float *__restrict__ vol, const floa
     }
 }
 
+// ---------------------------------------------------------------------------
+// Mid-plane symmetry (Section 3.1.2, Algorithm 1). When the detector rows and
+// the volume slices are centred on the same plane, v(nz-1-k) = nv-1-v(k)
+// while u and w do not depend on k. A thread then owns kTH lower voxels of
+// its column and their mirrors: v, its floor and fraction are computed once
+// for both. The producer stages the lower box (rows vb .. vb+BV-1) and its
+// vertical mirror (rows nv-vb-BV .. nv-1-vb); a lower voxel whose taps are
+// box rows r, r+1 with fraction f has its mirror's taps at rows BV-1-r and
+// BV-2-r of the mirrored box, weighted 1-f and f.
+// ---------------------------------------------------------------------------
+constexpr int kTH = 16;   // lower voxels per thread
+
+template <int BU>
+__device__ __forceinline__ void accumulate_sym_pairs(const float *__restrict__ lo,
+                                                     const float *__restrict__ hi_top, const ColView &c,
+                                                     f2 *acc_lo, f2 *acc_hi) {
+    // lo = lower box + c.cu; hi_top = mirrored box + (BV-1)*BU + c.cu
+    const f2 M2 = pk(kMagic, kMagic), FU = pk(c.fu, c.fu), WT = pk(c.wt, c.wt);
+#pragma unroll
+    for (int m = 0; m < kTH / 2; ++m) {
+        const float va = fmaf((float)(2 * m), c.dv, c.v0);
+        const float vb = fmaf((float)(2 * m + 1), c.dv, c.v0);
+        const f2 V = pk(va, vb);
+        const f2 TV = add2_rd(V, M2);
+        const f2 FV = sub2(V, sub2(TV, M2));
+        float ta, tb;
+        upk(TV, ta, tb);
+        const int ra = __float_as_int(ta) - kMagicBits, rb = __float_as_int(tb) - kMagicBits;
+        const float *pa = lo + ra * BU, *pb = lo + rb * BU;
+        const f2 Q00 = pk(pa[0], pb[0]), Q01 = pk(pa[1], pb[1]);
+        const f2 Q10 = pk(pa[BU], pb[BU]), Q11 = pk(pa[BU + 1], pb[BU + 1]);
+        const f2 S0 = fma2(FU, sub2(Q01, Q00), Q00);
+        const f2 S1 = fma2(FU, sub2(Q11, Q10), Q10);
+        acc_lo[m] = fma2(WT, fma2(FV, sub2(S1, S0), S0), acc_lo[m]);
+        // mirror: row BV-1-r (weight 1-f) and the row above it, BV-2-r (weight f)
+        const float *qa = hi_top - ra * BU, *qb = hi_top - rb * BU;
+        const f2 R00 = pk(qa[0], qb[0]), R01 = pk(qa[1], qb[1]);
+        const f2 R10 = pk(qa[-BU], qb[-BU]), R11 = pk(qa[1 - BU], qb[1 - BU]);
+        const f2 T0 = fma2(FU, sub2(R01, R00), R00);
+        const f2 T1 = fma2(FU, sub2(R11, R10), R10);
+        acc_hi[m] = fma2(WT, fma2(FV, sub2(T1, T0), T0), acc_hi[m]);
+    }
+}
+
+template <int BU>
+__device__ __forceinline__ void accumulate_sym_scalar(const float *__restrict__ lo,
+                                                      const float *__restrict__ hi_top, const ColView &c,
+                                                      int ez, float *acc_lo, float *acc_hi) {
+#pragma unroll
+    for (int kk = 0; kk < kTH; ++kk) {
+        if (kk >= ez) continue;
+        const float v = fmaf((float)kk, c.dv, c.v0);
+        const float tv = __fadd_rd(v, kMagic);
+        const float fv = v - (tv - kMagic);
+        const int row = __float_as_int(tv) - kMagicBits;
+        const float *p = lo + row * BU;
+        const float s0 = fmaf(c.fu, p[1] - p[0], p[0]);
+        const float s1 = fmaf(c.fu, p[BU + 1] - p[BU], p[BU]);
+        acc_lo[kk] = fmaf(c.wt, fmaf(fv, s1 - s0, s0), acc_lo[kk]);
+        const float *q = hi_top - row * BU;
+        const float t0 = fmaf(c.fu, q[1] - q[0], q[0]);
+        const float t1 = fmaf(c.fu, q[1 - BU] - q[-BU], q[-BU]);
+        acc_hi[kk] = fmaf(c.wt, fmaf(fv, t1 - t0, t0), acc_hi[kk]);
+    }
+}
+
+// Lower voxels k0 .. k0+ez-1 and, for k < nz/2, their mirrors nz-1-k (the
+// middle slice of an odd nz is its own mirror and is written once).
+__device__ __forceinline__ void store_sym(float *__restrict__ vol, const float *lo, const float *hi, int b,
+                                          int i, int j, int k0, int ez, int nx, int ny, int nz, float scale,
+                                          int accumulate) {
+    const size_t plane = (size_t)nx * ny;
+    const size_t col = (size_t)b * nz * plane + (size_t)j * nx + i;
+#pragma unroll
+    for (int kk = 0; kk < kTH; ++kk) {
+        if (kk < ez) {
+            const int k = k0 + kk;
+            const size_t a = col + (size_t)k * plane;
+            const float r = scale * lo[kk];
+            vol[a] = accumulate ? vol[a] + r : r;
+            if (k < nz / 2) {
+                const size_t m = col + (size_t)(nz - 1 - k) * plane;
+                const float rm = scale * hi[kk];
+                vol[m] = accumulate ? vol[m] + rm : rm;
+            }
+        }
+    }
+}
+
 template <typename T, int TK, int BU, int MB>
 __global__ void __launch_bounds__(kThreads, MB)
 bp_zcol_tma(const __grid_constant__ CUtensorMap tmap, const double *__restrict__ P, int view0,
@@ -308,6 +397,140 @@ bp_zcol_tma(const __grid_constant__ CUtensorMap tmap, const double *__restrict__
         } else {
             store_column<TK>(vol, acc, b, i0 + di, j0 + dj, k0, ez, nx, ny, nz, scale, accumulate);
         }
+    }
+}
+
+// The staged z-column kernel with mid-plane symmetry (FP32 projections): z
+// block y covers lower slices [16y, 16y+16) of the (nz+1)/2 lower slices and
+// their mirrors; each stage holds the lower box and the mirrored box. The
+// pipeline, bounded waits and drain are those of bp_zcol_tma.
+template <int BU, int MB>
+__global__ void __launch_bounds__(kThreads, MB)
+bp_zsym_tma(const __grid_constant__ CUtensorMap tmap, const double *__restrict__ P, int view0,
+            int nviews, int nx, int ny, int nz, int nv, int bv, int align, float *__restrict__ vol,
+            float scale, int accumulate, unsigned *err, unsigned long long timeout_ns, int drop_view,
+            int nst) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    ViewRec *recs = reinterpret_cast<ViewRec *>(smem);
+    unsigned long long *full = reinterpret_cast<unsigned long long *>(smem + kBarOffset);
+    unsigned long long *empty = full + kMaxStages;
+    unsigned char *stages = smem + kStageOffset;
+    const unsigned box_bytes = (unsigned)(BU * bv * sizeof(float));
+    const int half = stage_bytes<float>(BU, bv);   // offset of the mirrored box in a stage
+    const int sbytes = 2 * half;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int ntx = (nx + kTX - 1) / kTX;
+    const int i0 = (blockIdx.x % ntx) * kTX, j0 = (blockIdx.x / ntx) * kTY;
+    const int nlow = (nz + 1) / 2;
+    const int k0 = blockIdx.y * kTH;
+    const int b = blockIdx.z;
+    const int ex = min(kTX, nx - i0), ey = min(kTY, ny - j0), ez = min(kTH, nlow - k0);
+
+    int di = 0, dj = 0;
+    if (warp < kConsumerWarps) consumer_column(warp, lane, &di, &dj);
+    const bool col_ok = warp < kConsumerWarps && di < ex && dj < ey;
+    const float fdi = (float)di, fdj = (float)dj;
+
+    if (tid == 0) {
+        for (int s = 0; s < nst; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], kConsumerWarps);
+        }
+        fence_barrier_init();
+        prefetch_tmap(&tmap);
+    }
+    __syncthreads();
+
+    f2 acc_lo[kTH / 2], acc_hi[kTH / 2];
+#pragma unroll
+    for (int m = 0; m < kTH / 2; ++m) acc_lo[m] = acc_hi[m] = 0ull;
+
+    __shared__ unsigned arms[kMaxStages];
+    if (tid < kMaxStages) arms[tid] = 0;
+    bool alive = true;
+    int slot = 0;
+    unsigned phase = 0, g = 0;
+    for (int cb = 0; cb < nviews; cb += kRecChunk) {
+        const int cn = min(kRecChunk, nviews - cb);
+        __syncthreads();
+        for (int n = tid; n < cn; n += kThreads)
+            if (!make_rec(P + 12 * (size_t)(view0 + cb + n), i0, j0, k0, ex, ey, ez, align, BU, bv, &recs[n]))
+                atomicOr(err, DEV_ERR_FOOTPRINT);
+        __syncthreads();
+        if (warp == kConsumerWarps) {
+            if (lane == 0 && alive) {
+                for (int n = 0; n < cn; ++n, ++g) {
+                    if (g >= (unsigned)nst && !mbar_wait_bounded(&empty[slot], phase ^ 1u, timeout_ns)) {
+                        atomicOr(err, DEV_ERR_TIMEOUT);
+                        alive = false;
+                        break;
+                    }
+                    if (view0 + cb + n != drop_view) {   // test hook: skip this view's loads
+                        mbar_arrive_expect_tx(&full[slot], 2 * box_bytes);
+                        unsigned char *st = stages + slot * sbytes;
+                        tma_load_4d(st, &tmap, recs[n].u_box, recs[n].v_box, cb + n, b, &full[slot]);
+                        tma_load_4d(st + half, &tmap, recs[n].u_box, nv - recs[n].v_box - bv, cb + n, b,
+                                    &full[slot]);
+                        ++arms[slot];
+                    }
+                    if (++slot == nst) {
+                        slot = 0;
+                        phase ^= 1u;
+                    }
+                }
+            }
+        } else {
+            for (int n = 0; n < cn && alive; ++n) {
+                if (!mbar_wait_bounded(&full[slot], phase, timeout_ns)) {
+                    if (lane == 0) atomicOr(err, DEV_ERR_TIMEOUT);
+                    alive = false;
+                    break;
+                }
+                ColView cv;
+                if (col_ok && column_view<BU>(recs[n], fdi, fdj, ez, bv, err, cv)) {
+                    const float *lo = reinterpret_cast<const float *>(stages + slot * sbytes) + cv.cu;
+                    const float *hi_top = reinterpret_cast<const float *>(stages + slot * sbytes + half) +
+                                          (bv - 1) * BU + cv.cu;
+                    if (ez == kTH) {
+                        accumulate_sym_pairs<BU>(lo, hi_top, cv, acc_lo, acc_hi);
+                    } else {
+                        float tl[kTH], th[kTH];
+#pragma unroll
+                        for (int m = 0; m < kTH / 2; ++m) {
+                            upk(acc_lo[m], tl[2 * m], tl[2 * m + 1]);
+                            upk(acc_hi[m], th[2 * m], th[2 * m + 1]);
+                        }
+                        accumulate_sym_scalar<BU>(lo, hi_top, cv, ez, tl, th);
+#pragma unroll
+                        for (int m = 0; m < kTH / 2; ++m) {
+                            acc_lo[m] = pk(tl[2 * m], tl[2 * m + 1]);
+                            acc_hi[m] = pk(th[2 * m], th[2 * m + 1]);
+                        }
+                    }
+                }
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&empty[slot]);
+                if (++slot == nst) {
+                    slot = 0;
+                    phase ^= 1u;
+                }
+            }
+        }
+    }
+    if (warp == kConsumerWarps && lane == 0) {
+        for (int s = 0; s < nst; ++s)
+            if (arms[s] > 0 && !mbar_wait_bounded(&full[s], (arms[s] - 1) & 1, timeout_ns))
+                atomicOr(err, DEV_ERR_TIMEOUT);
+    }
+    if (col_ok && alive) {
+        float lo[kTH], hi[kTH];
+#pragma unroll
+        for (int m = 0; m < kTH / 2; ++m) {
+            upk(acc_lo[m], lo[2 * m], lo[2 * m + 1]);
+            upk(acc_hi[m], hi[2 * m], hi[2 * m + 1]);
+        }
+        store_sym(vol, lo, hi, b, i0 + di, j0 + dj, k0, ez, nx, ny, nz, scale, accumulate);
     }
 }
 
@@ -518,6 +741,34 @@ static cudaError_t launch_tma_bu(const CUtensorMap &map, bp_ctx *ctx, int bu, in
 #undef BP_TMA_CASE
 }
 
+template <int BU>
+static cudaError_t launch_sym_t(const CUtensorMap &map, bp_ctx *ctx, int view0, int nviews, int bv,
+                                float *vol, int batch, float scale, int accumulate, cudaStream_t st) {
+    const int nst = ctx->plan.stages;
+    const int smem = kStageOffset + nst * 2 * stage_bytes<float>(BU, bv);
+    auto kern = bp_zsym_tma<BU, 2>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid(((ctx->nx + kTX - 1) / kTX) * ((ctx->ny + kTY - 1) / kTY), ((ctx->nz + 1) / 2 + kTH - 1) / kTH,
+              batch);
+    kern<<<grid, kThreads, smem, st>>>(map, ctx->d_P, view0, nviews, ctx->nx, ctx->ny, ctx->nz, ctx->nv, bv, 4,
+                                       vol, scale, accumulate, ctx->d_err, ctx->timeout_ns, ctx->test_drop_view,
+                                       nst);
+    return cudaGetLastError();
+}
+
+static cudaError_t launch_sym(const CUtensorMap &map, bp_ctx *ctx, int bu, int view0, int nviews, int bv,
+                              float *vol, int batch, float scale, int accumulate, cudaStream_t st) {
+#define BP_SYM_CASE(W) \
+    case W: return launch_sym_t<W>(map, ctx, view0, nviews, bv, vol, batch, scale, accumulate, st);
+    switch (bu) {
+        BP_SYM_CASE(48) BP_SYM_CASE(80) BP_SYM_CASE(112) BP_SYM_CASE(144) BP_SYM_CASE(176)
+        BP_SYM_CASE(208) BP_SYM_CASE(240)
+        default: return cudaErrorInvalidValue;
+    }
+#undef BP_SYM_CASE
+}
+
 bp_status launch_backproject(bp_ctx *ctx, const void *proj, bp_dtype t, int view0, int nviews,
                              long long batch_stride, float *vol, int batch, float scale,
                              int accumulate, cudaStream_t st) {
@@ -537,25 +788,31 @@ bp_status launch_backproject(bp_ctx *ctx, const void *proj, bp_dtype t, int view
         return e == cudaSuccess ? BP_OK : cuda_fail(ctx, e, "bp_voxel_gen launch");
     }
     const Plan &pl = ctx->plan;
-    const int bu = (t == BP_F16) ? pl.bu16 : pl.bu;
+    const bool sym = t == BP_F32 && pl.sym_bu > 0;
+    const int bu = sym ? pl.sym_bu : (t == BP_F16) ? pl.bu16 : pl.bu;
+    const int bv = sym ? pl.sym_bv : pl.bv;
     const int align = (t == BP_F16) ? 8 : 4;
     PFN_encodeTiled enc = get_encode();
     bool tma = enc != nullptr && bu > 0 && (((size_t)ctx->nu * es) % 16 == 0) &&
                (((uintptr_t)proj) % 16 == 0) && ((batch_stride * es) % 16 == 0) &&
-               pl.bv <= 256 && bu <= 256;
+               bv <= 256 && bu <= 256;
     if (tma) {
         CUtensorMap map;
         cuuint64_t dims[4] = {(cuuint64_t)ctx->nu, (cuuint64_t)ctx->nv, (cuuint64_t)nviews,
                               (cuuint64_t)batch};
         cuuint64_t strides[3] = {(cuuint64_t)(ctx->nu * es), (cuuint64_t)(view_elems * es),
                                  (cuuint64_t)(batch_stride * es)};
-        cuuint32_t box[4] = {(cuuint32_t)bu, (cuuint32_t)pl.bv, 1, 1};
+        cuuint32_t box[4] = {(cuuint32_t)bu, (cuuint32_t)bv, 1, 1};
         cuuint32_t estr[4] = {1, 1, 1, 1};
         CUresult r = enc(&map, t == BP_F16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
                          4, const_cast<void *>(proj), dims, strides, box, estr,
                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (r != CUDA_SUCCESS) tma = false;
+        if (tma && sym) {
+            e = launch_sym(map, ctx, bu, view0, nviews, bv, vol, batch, scale, accumulate, st);
+            return e == cudaSuccess ? BP_OK : cuda_fail(ctx, e, "bp_zsym_tma launch");
+        }
         if (tma) {
             // variants: (voxels per thread along z, CTAs per SM the registers target)
             if (t == BP_F16) {

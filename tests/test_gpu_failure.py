@@ -28,12 +28,17 @@ def _built():
     __graft_entry__.build()
 
 
-def test_dropped_view_times_out_and_context_survives():
+@pytest.mark.parametrize("sym", [True, False])
+def test_dropped_view_times_out_and_context_survives(sym):
+    """Both staged kernels: the mid-plane symmetric one (default for this
+    centred geometry) and the plain z-column kernel."""
     g = inputs.preset("c1_small")["geom"]
     q = torch.from_numpy(inputs.uniform_array(11, (g["np"], g["nv"], g["nu"]), -1.0, 1.0)).float().cuda()
     scale = math.pi / g["np"]
     with api.bp_create(g) as ctx:
+        api.bp_set_symmetry(ctx, sym)
         plan = api.bp_get_plan(ctx)
+        assert plan["symmetric"] == sym
         if plan["bu32"] < 0:
             pytest.skip("the staged (TMA) kernel is not used for this geometry")
         ref = api.bp_backproject(ctx, q, scale=scale)

@@ -225,11 +225,14 @@ def _band(P, g, k0, nks):
     return r0, r1 - r0
 
 
-@pytest.mark.parametrize("name,k0,nks", [("c2_fdk256", 112, 32), ("c3_paper", 224, 64)])
-def test_full_size_slab(name, k0, nks):
+@pytest.mark.parametrize("name,k0,nks,sym", [("c2_fdk256", 112, 32, True), ("c3_paper", 224, 64, True),
+                                             ("c3_paper", 224, 64, False)])
+def test_full_size_slab(name, k0, nks, sym):
     """Oracle inputs on the detector band a z-slab sees; the GPU back-projects
-    the whole volume in the benchmark's configuration; the slab is compared
-    voxel by voxel (FP32 and FP16-stored projections)."""
+    the whole volume in the benchmark's configuration (mid-plane symmetry on,
+    the default for these centred geometries) and with the plain z-column
+    kernel; the slab is compared voxel by voxel (FP32 and FP16-stored
+    projections)."""
     p = inputs.preset(name)
     g = p["geom"]
     P = oracle.matrices(g)
@@ -242,6 +245,9 @@ def test_full_size_slab(name, k0, nks):
     scale = math.pi / g["np"]
     ref = oracle.backproject_slab(P, q, g["nx"], g["ny"], k0, nks, scale)
     with api.bp_create(g) as ctx:
+        if not sym:
+            api.bp_set_symmetry(ctx, False)
+        assert api.bp_get_plan(ctx)["symmetric"] == sym
         d = torch.from_numpy(q).cuda()
         vol = api.bp_backproject(ctx, d, scale=scale)
         slab = vol[k0:k0 + nks].cpu().numpy()
