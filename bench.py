@@ -489,7 +489,7 @@ def run_ours(args):
         host_proj = torch.empty(raw.shape, dtype=torch.float32, pin_memory=True)
         host_proj.copy_(raw)
         host_vol = torch.empty(ctx.vol_shape(), dtype=torch.float32, pin_memory=True)
-        pipe = api.HostPipeline(ctx, chunks=8)
+        pipe = api.HostPipeline(ctx)
         for _ in range(args.warmup):
             pipe.run(host_proj, host_vol)
         torch.cuda.synchronize()

@@ -274,14 +274,23 @@ class HostPipeline:
 
     Views are split into ``chunks`` blocks: block c+1 is copied on a copy
     stream while block c is filtered and back-projected (accumulating) on
-    the compute stream; the volume is copied back at the end. Device
-    buffers are allocated once, here, and reused by every call.
+    the compute stream; the volume is copied back at the end. The first
+    block is small (``first`` of the views), since nothing overlaps its copy;
+    the copy of a view is about 3x faster than its back-projection, so the
+    later, larger blocks always land before they are needed. Device buffers
+    are allocated once, here, and reused by every call.
     """
 
-    def __init__(self, ctx: Context, chunks: int = 8, dtype: torch.dtype = torch.float32):
+    def __init__(self, ctx: Context, chunks: int = 4, dtype: torch.dtype = torch.float32,
+                 first: float = 0.04):
         self.ctx = ctx
         self.chunks = max(1, min(int(chunks), ctx.n_views))
-        edges = np.linspace(0, ctx.n_views, self.chunks + 1).round().astype(int)
+        # an optional small first block (fraction ``first`` of the views) shortens
+        # the copy nothing can overlap; the rest is split evenly
+        n0 = int(round(first * ctx.n_views)) if self.chunks > 1 else 0
+        n0 = min(max(n0, 0), ctx.n_views - 1)
+        rest = np.linspace(n0, ctx.n_views, self.chunks + (0 if n0 else 1)).round().astype(int)
+        edges = ([0] if n0 else []) + list(rest)
         self.blocks = [(int(a), int(b)) for a, b in zip(edges[:-1], edges[1:]) if b > a]
         self.raw = torch.empty(ctx.proj_shape(), dtype=torch.float32, device="cuda")
         self.filt = torch.empty(ctx.proj_shape(), dtype=dtype, device="cuda")
