@@ -74,6 +74,7 @@ fp_zcol(const float *__restrict__ vol, const double *__restrict__ P, int nviews,
         }
     }
     float *pb = proj + (size_t)b * nviews * nu * nv;
+    for (int t = lane; t < wbox_n; t += 32) wbox[t] = 0.0f;   // the flush keeps it clean from here on
 
     for (int cb = 0; cb < nviews; cb += kRecChunk) {
         const int cn = min(kRecChunk, nviews - cb);
@@ -130,7 +131,6 @@ fp_zcol(const float *__restrict__ vol, const double *__restrict__ P, int nviews,
                 }
             }
             cols[tid] = c;
-            for (int t = lane; t < wbox_n; t += 32) wbox[t] = 0.0f;
             __syncwarp();
             if (any && fits) {
                 const float fl = (float)lane;
@@ -161,10 +161,24 @@ fp_zcol(const float *__restrict__ vol, const double *__restrict__ P, int nviews,
                 float *img = pb + (size_t)(cb + n) * nu * nv;
                 const int rows_used = min(wbv, (__float_as_int(__fadd_rd(vmax, kMagic)) - kMagicBits) + 2 - vo);
                 const int cols_used = min(wbu, (__float_as_int(__fadd_rd(umax, kMagic)) - kMagicBits) + 2 - uo);
-                // flattened over the used rows x columns so every lane has work
+                // flattened over the used rows x columns so every lane has work; the
+                // row is (t + 0.5) / cols rounded down in FP32 (within one of the exact
+                // quotient) and corrected by one step. Every value read is zeroed
+                // again, so the box is clean for the next view (the scatter writes
+                // only inside this region).
+                const float inv_cols = 1.0f / (float)cols_used;
                 for (int t = lane; t < rows_used * cols_used; t += 32) {
-                    const int rr = t / cols_used, ccol = t - rr * cols_used;
-                    const float val = wbox[rr * wpitch + ccol];
+                    int rr = (int)(((float)t + 0.5f) * inv_cols), ccol = t - rr * cols_used;
+                    if (ccol < 0) {
+                        --rr;
+                        ccol += cols_used;
+                    } else if (ccol >= cols_used) {
+                        ++rr;
+                        ccol -= cols_used;
+                    }
+                    float *cell = wbox + rr * wpitch + ccol;
+                    const float val = *cell;
+                    *cell = 0.0f;
                     const int r_ = r.v_box + vo + rr, c_ = r.u_box + uo + ccol;
                     if (val != 0.0f && r_ >= 0 && r_ < nv && c_ >= 0 && c_ < nu)
                         atomicAdd(img + (size_t)r_ * nu + c_, val);
