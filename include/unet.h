@@ -8,6 +8,10 @@
  * convolution computed as an implicit GEMM on the tensor cores with BF16
  * operands and FP32 accumulation.
  *
+ * Convolutions run as implicit GEMMs on the tensor cores: tcgen05.mma with
+ * TMEM accumulators and TMA-staged halo bricks where the layer fits that
+ * kernel's tile (cnn_set_tensor_path below), mma.sync otherwise.
+ *
  * Conventions
  *   - Activations are channels-last [N][D][H][W][cstride] tensors; a call
  *     reads or writes channels [coff, coff + C) of each voxel, so a
@@ -128,6 +132,21 @@ bp_status cnn_mse(const float *p, const float *t, float *g, float *loss, long lo
  * p16 (may be NULL) receives bf16(p). Then g is zeroed. */
 bp_status cnn_adam(float *p, float *g, float *m, float *v, void *p16, long long n, float lr,
                    float b1, float b2, float eps, int t, void *stream);
+
+/* Tuning and testing (no counterpart in the paper).
+ *   cnn_set_tensor_path  process-wide choice of the kernel behind
+ *                        cnn_conv3d_forward and cnn_conv3d_dgrad: 1 (default)
+ *                        the tcgen05 kernel (TMEM accumulators, TMA-staged
+ *                        bricks) for layers with Cout 32 that fit its tile
+ *                        (width a multiple of 128, even depth and height,
+ *                        Cin a multiple of 16, 16-byte aligned), where it
+ *                        measured faster; 2: the tcgen05 kernel for Cout 16
+ *                        too; 0: always the mma.sync kernel.
+ *   cnn_device_status    synchronise the stream, then read and clear the
+ *                        device error word of the tensor-core kernels
+ *                        (bounded waits): BP_OK, BP_ERR_TIMEOUT or BP_ERR_DEVICE. */
+bp_status cnn_set_tensor_path(int mode);
+bp_status cnn_device_status(void *stream);
 
 #ifdef __cplusplus
 }

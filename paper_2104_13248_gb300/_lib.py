@@ -76,6 +76,8 @@ PROTOTYPES = {
     "cnn_pack_input": (_i, [_vp, _vp, _i, _ll, _vp]),
     "cnn_mse": (_i, [_vp, _vp, _vp, _vp, _ll, _vp]),
     "cnn_adam": (_i, [_vp, _vp, _vp, _vp, _vp, _ll, _f, _f, _f, _f, _i, _vp]),
+    "cnn_set_tensor_path": (_i, [_i]),
+    "cnn_device_status": (_i, [_vp]),
     # include/iter.h
     "it_fill": (_i, [_vp, _ll, _f, _vp]),
     "it_ratio": (_i, [_vp, _vp, _vp, _ll, _f, _vp]),

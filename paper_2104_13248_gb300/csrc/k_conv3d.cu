@@ -444,6 +444,166 @@ __global__ void maxpool2_bwd_kernel(const bf16 *__restrict__ x, int cs, int coff
     }
 }
 
+// ---- 8-channel (16-byte) versions of the element-wise kernels: one index
+// decomposition per 8 channels instead of per element; used when every
+// channel stride and offset is a multiple of 8 and the pointers are 16-byte
+// aligned (which channels-last tensors of this library always are).
+__device__ __forceinline__ float2 bf2f(unsigned u) {
+    return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&u));
+}
+__device__ __forceinline__ unsigned f2bf(float a, float b) {
+    __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<unsigned *>(&h);
+}
+
+__global__ void upsample2_fwd_v8(const uint4 *__restrict__ x, bf16 *__restrict__ y, int ycs, int ycoff,
+                                 int N, int D, int H, int W, int c8) {
+    const long long total = (long long)N * D * H * W * c8;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int cv = (int)(t % c8);
+        long long v = t / c8;
+        const int xv = (int)(v % W);
+        v /= W;
+        const int yv = (int)(v % H);
+        v /= H;
+        const int zv = (int)(v % D);
+        const long long nb = v / D;
+        const uint4 val = x[t];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const long long u = ((nb * (2 * D) + 2 * zv + (k >> 2)) * (2 * H) + 2 * yv + ((k >> 1) & 1)) * (2 * W) +
+                                2 * xv + (k & 1);
+            *reinterpret_cast<uint4 *>(y + u * ycs + ycoff + cv * 8) = val;
+        }
+    }
+}
+
+__global__ void upsample2_bwd_v8(const bf16 *__restrict__ dy, int dycs, int dycoff, uint4 *__restrict__ dx,
+                                 int N, int D, int H, int W, int c8) {
+    const long long total = (long long)N * D * H * W * c8;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int cv = (int)(t % c8);
+        long long v = t / c8;
+        const int xv = (int)(v % W);
+        v /= W;
+        const int yv = (int)(v % H);
+        v /= H;
+        const int zv = (int)(v % D);
+        const long long nb = v / D;
+        float s[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const long long u = ((nb * (2 * D) + 2 * zv + (k >> 2)) * (2 * H) + 2 * yv + ((k >> 1) & 1)) * (2 * W) +
+                                2 * xv + (k & 1);
+            const uint4 q = *reinterpret_cast<const uint4 *>(dy + u * dycs + dycoff + cv * 8);
+            const float2 a = bf2f(q.x), b = bf2f(q.y), c = bf2f(q.z), d = bf2f(q.w);
+            s[0] += a.x; s[1] += a.y; s[2] += b.x; s[3] += b.y;
+            s[4] += c.x; s[5] += c.y; s[6] += d.x; s[7] += d.y;
+        }
+        dx[t] = make_uint4(f2bf(s[0], s[1]), f2bf(s[2], s[3]), f2bf(s[4], s[5]), f2bf(s[6], s[7]));
+    }
+}
+
+__global__ void relu_bwd_v8(bf16 *__restrict__ g, int gcs, int gcoff, const bf16 *__restrict__ y, int ycs,
+                            int ycoff, long long nvox, int c8) {
+    const long long total = nvox * c8;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        const long long v = t / c8;
+        const int cv = (int)(t % c8);
+        uint4 *gp = reinterpret_cast<uint4 *>(g + v * gcs + gcoff + cv * 8);
+        const uint4 yq = *reinterpret_cast<const uint4 *>(y + v * ycs + ycoff + cv * 8);
+        uint4 gq = *gp;
+        unsigned *gw = reinterpret_cast<unsigned *>(&gq);
+        const unsigned *yw = reinterpret_cast<const unsigned *>(&yq);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const float2 yy = bf2f(yw[i]);
+            // keep each half where y > 0, else +0
+            unsigned keep = (yy.x > 0.0f ? 0x0000FFFFu : 0u) | (yy.y > 0.0f ? 0xFFFF0000u : 0u);
+            gw[i] &= keep;
+        }
+        *gp = gq;
+    }
+}
+
+__global__ void pack_input_v8(const float *__restrict__ x, uint4 *__restrict__ y, int c8, long long nvox) {
+    const long long total = nvox * c8;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        const long long v = t / c8;
+        const int cv = (int)(t % c8);
+        y[t] = cv == 0 ? make_uint4(f2bf(x[v], 0.0f), 0u, 0u, 0u) : make_uint4(0u, 0u, 0u, 0u);
+    }
+}
+
+// Output head, four consecutive voxels along x per thread: per (dz, dy) the
+// six input voxels x-1 .. x+4 are loaded once, 8 channels at a time (16-byte
+// loads), and serve the three dx taps of all four outputs; the weights are
+// read from shared memory as broadcasts.
+__global__ void head_fwd_v4(const bf16 *__restrict__ x, int cs, const float *__restrict__ w,
+                            const float *__restrict__ bptr, const float *__restrict__ res,
+                            float *__restrict__ out, int N, int D, int H, int W, int cin) {
+    extern __shared__ float ws[];   // [27][cin]
+    for (int t = threadIdx.x; t < 27 * cin; t += blockDim.x) ws[t] = w[t];
+    __syncthreads();
+    const float b0 = bptr ? *bptr : 0.0f;
+    const int W4 = W / 4;
+    const long long total = (long long)N * D * H * W4;
+    const int c8n = cin / 8;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        long long v = t;
+        const int x0 = (int)(v % W4) * 4;
+        v /= W4;
+        const int yv = (int)(v % H);
+        v /= H;
+        const int z = (int)(v % D);
+        const long long nb = v / D;
+        float acc[4] = {b0, b0, b0, b0};
+        for (int dz = 0; dz < 3; ++dz) {
+            const int zz = z + dz - 1;
+            if (zz < 0 || zz >= D) continue;
+            for (int dy = 0; dy < 3; ++dy) {
+                const int yy = yv + dy - 1;
+                if (yy < 0 || yy >= H) continue;
+                const bf16 *row = x + ((nb * D + zz) * H + yy) * (long long)W * cs;
+                const float *wt = ws + (dz * 3 + dy) * 3 * cin;
+                for (int g8 = 0; g8 < c8n; ++g8) {
+                    float in[6][8];
+#pragma unroll
+                    for (int p = 0; p < 6; ++p) {
+                        const int xx = x0 + p - 1;
+                        if (xx >= 0 && xx < W) {
+                            const uint4 q = *reinterpret_cast<const uint4 *>(row + (long long)xx * cs + g8 * 8);
+                            const float2 a = bf2f(q.x), b = bf2f(q.y), c = bf2f(q.z), d = bf2f(q.w);
+                            in[p][0] = a.x; in[p][1] = a.y; in[p][2] = b.x; in[p][3] = b.y;
+                            in[p][4] = c.x; in[p][5] = c.y; in[p][6] = d.x; in[p][7] = d.y;
+                        } else {
+#pragma unroll
+                            for (int j = 0; j < 8; ++j) in[p][j] = 0.0f;
+                        }
+                    }
+#pragma unroll
+                    for (int dx = 0; dx < 3; ++dx) {
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) {
+                            const float wv = wt[dx * cin + g8 * 8 + j];
+#pragma unroll
+                            for (int o = 0; o < 4; ++o) acc[o] = fmaf(wv, in[o + dx][j], acc[o]);
+                        }
+                    }
+                }
+            }
+        }
+        const long long vo = ((nb * D + z) * H + yv) * (long long)W + x0;
+#pragma unroll
+        for (int o = 0; o < 4; ++o) out[vo + o] = acc[o] + (res ? res[vo + o] : 0.0f);
+    }
+}
+
 __global__ void upsample2_fwd_kernel(const bf16 *__restrict__ x, bf16 *__restrict__ y, int ycs,
                                      int ycoff, int N, int D, int H, int W, int c) {
     const int Du = 2 * D, Hu = 2 * H, Wu = 2 * W;
@@ -560,9 +720,19 @@ static TileGrid make_grid(int n, int d, int h, int wd, long long *ntiles) {
     return g;
 }
 
+bool conv_tc_applies(const void *x, int xcs, int xco, const void *w, const void *y, int ycs, int yco, int yf32,
+                     int d, int h, int wd, int cin, int cout);
+cudaError_t conv_fwd_tc(const void *x, int xcs, int xco, const void *w, const float *b, void *y, int ycs, int yco,
+                        int yf32, int n, int d, int h, int wd, int cin, int cout, int relu, cudaStream_t st);
+
 static bp_status conv_fwd(const bf16 *x, int xcs, int xco, const bf16 *w, const float *b, void *y,
                           int ycs, int yco, int yf32, int n, int d, int h, int wd, int cin, int cout,
                           int relu, cudaStream_t st) {
+    // tcgen05 implicit GEMM (k_conv_tc.cu) where its tile fits the layer
+    if (conv_tc_applies(x, xcs, xco, w, y, ycs, yco, yf32, d, h, wd, cin, cout)) {
+        cudaError_t e = conv_fwd_tc(x, xcs, xco, w, b, y, ycs, yco, yf32, n, d, h, wd, cin, cout, relu, st);
+        return e == cudaSuccess ? BP_OK : cuda_fail(nullptr, e, "conv3d_fwd_tc");
+    }
     long long nt;
     TileGrid g = make_grid(n, d, h, wd, &nt);
     if (nt > 0x7fffffffLL) return fail(nullptr, BP_ERR_INVALID_ARG, "conv3d: volume too large");
@@ -720,6 +890,11 @@ bp_status cnn_head_forward(const void *x, int x_cstride, const float *w, const f
     if (!x || !w || !out || cin < 1 || cin > x_cstride || n < 1)
         return fail(nullptr, BP_ERR_INVALID_ARG, "cnn_head_forward: bad arguments");
     const long long nvox = (long long)n * d * h * wd;
+    if (cin % 8 == 0 && x_cstride % 8 == 0 && wd % 4 == 0 && al16(x)) {
+        head_fwd_v4<<<ew_blocks(nvox / 4), 256, 27 * cin * sizeof(float), (cudaStream_t)stream>>>(
+            (const bf16 *)x, x_cstride, w, b, res, out, n, d, h, wd, cin);
+        return launch_ok("head_fwd_v4");
+    }
     head_fwd_kernel<<<ew_blocks(nvox), 256, 27 * cin * sizeof(float), (cudaStream_t)stream>>>(
         (const bf16 *)x, x_cstride, w, b, res, out, n, d, h, wd, cin);
     return launch_ok("head_fwd_kernel");
@@ -762,6 +937,11 @@ bp_status cnn_upsample2_forward(const void *x, void *y, int y_cstride, int y_cof
                                 int wd, int c, void *stream) {
     if (!x || !y || y_coff + c > y_cstride)
         return fail(nullptr, BP_ERR_INVALID_ARG, "cnn_upsample2_forward: bad arguments");
+    if (c % 8 == 0 && y_cstride % 8 == 0 && y_coff % 8 == 0 && al16(x) && al16(y)) {
+        const long long tot8 = (long long)n * d * h * wd * (c / 8);
+        upsample2_fwd_v8<<<ew_blocks(tot8), 256, 0, (cudaStream_t)stream>>>((const uint4 *)x, (bf16 *)y, y_cstride, y_coff, n, d, h, wd, c / 8);
+        return launch_ok("upsample2_fwd_v8");
+    }
     const long long tot = (long long)n * 8 * d * h * wd * c;
     upsample2_fwd_kernel<<<ew_blocks(tot), 256, 0, (cudaStream_t)stream>>>((const bf16 *)x, (bf16 *)y, y_cstride, y_coff, n, d, h, wd, c);
     return launch_ok("upsample2_fwd_kernel");
@@ -771,6 +951,11 @@ bp_status cnn_upsample2_backward(const void *dy, int dy_cstride, int dy_coff, vo
                                  int h, int wd, int c, void *stream) {
     if (!dy || !dx || dy_coff + c > dy_cstride)
         return fail(nullptr, BP_ERR_INVALID_ARG, "cnn_upsample2_backward: bad arguments");
+    if (c % 8 == 0 && dy_cstride % 8 == 0 && dy_coff % 8 == 0 && al16(dy) && al16(dx)) {
+        const long long tot8 = (long long)n * d * h * wd * (c / 8);
+        upsample2_bwd_v8<<<ew_blocks(tot8), 256, 0, (cudaStream_t)stream>>>((const bf16 *)dy, dy_cstride, dy_coff, (uint4 *)dx, n, d, h, wd, c / 8);
+        return launch_ok("upsample2_bwd_v8");
+    }
     const long long tot = (long long)n * d * h * wd * c;
     upsample2_bwd_kernel<<<ew_blocks(tot), 256, 0, (cudaStream_t)stream>>>((const bf16 *)dy, dy_cstride, dy_coff, (bf16 *)dx, n, d, h, wd, c);
     return launch_ok("upsample2_bwd_kernel");
@@ -780,12 +965,21 @@ bp_status cnn_relu_backward(void *g, int g_cstride, int g_coff, const void *y, i
                             long long nvox, int c, void *stream) {
     if (!g || !y || g_coff + c > g_cstride || y_coff + c > y_cstride)
         return fail(nullptr, BP_ERR_INVALID_ARG, "cnn_relu_backward: bad arguments");
+    if (c % 8 == 0 && g_cstride % 8 == 0 && g_coff % 8 == 0 && y_cstride % 8 == 0 && y_coff % 8 == 0 && al16(g) &&
+        al16(y)) {
+        relu_bwd_v8<<<ew_blocks(nvox * (c / 8)), 256, 0, (cudaStream_t)stream>>>((bf16 *)g, g_cstride, g_coff, (const bf16 *)y, y_cstride, y_coff, nvox, c / 8);
+        return launch_ok("relu_bwd_v8");
+    }
     relu_bwd_kernel<<<ew_blocks(nvox * c), 256, 0, (cudaStream_t)stream>>>((bf16 *)g, g_cstride, g_coff, (const bf16 *)y, y_cstride, y_coff, nvox, c);
     return launch_ok("relu_bwd_kernel");
 }
 
 bp_status cnn_pack_input(const float *x, void *y, int cstride, long long nvox, void *stream) {
     if (!x || !y || cstride < 1) return fail(nullptr, BP_ERR_INVALID_ARG, "cnn_pack_input: bad arguments");
+    if (cstride % 8 == 0 && al16(y)) {
+        pack_input_v8<<<ew_blocks(nvox * (cstride / 8)), 256, 0, (cudaStream_t)stream>>>(x, (uint4 *)y, cstride / 8, nvox);
+        return launch_ok("pack_input_v8");
+    }
     pack_input_kernel<<<ew_blocks(nvox), 256, 0, (cudaStream_t)stream>>>(x, (bf16 *)y, cstride, nvox);
     return launch_ok("pack_input_kernel");
 }

@@ -1,0 +1,372 @@
+// 3x3x3 convolution forward on the 5th-generation tensor cores (tcgen05):
+// implicit GEMM with M = 128 consecutive output voxels along x, N = Cout,
+// K = 16 input channels of one tap, BF16 operands from shared memory and the
+// FP32 accumulators in tensor memory. The paper has no learned component;
+// this serves the few-view correction network.
+//
+// CTA tile: 2 (y) x 2 (z) output rows of 128 voxels, all Cout channels; one
+// TMEM accumulator of Cout columns per row (lanes = voxels). Per 16-channel
+// chunk of the input:
+//   - the halo brick (130 x 4 x 4 voxels) arrives by two 5-D TMA loads, one
+//     per 8-channel half, as two planes [voxel][8 channels] (16 bytes a voxel;
+//     zero fill outside the volume is the convolution's zero padding). Eight
+//     consecutive voxels of a plane are one 8 x 16-byte core matrix, so the A
+//     operand of row r and tap (dz, dy, dx) is a descriptor into the brick:
+//     start at voxel (tz+dz, ty+dy, dx), stride 128 bytes between 8-voxel
+//     groups (SBO), the plane size between the two channel halves (LBO);
+//   - the chunk's weights are copied with cp.async into [tap][half][cout][8]
+//     (B operand per tap: SBO 128 bytes, LBO Cout x 16 bytes);
+//   - one thread issues 4 rows x 27 taps of tcgen05.mma (kind::f16, M 128,
+//     N Cout, K 16) and commits them to an mbarrier, which every thread
+//     waits for (bounded) before the next chunk overwrites shared memory.
+// Epilogue: each warp reads its 32 TMEM lanes (tcgen05.ld 32x32b) per row,
+// adds the bias, applies ReLU and stores Cout channels per voxel.
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include <cstdint>
+#include <mutex>
+
+#include "geom_dev.cuh"
+#include "../../include/unet.h"
+
+namespace bp {
+
+namespace {
+
+typedef __nv_bfloat16 bf16;
+
+constexpr int kTcThreads = 128;
+constexpr int kBX = 130, kBY = 4, kBZ = 4;            // halo brick
+constexpr int kPlaneBytes = kBX * kBY * kBZ * 16;     // one 8-channel plane
+constexpr int kRows = 4;                               // output rows per CTA (2 y x 2 z)
+
+template <int COUT>
+struct TcCfg {
+    static constexpr int WBYTES = 27 * 2 * COUT * 16;  // weights of one 16-channel chunk
+    static constexpr int TMEM_COLS = kRows * COUT;     // 64 or 128 (a power of two >= 32)
+    static constexpr int SMEM = 2 * kPlaneBytes + WBYTES + 1024;   // + alignment slack
+};
+
+__device__ __forceinline__ unsigned s_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+// Shared-memory matrix descriptor (no swizzle, K-major core matrices):
+// start >> 4 in bits 0-13, leading (K) byte offset >> 4 in 16-29, stride
+// (M/N) byte offset >> 4 in 32-45, descriptor version 1 in bits 46-47.
+__device__ __forceinline__ unsigned long long smem_desc(unsigned addr, unsigned lbo, unsigned sbo) {
+    return (unsigned long long)((addr >> 4) & 0x3FFF) | ((unsigned long long)((lbo >> 4) & 0x3FFF) << 16) |
+           ((unsigned long long)((sbo >> 4) & 0x3FFF) << 32) | (1ull << 46);
+}
+
+// Instruction descriptor of kind::f16: FP32 accumulator (bits 4-5 = 1), BF16
+// A and B (bits 7-9, 10-12 = 1), both K-major, N >> 3 in bits 17-22,
+// M >> 4 in bits 24-28.
+template <int N>
+__device__ __forceinline__ unsigned idesc_bf16() {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(N >> 3) << 17) | ((unsigned)(128 >> 4) << 24);
+}
+
+__device__ __forceinline__ void tma_load_5d(void *dst, const CUtensorMap *map, int c0, int c1, int c2, int c3,
+                                            int c4, unsigned long long *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(s_u32(dst)),
+        "l"(reinterpret_cast<unsigned long long>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4),
+        "r"(s_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s_u32(dst)), "l"(src) : "memory");
+}
+
+template <int N>
+struct TmemRow;
+template <>
+struct TmemRow<16> {
+    __device__ __forceinline__ static void load(unsigned addr, float *v) {
+        unsigned r[16];
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+            : "r"(addr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+    }
+};
+template <>
+struct TmemRow<32> {
+    __device__ __forceinline__ static void load(unsigned addr, float *v) {
+        TmemRow<16>::load(addr, v);
+        TmemRow<16>::load(addr + 16, v + 16);
+    }
+};
+
+template <int COUT, bool OUT_F32>
+__global__ void __launch_bounds__(kTcThreads, 2)
+conv3d_fwd_tc(const __grid_constant__ CUtensorMap xmap, int xco, const bf16 *__restrict__ w,
+              const float *__restrict__ bias, void *__restrict__ y, int ycs, int yco, int d, int h, int wd,
+              int cin, int relu, unsigned *err, unsigned long long timeout_ns) {
+    using Cfg = TcCfg<COUT>;
+    extern __shared__ unsigned char smem_raw[];
+    // 1024-byte aligned base: planes, then weights
+    unsigned char *smem = reinterpret_cast<unsigned char *>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    unsigned char *plane0 = smem;
+    unsigned char *wsm = smem + 2 * kPlaneBytes;
+    __shared__ __align__(8) unsigned long long tma_bar, mma_bar;
+    __shared__ unsigned tmem_base;
+    __shared__ int alive_s;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int ntx = wd / 128, nty = h / 2, ntz = d / 2;
+    int t = blockIdx.x;
+    const int tx = t % ntx;
+    t /= ntx;
+    const int ty = t % nty;
+    t /= nty;
+    const int tz = t % ntz;
+    const int nb = t / ntz;
+    const int x0 = tx * 128, y0 = ty * 2, z0 = tz * 2;
+
+    if (tid == 0) {
+        mbar_init(&tma_bar, 1);
+        mbar_init(&mma_bar, 1);
+        fence_barrier_init();
+        alive_s = 1;
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(s_u32(&tmem_base)),
+                     "r"(Cfg::TMEM_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const unsigned tmem = tmem_base;
+    const int nchunks = cin / 16;
+    const unsigned idesc = idesc_bf16<COUT>();
+
+    for (int ch = 0; ch < nchunks; ++ch) {
+        // weights of this chunk: w[co][tap][16 ch + i] -> wsm[tap][half][co][8]
+        for (int p = tid; p < 27 * 2 * COUT; p += kTcThreads) {
+            const int half = p & 1, co = (p >> 1) % COUT, tap = (p >> 1) / COUT;
+            cp_async16(wsm + ((tap * 2 + half) * COUT + co) * 16,
+                       w + ((size_t)co * 27 + tap) * cin + ch * 16 + half * 8);
+        }
+        asm volatile("cp.async.commit_group;\ncp.async.wait_all;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // generic writes -> tensor core reads
+        __syncthreads();
+        if (tid == 0) {
+            mbar_arrive_expect_tx(&tma_bar, 2u * kPlaneBytes);
+            tma_load_5d(plane0, &xmap, xco + ch * 16, x0 - 1, y0 - 1, z0 - 1, nb, &tma_bar);
+            tma_load_5d(plane0 + kPlaneBytes, &xmap, xco + ch * 16 + 8, x0 - 1, y0 - 1, z0 - 1, nb, &tma_bar);
+            bool ok = mbar_wait_bounded(&tma_bar, ch & 1, timeout_ns);
+            if (ok) {
+                asm volatile("tcgen05.fence::after_thread_sync;");
+                const unsigned pa = s_u32(plane0), wb = s_u32(wsm);
+#pragma unroll 1
+                for (int r = 0; r < kRows; ++r) {
+                    const int ry = r & 1, rz = r >> 1;
+#pragma unroll 1
+                    for (int tap = 0; tap < 27; ++tap) {
+                        const int dz = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;
+                        const unsigned voff = (unsigned)(((rz + dz) * kBY + (ry + dy)) * kBX + dx) * 16u;
+                        const unsigned long long ad = smem_desc(pa + voff, kPlaneBytes, 128);
+                        const unsigned long long bd = smem_desc(wb + (unsigned)tap * 2u * COUT * 16u, COUT * 16, 128);
+                        const unsigned acc = (ch > 0 || tap > 0) ? 1u : 0u;
+                        asm volatile(
+                            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem + (unsigned)(r * COUT)),
+                            "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+                    }
+                }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                    s_u32(&mma_bar)));
+            } else {
+                atomicOr(err, DEV_ERR_TIMEOUT);
+                alive_s = 0;
+                // the loads may still land: give them one more bounded wait before exiting
+                mbar_wait_bounded(&tma_bar, ch & 1, timeout_ns);
+            }
+        }
+        __syncthreads();
+        if (!alive_s) break;
+        // the MMAs of this chunk must have read shared memory before it is refilled
+        if (!mbar_wait_bounded(&mma_bar, ch & 1, timeout_ns)) {
+            if (tid == 0) atomicOr(err, DEV_ERR_TIMEOUT);
+            alive_s = 0;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        __syncthreads();
+        if (!alive_s) break;
+    }
+
+    if (alive_s) {
+        const size_t vox_row = (size_t)wd;
+#pragma unroll 1
+        for (int r = 0; r < kRows; ++r) {
+            float v[COUT];
+            TmemRow<COUT>::load(tmem + ((unsigned)(warp * 32) << 16) + (unsigned)(r * COUT), v);
+            const int yy = y0 + (r & 1), zz = z0 + (r >> 1);
+            const int xx = x0 + warp * 32 + lane;
+            const size_t vox = (((size_t)nb * d + zz) * h + yy) * vox_row + xx;
+#pragma unroll
+            for (int c = 0; c < COUT; ++c) {
+                float o = v[c] + (bias ? __ldg(bias + c) : 0.0f);
+                v[c] = (relu && o < 0.0f) ? 0.0f : o;
+            }
+            if constexpr (OUT_F32) {
+                float4 *dst = reinterpret_cast<float4 *>(reinterpret_cast<float *>(y) + vox * ycs + yco);
+#pragma unroll
+                for (int c = 0; c < COUT / 4; ++c)
+                    dst[c] = make_float4(v[4 * c], v[4 * c + 1], v[4 * c + 2], v[4 * c + 3]);
+            } else {
+                uint4 *dst = reinterpret_cast<uint4 *>(reinterpret_cast<bf16 *>(y) + vox * ycs + yco);
+#pragma unroll
+                for (int c = 0; c < COUT / 8; ++c) {
+                    uint4 q;
+                    __nv_bfloat162 h0 = __floats2bfloat162_rn(v[8 * c], v[8 * c + 1]);
+                    __nv_bfloat162 h1 = __floats2bfloat162_rn(v[8 * c + 2], v[8 * c + 3]);
+                    __nv_bfloat162 h2 = __floats2bfloat162_rn(v[8 * c + 4], v[8 * c + 5]);
+                    __nv_bfloat162 h3 = __floats2bfloat162_rn(v[8 * c + 6], v[8 * c + 7]);
+                    q.x = *reinterpret_cast<unsigned *>(&h0);
+                    q.y = *reinterpret_cast<unsigned *>(&h1);
+                    q.z = *reinterpret_cast<unsigned *>(&h2);
+                    q.w = *reinterpret_cast<unsigned *>(&h3);
+                    dst[c] = q;
+                }
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(Cfg::TMEM_COLS));
+}
+
+typedef CUresult (*PFN_encode5)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+PFN_encode5 encode_fn() {
+    static PFN_encode5 fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_encode5>(p);
+    }
+    return fn;
+}
+
+// Device error word of the tensor-core convolutions (bounded waits).
+__device__ unsigned g_tc_err;
+
+}  // namespace
+
+static std::mutex g_tc_mu;
+static unsigned *g_tc_err_addr[64] = {};
+// 0: mma.sync only; 1 (default): tcgen05 for Cout 32, where it measured faster
+// (with Cout 16 each 128 x 16 x 16 MMA re-reads a 4 KB A tile from shared
+// memory for too little work, and the mma.sync kernel wins); 2: tcgen05
+// wherever its tile applies
+static int g_tc_mode = 1;
+
+static cudaError_t tc_err_address(unsigned **out) {
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(g_tc_mu);
+    if (!g_tc_err_addr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_tc_err);
+        if (e != cudaSuccess) return e;
+        g_tc_err_addr[dev] = static_cast<unsigned *>(p);
+    }
+    *out = g_tc_err_addr[dev];
+    return cudaSuccess;
+}
+
+// The tensor-core path applies when the width is a multiple of 128, depth
+// and height are even, Cout is 16 or 32, Cin a multiple of 16, and every
+// pointer, stride and offset is 16-byte aligned.
+bool conv_tc_applies(const void *x, int xcs, int xco, const void *w, const void *y, int ycs, int yco, int yf32,
+                     int d, int h, int wd, int cin, int cout) {
+    (void)yf32;
+    return (g_tc_mode == 2 ? (cout == 16 || cout == 32) : (g_tc_mode == 1 && cout == 32)) && cin % 16 == 0 && cin > 0 && wd % 128 == 0 && wd > 0 && h % 2 == 0 &&
+           d % 2 == 0 && h > 0 && d > 0 && xcs % 8 == 0 && xco % 8 == 0 && ycs % 8 == 0 && yco % 8 == 0 &&
+           (reinterpret_cast<uintptr_t>(x) & 15) == 0 && (reinterpret_cast<uintptr_t>(w) & 15) == 0 &&
+           (reinterpret_cast<uintptr_t>(y) & 15) == 0 && encode_fn() != nullptr;
+}
+
+cudaError_t conv_fwd_tc(const void *x, int xcs, int xco, const void *w, const float *b, void *y, int ycs, int yco,
+                        int yf32, int n, int d, int h, int wd, int cin, int cout, int relu, cudaStream_t st) {
+    unsigned *err = nullptr;
+    cudaError_t ea = tc_err_address(&err);
+    if (ea != cudaSuccess) return ea;
+    CUtensorMap map;
+    const cuuint64_t es = 2;
+    cuuint64_t dims[5] = {(cuuint64_t)xcs, (cuuint64_t)wd, (cuuint64_t)h, (cuuint64_t)d, (cuuint64_t)n};
+    cuuint64_t strides[4] = {(cuuint64_t)xcs * es, (cuuint64_t)xcs * wd * es, (cuuint64_t)xcs * wd * h * es,
+                             (cuuint64_t)xcs * wd * h * d * es};
+    cuuint32_t box[5] = {8, (cuuint32_t)kBX, (cuuint32_t)kBY, (cuuint32_t)kBZ, 1};
+    cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+    CUresult r = encode_fn()(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<void *>(x), dims, strides, box,
+                             estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+    const long long nblk = (long long)n * (d / 2) * (h / 2) * (wd / 128);
+    if (nblk <= 0) return cudaSuccess;
+    if (nblk > 0x7fffffffLL) return cudaErrorInvalidValue;
+    const unsigned long long timeout_ns = 2000000000ull;
+#define TC_CASE(C, F)                                                                                        \
+    {                                                                                                        \
+        auto k = conv3d_fwd_tc<C, F>;                                                                        \
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, TcCfg<C>::SMEM); \
+        if (e != cudaSuccess) return e;                                                                      \
+        k<<<(unsigned)nblk, kTcThreads, TcCfg<C>::SMEM, st>>>(map, xco, (const bf16 *)w, b, y, ycs, yco, d, h, \
+                                                              wd, cin, relu, err, timeout_ns);               \
+        return cudaGetLastError();                                                                           \
+    }
+    if (cout == 16) {
+        if (yf32) TC_CASE(16, true) else TC_CASE(16, false)
+    } else {
+        if (yf32) TC_CASE(32, true) else TC_CASE(32, false)
+    }
+#undef TC_CASE
+}
+
+}  // namespace bp
+
+using namespace bp;
+
+extern "C" {
+
+bp_status cnn_set_tensor_path(int mode) {
+    if (mode < 0 || mode > 2) return fail(nullptr, BP_ERR_INVALID_ARG, "cnn_set_tensor_path: mode must be 0, 1 or 2");
+    g_tc_mode = mode;
+    return BP_OK;
+}
+
+bp_status cnn_device_status(void *stream) {
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "cnn_device_status: stream synchronise");
+    unsigned *err = nullptr;
+    e = tc_err_address(&err);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "cnn_device_status: error word");
+    unsigned v = 0;
+    e = cudaMemcpy(&v, err, sizeof(v), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && v != 0) e = cudaMemset(err, 0, sizeof(v));
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "cnn_device_status: read");
+    if (v & DEV_ERR_TIMEOUT) return fail(nullptr, BP_ERR_TIMEOUT, "tensor-core convolution: a bounded wait ran out");
+    if (v) return fail(nullptr, BP_ERR_DEVICE, "tensor-core convolution: device error");
+    return BP_OK;
+}
+
+}  // extern "C"
