@@ -19,6 +19,10 @@
 //   - one thread issues 4 rows x 27 taps of tcgen05.mma (kind::f16, M 128,
 //     N Cout, K 16) and commits them to an mbarrier, which every thread
 //     waits for (bounded) before the next chunk overwrites shared memory.
+// Two CTAs share an SM, so one's loads overlap the other's MMAs. (A
+// warp-specialised persistent version with one CTA per SM and two stages was
+// slower: its single producer warp serialised the weight copies and the
+// brick loads of every chunk.)
 // Epilogue: each warp reads its 32 TMEM lanes (tcgen05.ld 32x32b) per row,
 // adds the bias, applies ReLU and stores Cout channels per voxel.
 #include <cuda.h>
@@ -150,6 +154,12 @@ conv3d_fwd_tc(const __grid_constant__ CUtensorMap xmap, int xco, const bf16 *__r
     const unsigned idesc = idesc_bf16<COUT>();
 
     for (int ch = 0; ch < nchunks; ++ch) {
+        // the brick's TMA first, so its latency overlaps the weight copies
+        if (tid == 0) {
+            mbar_arrive_expect_tx(&tma_bar, 2u * kPlaneBytes);
+            tma_load_5d(plane0, &xmap, xco + ch * 16, x0 - 1, y0 - 1, z0 - 1, nb, &tma_bar);
+            tma_load_5d(plane0 + kPlaneBytes, &xmap, xco + ch * 16 + 8, x0 - 1, y0 - 1, z0 - 1, nb, &tma_bar);
+        }
         // weights of this chunk: w[co][tap][16 ch + i] -> wsm[tap][half][co][8]
         for (int p = tid; p < 27 * 2 * COUT; p += kTcThreads) {
             const int half = p & 1, co = (p >> 1) % COUT, tap = (p >> 1) / COUT;
@@ -160,9 +170,6 @@ conv3d_fwd_tc(const __grid_constant__ CUtensorMap xmap, int xco, const bf16 *__r
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // generic writes -> tensor core reads
         __syncthreads();
         if (tid == 0) {
-            mbar_arrive_expect_tx(&tma_bar, 2u * kPlaneBytes);
-            tma_load_5d(plane0, &xmap, xco + ch * 16, x0 - 1, y0 - 1, z0 - 1, nb, &tma_bar);
-            tma_load_5d(plane0 + kPlaneBytes, &xmap, xco + ch * 16 + 8, x0 - 1, y0 - 1, z0 - 1, nb, &tma_bar);
             bool ok = mbar_wait_bounded(&tma_bar, ch & 1, timeout_ns);
             if (ok) {
                 asm volatile("tcgen05.fence::after_thread_sync;");
