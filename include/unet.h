@@ -137,11 +137,11 @@ bp_status cnn_adam(float *p, float *g, float *m, float *v, void *p16, long long 
  *   cnn_set_tensor_path  process-wide choice of the kernel behind
  *                        cnn_conv3d_forward and cnn_conv3d_dgrad: 1 (default)
  *                        the tcgen05 kernel (TMEM accumulators, TMA-staged
- *                        bricks) for layers with Cout 32 that fit its tile
- *                        (width a multiple of 128, even depth and height,
- *                        Cin a multiple of 16, 16-byte aligned), where it
- *                        measured faster; 2: the tcgen05 kernel for Cout 16
- *                        too; 0: always the mma.sync kernel.
+ *                        bricks, one MMA per brick row shared by the output
+ *                        rows it feeds) for every layer that fits its tile
+ *                        (width a multiple of 128, depth a multiple of 4,
+ *                        Cout 16 or 32, Cin a multiple of 16, 16-byte
+ *                        aligned); 0: always the mma.sync kernel.
  *   cnn_device_status    synchronise the stream, then read and clear the
  *                        device error word of the tensor-core kernels
  *                        (bounded waits): BP_OK, BP_ERR_TIMEOUT or BP_ERR_DEVICE. */

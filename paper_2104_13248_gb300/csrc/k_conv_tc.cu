@@ -4,25 +4,30 @@
 // FP32 accumulators in tensor memory. The paper has no learned component;
 // this serves the few-view correction network.
 //
-// CTA tile: 2 (y) x 2 (z) output rows of 128 voxels, all Cout channels; one
-// TMEM accumulator of Cout columns per row (lanes = voxels). Per 16-channel
-// chunk of the input:
-//   - the halo brick (130 x 4 x 4 voxels) arrives by two 5-D TMA loads, one
+// CTA tile: 4 output rows of 128 voxels stacked along z (one y), all Cout
+// channels; one TMEM accumulator of Cout columns per row (lanes = voxels).
+// Per 16-channel chunk of the input:
+//   - the halo brick (130 x 3 x 6 voxels) arrives by two 5-D TMA loads, one
 //     per 8-channel half, as two planes [voxel][8 channels] (16 bytes a voxel;
 //     zero fill outside the volume is the convolution's zero padding). Eight
 //     consecutive voxels of a plane are one 8 x 16-byte core matrix, so the A
-//     operand of row r and tap (dz, dy, dx) is a descriptor into the brick:
-//     start at voxel (tz+dz, ty+dy, dx), stride 128 bytes between 8-voxel
-//     groups (SBO), the plane size between the two channel halves (LBO);
-//   - the chunk's weights are copied with cp.async into [tap][half][cout][8]
-//     (B operand per tap: SBO 128 bytes, LBO Cout x 16 bytes);
-//   - one thread issues 4 rows x 27 taps of tcgen05.mma (kind::f16, M 128,
-//     N Cout, K 16) and commits them to an mbarrier, which every thread
-//     waits for (bounded) before the next chunk overwrites shared memory.
-// Two CTAs share an SM, so one's loads overlap the other's MMAs. (A
-// warp-specialised persistent version with one CTA per SM and two stages was
-// slower: its single producer warp serialised the weight copies and the
-// brick loads of every chunk.)
+//     operand of brick row (z', dy) shifted by dx is a descriptor into the
+//     brick: stride 128 bytes between 8-voxel groups (SBO), the plane size
+//     between the two channel halves (LBO);
+//   - that A operand serves every output row rz = z' - dz (dz = 0..2) at
+//     once: one MMA with N = (rows) x Cout, whose B rows are the weights of
+//     taps (dz, dy, dx) for those rows, laid out [dy][dx][half][dz][cout][8]
+//     by cp.async so the rows follow at a uniform 128-byte stride, and whose
+//     D columns are those rows' accumulators (row rz at column (3 - rz) Cout).
+//     That is 54 MMAs of N = 16-48 (Cout 16) per chunk instead of 108 of
+//     N = 16, and half the A-operand reads;
+//   - one thread issues them (tcgen05.mma kind::f16, M 128, K 16) and commits
+//     to an mbarrier, which every thread waits for (bounded) before the next
+//     chunk overwrites shared memory.
+// Two CTAs share an SM, so one's loads overlap the other's MMAs (the brick's
+// TMA is issued before the weight copies). A warp-specialised persistent
+// version with one CTA per SM and two stages was slower: its single producer
+// warp serialised the weight copies and the brick loads of every chunk.
 // Epilogue: each warp reads its 32 TMEM lanes (tcgen05.ld 32x32b) per row,
 // adds the bias, applies ReLU and stores Cout channels per voxel.
 #include <cuda.h>
@@ -41,15 +46,18 @@ namespace {
 typedef __nv_bfloat16 bf16;
 
 constexpr int kTcThreads = 128;
-constexpr int kBX = 130, kBY = 4, kBZ = 4;            // halo brick
-constexpr int kPlaneBytes = kBX * kBY * kBZ * 16;     // one 8-channel plane
-constexpr int kRows = 4;                               // output rows per CTA (2 y x 2 z)
+constexpr int kBX = 130, kBY = 3, kBZ = 6;            // halo brick
+constexpr int kPlaneBytes = kBX * kBY * kBZ * 16;     // one 8-channel plane (bytes a TMA load writes)
+// planes start 128-byte aligned (a TMA destination must be): 37440 -> 37504
+constexpr int kPlaneStride = (kPlaneBytes + 127) / 128 * 128;
+constexpr int kRows = 4;                               // output rows per CTA (4 along z)
+static_assert(kPlaneStride % 128 == 0 && (2 * kPlaneStride) % 128 == 0, "TMA destinations need 128-byte alignment");
 
 template <int COUT>
 struct TcCfg {
     static constexpr int WBYTES = 27 * 2 * COUT * 16;  // weights of one 16-channel chunk
     static constexpr int TMEM_COLS = kRows * COUT;     // 64 or 128 (a power of two >= 32)
-    static constexpr int SMEM = 2 * kPlaneBytes + WBYTES + 1024;   // + alignment slack
+    static constexpr int SMEM = 2 * kPlaneStride + WBYTES + 1024;   // + alignment slack
 };
 
 __device__ __forceinline__ unsigned s_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
@@ -119,13 +127,13 @@ conv3d_fwd_tc(const __grid_constant__ CUtensorMap xmap, int xco, const bf16 *__r
     unsigned char *smem = reinterpret_cast<unsigned char *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     unsigned char *plane0 = smem;
-    unsigned char *wsm = smem + 2 * kPlaneBytes;
+    unsigned char *wsm = smem + 2 * kPlaneStride;
     __shared__ __align__(8) unsigned long long tma_bar, mma_bar;
     __shared__ unsigned tmem_base;
     __shared__ int alive_s;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int ntx = wd / 128, nty = h / 2, ntz = d / 2;
+    const int ntx = wd / 128, nty = h, ntz = d / 4;
     int t = blockIdx.x;
     const int tx = t % ntx;
     t /= ntx;
@@ -133,7 +141,7 @@ conv3d_fwd_tc(const __grid_constant__ CUtensorMap xmap, int xco, const bf16 *__r
     t /= nty;
     const int tz = t % ntz;
     const int nb = t / ntz;
-    const int x0 = tx * 128, y0 = ty * 2, z0 = tz * 2;
+    const int x0 = tx * 128, y0 = ty, z0 = tz * 4;
 
     if (tid == 0) {
         mbar_init(&tma_bar, 1);
@@ -151,19 +159,19 @@ conv3d_fwd_tc(const __grid_constant__ CUtensorMap xmap, int xco, const bf16 *__r
     asm volatile("tcgen05.fence::after_thread_sync;");
     const unsigned tmem = tmem_base;
     const int nchunks = cin / 16;
-    const unsigned idesc = idesc_bf16<COUT>();
 
     for (int ch = 0; ch < nchunks; ++ch) {
         // the brick's TMA first, so its latency overlaps the weight copies
         if (tid == 0) {
             mbar_arrive_expect_tx(&tma_bar, 2u * kPlaneBytes);
             tma_load_5d(plane0, &xmap, xco + ch * 16, x0 - 1, y0 - 1, z0 - 1, nb, &tma_bar);
-            tma_load_5d(plane0 + kPlaneBytes, &xmap, xco + ch * 16 + 8, x0 - 1, y0 - 1, z0 - 1, nb, &tma_bar);
+            tma_load_5d(plane0 + kPlaneStride, &xmap, xco + ch * 16 + 8, x0 - 1, y0 - 1, z0 - 1, nb, &tma_bar);
         }
-        // weights of this chunk: w[co][tap][16 ch + i] -> wsm[tap][half][co][8]
+        // weights of this chunk: w[co][tap][16 ch + i] -> wsm[dy][dx][half][dz][co][8]
         for (int p = tid; p < 27 * 2 * COUT; p += kTcThreads) {
             const int half = p & 1, co = (p >> 1) % COUT, tap = (p >> 1) / COUT;
-            cp_async16(wsm + ((tap * 2 + half) * COUT + co) * 16,
+            const int dz = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;
+            cp_async16(wsm + ((((dy * 3 + dx) * 2 + half) * 3 + dz) * COUT + co) * 16,
                        w + ((size_t)co * 27 + tap) * cin + ch * 16 + half * 8);
         }
         asm volatile("cp.async.commit_group;\ncp.async.wait_all;" ::: "memory");
@@ -174,20 +182,34 @@ conv3d_fwd_tc(const __grid_constant__ CUtensorMap xmap, int xco, const bf16 *__r
             if (ok) {
                 asm volatile("tcgen05.fence::after_thread_sync;");
                 const unsigned pa = s_u32(plane0), wb = s_u32(wsm);
+                // Brick row (z', dy) shifted by dx feeds output rows rz = z'-dz for
+                // dz = 0..2: rows rz_hi = min(3, z') down to rz_lo = max(0, z'-2) in one
+                // MMA with N = (rz_hi - rz_lo + 1) x Cout. Row rz's accumulator sits at
+                // TMEM column (3 - rz) x Cout and its weights for that tap at block
+                // (dy, dx, half, dz = z' - rz) of wsm, so D columns and B rows both
+                // run with rz descending / dz ascending at uniform strides. The first
+                // group (dy, dx) = (0, 0) issues z' = 3 (rows 1-3) and z' = 0 (row 0)
+                // first, with accumulation off: every row starts exactly once.
 #pragma unroll 1
-                for (int r = 0; r < kRows; ++r) {
-                    const int ry = r & 1, rz = r >> 1;
+                for (int g = 0; g < 9; ++g) {
+                    const int dy = g / 3, dx = g % 3;
 #pragma unroll 1
-                    for (int tap = 0; tap < 27; ++tap) {
-                        const int dz = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;
-                        const unsigned voff = (unsigned)(((rz + dz) * kBY + (ry + dy)) * kBX + dx) * 16u;
-                        const unsigned long long ad = smem_desc(pa + voff, kPlaneBytes, 128);
-                        const unsigned long long bd = smem_desc(wb + (unsigned)tap * 2u * COUT * 16u, COUT * 16, 128);
-                        const unsigned acc = (ch > 0 || tap > 0) ? 1u : 0u;
+                    for (int q = 0; q < 6; ++q) {
+                        const int zp = (g == 0) ? (q == 0 ? 3 : q == 1 ? 0 : q - 1 + (q >= 4 ? 1 : 0)) : q;
+                        const int rz_hi = zp < 3 ? zp : 3, rz_lo = zp > 2 ? zp - 2 : 0;
+                        const int nrows = rz_hi - rz_lo + 1;
+                        const unsigned voff = (unsigned)((zp * kBY + dy) * kBX + dx) * 16u;
+                        const unsigned long long ad = smem_desc(pa + voff, kPlaneStride, 128);
+                        const unsigned boff = (unsigned)((((dy * 3 + dx) * 2) * 3 + (zp - rz_hi)) * COUT * 16);
+                        const unsigned long long bd = smem_desc(wb + boff, 3 * COUT * 16, 128);
+                        const unsigned id = (1u << 4) | (1u << 7) | (1u << 10) |
+                                            ((unsigned)((nrows * COUT) >> 3) << 17) | ((unsigned)(128 >> 4) << 24);
+                        const unsigned acc = (ch > 0 || g > 0 || q > 1) ? 1u : 0u;
                         asm volatile(
                             "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem + (unsigned)(r * COUT)),
-                            "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+                            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(
+                                tmem + (unsigned)((3 - rz_hi) * COUT)),
+                            "l"(ad), "l"(bd), "r"(id), "r"(acc));
                     }
                 }
                 asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
@@ -216,8 +238,8 @@ conv3d_fwd_tc(const __grid_constant__ CUtensorMap xmap, int xco, const bf16 *__r
 #pragma unroll 1
         for (int r = 0; r < kRows; ++r) {
             float v[COUT];
-            TmemRow<COUT>::load(tmem + ((unsigned)(warp * 32) << 16) + (unsigned)(r * COUT), v);
-            const int yy = y0 + (r & 1), zz = z0 + (r >> 1);
+            TmemRow<COUT>::load(tmem + ((unsigned)(warp * 32) << 16) + (unsigned)((3 - r) * COUT), v);
+            const int yy = y0, zz = z0 + r;
             const int xx = x0 + warp * 32 + lane;
             const size_t vox = (((size_t)nb * d + zz) * h + yy) * vox_row + xx;
 #pragma unroll
@@ -278,10 +300,7 @@ __device__ unsigned g_tc_err;
 
 static std::mutex g_tc_mu;
 static unsigned *g_tc_err_addr[64] = {};
-// 0: mma.sync only; 1 (default): tcgen05 for Cout 32, where it measured faster
-// (with Cout 16 each 128 x 16 x 16 MMA re-reads a 4 KB A tile from shared
-// memory for too little work, and the mma.sync kernel wins); 2: tcgen05
-// wherever its tile applies
+// 1 (default): tcgen05 wherever its tile applies; 0: mma.sync only
 static int g_tc_mode = 1;
 
 static cudaError_t tc_err_address(unsigned **out) {
@@ -300,14 +319,14 @@ static cudaError_t tc_err_address(unsigned **out) {
     return cudaSuccess;
 }
 
-// The tensor-core path applies when the width is a multiple of 128, depth
-// and height are even, Cout is 16 or 32, Cin a multiple of 16, and every
+// The tensor-core path applies when the width is a multiple of 128, the
+// depth a multiple of 4, Cout is 16 or 32, Cin a multiple of 16, and every
 // pointer, stride and offset is 16-byte aligned.
 bool conv_tc_applies(const void *x, int xcs, int xco, const void *w, const void *y, int ycs, int yco, int yf32,
                      int d, int h, int wd, int cin, int cout) {
     (void)yf32;
-    return (g_tc_mode == 2 ? (cout == 16 || cout == 32) : (g_tc_mode == 1 && cout == 32)) && cin % 16 == 0 && cin > 0 && wd % 128 == 0 && wd > 0 && h % 2 == 0 &&
-           d % 2 == 0 && h > 0 && d > 0 && xcs % 8 == 0 && xco % 8 == 0 && ycs % 8 == 0 && yco % 8 == 0 &&
+    return g_tc_mode == 1 && (cout == 16 || cout == 32) && cin % 16 == 0 && cin > 0 && wd % 128 == 0 && wd > 0 &&
+           d % 4 == 0 && h > 0 && d > 0 && xcs % 8 == 0 && xco % 8 == 0 && ycs % 8 == 0 && yco % 8 == 0 &&
            (reinterpret_cast<uintptr_t>(x) & 15) == 0 && (reinterpret_cast<uintptr_t>(w) & 15) == 0 &&
            (reinterpret_cast<uintptr_t>(y) & 15) == 0 && encode_fn() != nullptr;
 }
@@ -328,7 +347,7 @@ cudaError_t conv_fwd_tc(const void *x, int xcs, int xco, const void *w, const fl
                              estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
-    const long long nblk = (long long)n * (d / 2) * (h / 2) * (wd / 128);
+    const long long nblk = (long long)n * (d / 4) * h * (wd / 128);
     if (nblk <= 0) return cudaSuccess;
     if (nblk > 0x7fffffffLL) return cudaErrorInvalidValue;
     const unsigned long long timeout_ns = 2000000000ull;
@@ -356,7 +375,7 @@ using namespace bp;
 extern "C" {
 
 bp_status cnn_set_tensor_path(int mode) {
-    if (mode < 0 || mode > 2) return fail(nullptr, BP_ERR_INVALID_ARG, "cnn_set_tensor_path: mode must be 0, 1 or 2");
+    if (mode != 0 && mode != 1) return fail(nullptr, BP_ERR_INVALID_ARG, "cnn_set_tensor_path: mode must be 0 or 1");
     g_tc_mode = mode;
     return BP_OK;
 }
