@@ -1,7 +1,8 @@
 """Back-projection with the mid-plane symmetry (Section 3.1.2, Algorithm 1)
 against the FP64 oracle: v, its floor and fraction are computed once for
 voxels k and nz-1-k, whose taps come from the staged box and its vertical
-mirror. Same tolerance as the plain kernel (1e-5 max-relative, FP32)."""
+mirror. Same tolerances as the plain kernel: 1e-5 max-relative for FP32
+projections, 2e-3 for FP16-stored ones."""
 import math
 
 import numpy as np
@@ -10,7 +11,7 @@ import torch
 
 import oracle
 from paper_2104_13248_gb300 import _lib, api, inputs
-from tests.test_gpu_parity import TOL32, _band, rel
+from tests.test_gpu_parity import TOL16, TOL32, _band, rel
 
 pytestmark = pytest.mark.gpu
 
@@ -29,9 +30,11 @@ def _check(g, q, views_chunk=None):
         d = torch.from_numpy(q).cuda()
         assert api.bp_get_plan(ctx)["symmetric"]          # the default for centred geometries
         sym = api.bp_backproject(ctx, d, scale=scale).cpu().numpy()
+        sym16 = api.bp_backproject(ctx, d.half(), scale=scale).cpu().numpy()
         api.bp_set_symmetry(ctx, False)
         assert not api.bp_get_plan(ctx)["symmetric"]
         plain = api.bp_backproject(ctx, d, scale=scale).cpu().numpy()
+        plain16 = api.bp_backproject(ctx, d.half(), scale=scale).cpu().numpy()
         api.bp_set_symmetry(ctx, True)
         if views_chunk:
             # accumulate over view ranges through the same symmetric kernel
@@ -43,6 +46,9 @@ def _check(g, q, views_chunk=None):
         api.bp_device_status(ctx)
     assert rel(sym, ref) <= TOL32
     assert rel(plain, ref) <= TOL32
+    # FP16-stored projections (the plain kernel either way; the oracle takes the unquantised values)
+    assert rel(sym16, ref) <= TOL16
+    assert rel(plain16, ref) <= TOL16
     return sym, plain
 
 
