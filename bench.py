@@ -56,6 +56,24 @@ def parse_args(argv=None):
     return ap.parse_args(argv)
 
 
+def max_over_ranks(x: float, world: int, device="cpu") -> float:
+    """The slowest rank's time: an all-reduce (MAX) of one number, the only
+    collective of the replicas layout (each rank reconstructs its own data)."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(units_per_rank: float, world: int, slowest_ms: float) -> float:
+    """Whole-job throughput (GUPS) of world independent replicas: all ranks'
+    updates over the slowest rank's time."""
+    return world * units_per_rank / (slowest_ms * 1e-3) / 1e9
+
+
 def backprojector_source_hash() -> str:
     import hashlib
     h = hashlib.sha256()
@@ -403,12 +421,8 @@ def run_ours(args):
         if world > 1:
             dist.barrier()
 
-    def max_over_ranks(x: float) -> float:
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    def slowest(x: float) -> float:
+        return max_over_ranks(x, world, dev)
 
     p = inputs.preset(args.workload)
     g = p["geom"]
@@ -460,12 +474,12 @@ def run_ours(args):
         step_ms, bp_ms = time_steps(q32, K, evs)
     clocks = clk.summary()
     api.bp_device_status(ctx)
-    step_ms_max = max_over_ranks(step_ms)
-    bp_ms_max = max_over_ranks(bp_ms)
+    step_ms_max = slowest(step_ms)
+    bp_ms_max = slowest(bp_ms)
     step16_ms, bp16_ms = time_steps(q16, K, evs)
     api.bp_device_status(ctx)
-    step16_ms = max_over_ranks(step16_ms)
-    bp16_ms = max_over_ranks(bp16_ms)
+    step16_ms = slowest(step16_ms)
+    bp16_ms = slowest(bp16_ms)
 
     peaks, peak_src = measured_peaks()
     n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
@@ -502,7 +516,7 @@ def run_ours(args):
             float(host_vol[g["nz"] // 2, g["ny"] // 2, g["nx"] // 2])   # read the result
         t_e2e = (time.perf_counter() - t0) / n_e2e
         barrier()
-        t_e2e = max_over_ranks(t_e2e)
+        t_e2e = slowest(t_e2e)
         api.bp_device_status(ctx)
         e2e = {"value": world * U / t_e2e / 1e9, "unit": "GUPS",
                "h2d_bytes_per_step": host_proj.numel() * 4, "d2h_bytes_per_step": host_vol.numel() * 4,
@@ -515,7 +529,7 @@ def run_ours(args):
     # the launches inside the timed region: filter + back-projection per step
     line = {
         "metric": "fdk_backprojection_gups",
-        "value": world * U / (step_ms_max * 1e-3) / 1e9,
+        "value": replica_value(U, world, step_ms_max),
         "unit": "GUPS",
         "n_gpus": world, "steps": K, "warmup": args.warmup,
         "ms_per_step": step_ms_max,
