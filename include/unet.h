@@ -123,6 +123,57 @@ bp_status cnn_relu_backward(void *g, int g_cstride, int g_coff, const void *y, i
  * channels 1..cstride-1 are zeroed. */
 bp_status cnn_pack_input(const float *x, void *y, int cstride, long long nvox, void *stream);
 
+/* Input layer for a one-channel FP32 volume x [N][D][H][W] (the network's
+ * first convolution, on the CUDA cores: a tensor-core layer would spend 15/16
+ * of its products on zero channels):
+ *   y[v][y_coff + co] = act(b[co] + sum_tap w[co][tap] * bf16(x[v + tap]))
+ * x is rounded to BF16 (the network's activation type) before the products,
+ * which accumulate in FP32 from the bias in tap order; act = ReLU when
+ * relu != 0. w is BF16 [cout][27] (tap index (dz*3+dy)*3+dx), b FP32 [cout]
+ * (may be NULL), y BF16 [N][D][H][W][y_cstride]. cout is a multiple of 8 up
+ * to 32, wd a multiple of 4, y_cstride and y_coff multiples of 8, y 16-byte
+ * aligned; anything else returns BP_ERR_INVALID_ARG. */
+bp_status cnn_stem_forward(const float *x, const void *w, const float *b, void *y, int y_cstride,
+                           int y_coff, int n, int d, int h, int wd, int cout, int relu,
+                           void *stream);
+
+/* Its weight and bias gradients (FP32, accumulated):
+ *   dw[co][tap] += sum_v dy[v][dy_coff + co] * bf16(x[v + tap]),
+ *   db[co] += sum_v dy[v][dy_coff + co]   (db may be NULL)
+ * dy BF16 [N][D][H][W][dy_cstride]; same limits on cout and the channel
+ * layout as cnn_stem_forward (any wd). */
+bp_status cnn_stem_wgrad(const float *x, const void *dy, int dy_cstride, int dy_coff, float *dw,
+                         float *db, int n, int d, int h, int wd, int cout, void *stream);
+
+/* Additive skip connection: nearest 2x upsampling of x (BF16
+ * [N][D][H][W][c], dense) plus a skip tensor at the fine resolution:
+ *   y[2z+a][2y+b][2x+c][y_coff + ch] =
+ *       bf16(x[z][y][x][ch] + skip[2z+a][2y+b][2x+c][s_coff + ch])
+ * (the two BF16 values summed in FP32, rounded once). d, h, wd are the
+ * coarse dimensions. c, the strides and the offsets are multiples of 8 and
+ * the pointers 16-byte aligned. Its gradient is cnn_upsample2_backward for
+ * x and the output gradient itself for skip. */
+bp_status cnn_upsample2_add_forward(const void *x, const void *skip, int s_cstride, int s_coff,
+                                    void *y, int y_cstride, int y_coff, int n, int d, int h,
+                                    int wd, int c, void *stream);
+
+/* 1x1x1 output head (cin channels -> 1), the usual last layer of a U-Net:
+ *   out[v] = res[v] + b[0] + sum_ci w[ci] x[v][ci]
+ * x BF16 [nvox][x_cstride] (channels 0..cin-1), w FP32 [cin], b FP32 [1]
+ * (device, may be NULL), res and out FP32 [nvox] (res may be NULL); FP32
+ * products summed in channel order. cin a multiple of 8 up to 32,
+ * x_cstride a multiple of 8, x 16-byte aligned. */
+bp_status cnn_head1_forward(const void *x, int x_cstride, const float *w, const float *b,
+                            const float *res, float *out, long long nvox, int cin, void *stream);
+
+/* Its gradients for an FP32 output gradient g [nvox]:
+ *   dx[v][ci] = bf16(w[ci] g[v])   (BF16 [nvox][dx_cstride], overwritten)
+ *   dw[ci] += sum_v g[v] x[v][ci],  db[0] += sum_v g[v]   (FP32; db may be NULL)
+ * Same layout limits as cnn_head1_forward. */
+bp_status cnn_head1_backward(const void *x, int x_cstride, const float *w, const float *g, void *dx,
+                             int dx_cstride, float *dw, float *db, long long nvox, int cin,
+                             void *stream);
+
 /* Mean-square error: g = 2 (p - t) / n (FP32), and sum (p - t)^2 added
  * into loss[0] (FP32, caller zeroes it). */
 bp_status cnn_mse(const float *p, const float *t, float *g, float *loss, long long n, void *stream);
@@ -136,12 +187,18 @@ bp_status cnn_adam(float *p, float *g, float *m, float *v, void *p16, long long 
 /* Tuning and testing (no counterpart in the paper).
  *   cnn_set_tensor_path  process-wide choice of the kernel behind
  *                        cnn_conv3d_forward and cnn_conv3d_dgrad: 1 (default)
- *                        the tcgen05 kernel (TMEM accumulators, TMA-staged
+ *                        the tcgen05 kernels (TMEM accumulators, TMA-staged
  *                        bricks, one MMA per brick row shared by the output
- *                        rows it feeds) for every layer that fits its tile
+ *                        rows it feeds) for every layer that fits their tile
  *                        (width a multiple of 128, depth a multiple of 4,
  *                        Cout 16 or 32, Cin a multiple of 16, 16-byte
- *                        aligned); 0: always the mma.sync kernel.
+ *                        aligned): the persistent one (one CTA per SM,
+ *                        resident weights, two brick stages, two TMEM
+ *                        accumulator sets) where all weights fit in shared
+ *                        memory beside the stages (27 Cin Cout x 2 bytes up
+ *                        to 81 KB), the per-tile one otherwise; 2: the
+ *                        per-tile tcgen05 kernel only; 0: always the
+ *                        mma.sync kernel.
  *   cnn_device_status    synchronise the stream, then read and clear the
  *                        device error word of the tensor-core kernels
  *                        (bounded waits): BP_OK, BP_ERR_TIMEOUT or BP_ERR_DEVICE. */

@@ -74,6 +74,11 @@ PROTOTYPES = {
     "cnn_upsample2_backward": (_i, [_vp, _i, _i, _vp, _i, _i, _i, _i, _i, _vp]),
     "cnn_relu_backward": (_i, [_vp, _i, _i, _vp, _i, _i, _ll, _i, _vp]),
     "cnn_pack_input": (_i, [_vp, _vp, _i, _ll, _vp]),
+    "cnn_stem_forward": (_i, [_vp, _vp, _vp, _vp, _i, _i, _i, _i, _i, _i, _i, _i, _vp]),
+    "cnn_stem_wgrad": (_i, [_vp, _vp, _i, _i, _vp, _vp, _i, _i, _i, _i, _i, _vp]),
+    "cnn_head1_forward": (_i, [_vp, _i, _vp, _vp, _vp, _vp, _ll, _i, _vp]),
+    "cnn_head1_backward": (_i, [_vp, _i, _vp, _vp, _vp, _i, _vp, _vp, _ll, _i, _vp]),
+    "cnn_upsample2_add_forward": (_i, [_vp, _vp, _i, _i, _vp, _i, _i, _i, _i, _i, _i, _i, _vp]),
     "cnn_mse": (_i, [_vp, _vp, _vp, _vp, _ll, _vp]),
     "cnn_adam": (_i, [_vp, _vp, _vp, _vp, _vp, _ll, _f, _f, _f, _f, _i, _vp]),
     "cnn_set_tensor_path": (_i, [_i]),

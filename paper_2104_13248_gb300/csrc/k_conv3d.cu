@@ -604,6 +604,154 @@ __global__ void head_fwd_v4(const bf16 *__restrict__ x, int cs, const float *__r
     }
 }
 
+// FP32 pairs: fma.rn.f32x2 (sm_100 family) computes two independent IEEE
+// FMAs per instruction.
+typedef unsigned long long f2x;
+__device__ __forceinline__ f2x pk2(float a, float b) {
+    f2x r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ float2 upk2(f2x r) {
+    float2 v;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(v.x), "=f"(v.y) : "l"(r));
+    return v;
+}
+__device__ __forceinline__ f2x fma2x(f2x a, f2x b, f2x c) {
+    f2x r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+// A BF16 pair word (channel 2c in the low half) as its FP32 pair: BF16 is the
+// upper half of the FP32 encoding, so one shift and one mask.
+__device__ __forceinline__ f2x bfw2f2(unsigned u) {
+    return pk2(__uint_as_float(u << 16), __uint_as_float(u & 0xFFFF0000u));
+}
+
+// Output head (16 channels -> 1) on a shared-memory tile: 64 (x) x 8 (y) x 2
+// (z) outputs per CTA of 256 threads, each owning four x-consecutive
+// outputs. The haloed input (66 x 10 x 4 voxels, 16 BF16 channels = two
+// 16-byte halves a voxel) is staged once. Within each 128-byte group of four
+// voxels the eight halves are permuted by the group index, so the eight
+// threads of a quarter-warp, which read the same offset of eight consecutive
+// groups, hit eight different bank groups. Products run on channel pairs with
+// fma.rn.f32x2; the pair sums are added once at the end.
+constexpr int kHdTX = 64, kHdTY = 8, kHdTZ = 2, kHdCin = 16;
+constexpr int kHdHX = kHdTX + 2, kHdHY = kHdTY + 2, kHdHZ = kHdTZ + 2;
+constexpr int kHdRowChunks = (kHdHX + 3) / 4 * 8;   // 16-byte slots per staged row (17 groups)
+constexpr int kHdSmem = kHdHZ * kHdHY * kHdRowChunks * 16;   // 87,040 bytes
+constexpr int kHdThreads = 256;
+
+__device__ __forceinline__ int head_slot(int row, int i, int h) {
+    const int g = i >> 2;
+    return row * kHdRowChunks + g * 8 + (((i & 3) * 2 + h) ^ (g & 7));
+}
+
+__global__ void __launch_bounds__(kHdThreads)
+head_fwd_tile(const bf16 *__restrict__ x, int cs, const float *__restrict__ w, const float *__restrict__ bptr,
+              const float *__restrict__ res, float *__restrict__ out, int D, int H, int W, int tx, int ty, int tz) {
+    extern __shared__ __align__(128) uint4 hs[];
+    __shared__ __align__(16) float ws[27 * kHdCin];
+    long long r = blockIdx.x;
+    const int x0 = (int)(r % tx) * kHdTX;
+    r /= tx;
+    const int y0 = (int)(r % ty) * kHdTY;
+    r /= ty;
+    const int z0 = (int)(r % tz) * kHdTZ;
+    const long long nb = r / tz;
+    for (int t = threadIdx.x; t < 27 * kHdCin; t += kHdThreads) ws[t] = w[t];
+    // every copy of the CTA in flight at once (cp.async, zero fill outside the volume)
+    for (int c = threadIdx.x; c < kHdHZ * kHdHY * kHdHX * 2; c += kHdThreads) {
+        const int row = c / (kHdHX * 2), rem = c - row * (kHdHX * 2);
+        const int i = rem >> 1, h = rem & 1;
+        const int z = z0 + row / kHdHY - 1, yy = y0 + row % kHdHY - 1, xx = x0 + i - 1;
+        const bool in = z >= 0 && z < D && yy >= 0 && yy < H && xx >= 0 && xx < W;
+        const bf16 *src = in ? x + (((nb * D + z) * H + yy) * (long long)W + xx) * cs + h * 8 : x;
+        const unsigned dst = static_cast<unsigned>(__cvta_generic_to_shared(hs + head_slot(row, i, h)));
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(in ? 16 : 0)
+                     : "memory");
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    __syncthreads();
+    const int t = threadIdx.x;
+    const int ox = (t & 15) * 4, oy = (t >> 4) & 7, oz = t >> 7;
+    const f2x *w2 = reinterpret_cast<const f2x *>(ws);   // [27][8] channel pairs
+    f2x acc[4] = {0, 0, 0, 0};
+#pragma unroll
+    for (int dz = 0; dz < 3; ++dz) {
+#pragma unroll
+        for (int dy = 0; dy < 3; ++dy) {
+            const int row = (oz + dz) * kHdHY + oy + dy;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                f2x X[6][4];
+#pragma unroll
+                for (int p = 0; p < 6; ++p) {
+                    const uint4 q = hs[head_slot(row, ox + p, h)];
+                    X[p][0] = bfw2f2(q.x);
+                    X[p][1] = bfw2f2(q.y);
+                    X[p][2] = bfw2f2(q.z);
+                    X[p][3] = bfw2f2(q.w);
+                }
+#pragma unroll
+                for (int dx = 0; dx < 3; ++dx) {
+                    const int tap = (dz * 3 + dy) * 3 + dx;
+                    f2x Wp[4];
+#pragma unroll
+                    for (int c2 = 0; c2 < 4; ++c2) Wp[c2] = w2[tap * 8 + h * 4 + c2];
+#pragma unroll
+                    for (int o = 0; o < 4; ++o)
+#pragma unroll
+                        for (int c2 = 0; c2 < 4; ++c2) acc[o] = fma2x(Wp[c2], X[o + dx][c2], acc[o]);
+                }
+            }
+        }
+    }
+    const int z = z0 + oz, yy = y0 + oy;
+    if (z >= D || yy >= H) return;
+    const float b0 = bptr ? *bptr : 0.0f;
+    const long long vo = ((nb * D + z) * H + yy) * (long long)W;
+#pragma unroll
+    for (int o = 0; o < 4; ++o) {
+        const int xx = x0 + ox + o;
+        if (xx < W) {
+            const float2 a = upk2(acc[o]);
+            out[vo + xx] = (a.x + a.y) + b0 + (res ? res[vo + xx] : 0.0f);
+        }
+    }
+}
+
+// 2x2x2 max pooling, eight channels (16 bytes) per thread; y dense.
+__global__ void maxpool2_fwd_v8(const bf16 *__restrict__ x, int cs, int coff, uint4 *__restrict__ y, int N,
+                                int D, int H, int W, int c8) {
+    const int Do = D / 2, Ho = H / 2, Wo = W / 2;
+    const long long total = (long long)N * Do * Ho * Wo * c8;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int cv = (int)(t % c8);
+        long long v = t / c8;
+        const int xo = (int)(v % Wo);
+        v /= Wo;
+        const int yo = (int)(v % Ho);
+        v /= Ho;
+        const int zo = (int)(v % Do);
+        const long long nb = v / Do;
+        float m[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) m[j] = -3.0e38f;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int z = 2 * zo + (k >> 2), yy = 2 * yo + ((k >> 1) & 1), xx = 2 * xo + (k & 1);
+            const uint4 q =
+                *reinterpret_cast<const uint4 *>(x + (((nb * D + z) * H + yy) * (long long)W + xx) * cs + coff + cv * 8);
+            const float2 a = bf2f(q.x), b = bf2f(q.y), c = bf2f(q.z), d = bf2f(q.w);
+            m[0] = fmaxf(m[0], a.x); m[1] = fmaxf(m[1], a.y); m[2] = fmaxf(m[2], b.x); m[3] = fmaxf(m[3], b.y);
+            m[4] = fmaxf(m[4], c.x); m[5] = fmaxf(m[5], c.y); m[6] = fmaxf(m[6], d.x); m[7] = fmaxf(m[7], d.y);
+        }
+        y[t] = make_uint4(f2bf(m[0], m[1]), f2bf(m[2], m[3]), f2bf(m[4], m[5]), f2bf(m[6], m[7]));
+    }
+}
+
 __global__ void upsample2_fwd_kernel(const bf16 *__restrict__ x, bf16 *__restrict__ y, int ycs,
                                      int ycoff, int N, int D, int H, int W, int c) {
     const int Du = 2 * D, Hu = 2 * H, Wu = 2 * W;
@@ -890,6 +1038,16 @@ bp_status cnn_head_forward(const void *x, int x_cstride, const float *w, const f
     if (!x || !w || !out || cin < 1 || cin > x_cstride || n < 1)
         return fail(nullptr, BP_ERR_INVALID_ARG, "cnn_head_forward: bad arguments");
     const long long nvox = (long long)n * d * h * wd;
+    if (cin == kHdCin && x_cstride % 8 == 0 && al16(x)) {
+        const int tx = (wd + kHdTX - 1) / kHdTX, ty = (h + kHdTY - 1) / kHdTY, tz = (d + kHdTZ - 1) / kHdTZ;
+        const long long nt = (long long)n * tx * ty * tz;
+        if (nt > 0x7fffffffLL) return fail(nullptr, BP_ERR_INVALID_ARG, "cnn_head_forward: volume too large");
+        cudaError_t e = cudaFuncSetAttribute(head_fwd_tile, cudaFuncAttributeMaxDynamicSharedMemorySize, kHdSmem);
+        if (e != cudaSuccess) return cuda_fail(nullptr, e, "cnn_head_forward: shared memory limit");
+        head_fwd_tile<<<(unsigned)nt, kHdThreads, kHdSmem, (cudaStream_t)stream>>>(
+            (const bf16 *)x, x_cstride, w, b, res, out, d, h, wd, tx, ty, tz);
+        return launch_ok("head_fwd_tile");
+    }
     if (cin % 8 == 0 && x_cstride % 8 == 0 && wd % 4 == 0 && al16(x)) {
         head_fwd_v4<<<ew_blocks(nvox / 4), 256, 27 * cin * sizeof(float), (cudaStream_t)stream>>>(
             (const bf16 *)x, x_cstride, w, b, res, out, n, d, h, wd, cin);
@@ -918,6 +1076,11 @@ bp_status cnn_maxpool2_forward(const void *x, int x_cstride, int x_coff, void *y
                                int wd, int c, void *stream) {
     if (!x || !y || d % 2 || h % 2 || wd % 2 || x_coff + c > x_cstride)
         return fail(nullptr, BP_ERR_INVALID_ARG, "cnn_maxpool2_forward: bad arguments");
+    if (c % 8 == 0 && x_cstride % 8 == 0 && x_coff % 8 == 0 && al16(x) && al16(y)) {
+        const long long tot8 = (long long)n * (d / 2) * (h / 2) * (wd / 2) * (c / 8);
+        maxpool2_fwd_v8<<<ew_blocks(tot8), 256, 0, (cudaStream_t)stream>>>((const bf16 *)x, x_cstride, x_coff, (uint4 *)y, n, d, h, wd, c / 8);
+        return launch_ok("maxpool2_fwd_v8");
+    }
     const long long tot = (long long)n * (d / 2) * (h / 2) * (wd / 2) * c;
     maxpool2_fwd_kernel<<<ew_blocks(tot), 256, 0, (cudaStream_t)stream>>>((const bf16 *)x, x_cstride, x_coff, (bf16 *)y, n, d, h, wd, c);
     return launch_ok("maxpool2_fwd_kernel");

@@ -276,6 +276,289 @@ conv3d_fwd_tc(const __grid_constant__ CUtensorMap xmap, int xco, const bf16 *__r
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(Cfg::TMEM_COLS));
 }
 
+// ---------------------------------------------------------------------------
+// Persistent, warp-specialised version (the default where every chunk's
+// weights fit in shared memory next to two brick stages): one CTA per SM
+// walks tiles blockIdx.x, blockIdx.x + gridDim.x, ... so the CTAs in flight
+// cover neighbouring tiles and share their bricks in L2.
+//   - the weights of all chunks are copied once per CTA and stay resident;
+//   - warp 4 (one lane) streams bricks into two stages by TMA, ahead of
+//   - warp 5, which issues each (tile, chunk)'s 54 MMAs (fully unrolled, the
+//     descriptors warp-uniform, one lane issuing) and commits the stage back
+//     to the producer, and after a tile's last chunk commits its accumulator to
+//   - warps 0-3, the epilogue, which drain one of two TMEM accumulator sets
+//     (bias, ReLU, stores) while the MMAs of the next tile fill the other.
+// Every wait is bounded; a role whose wait runs out records DEV_ERR_TIMEOUT
+// and leaves its loop, the others' waits then run out in turn, and before the
+// CTA exits the producer waits for its loads in flight and the MMA lane for
+// its MMAs.
+// ---------------------------------------------------------------------------
+// Its bricks arrive by one TMA load per (tile, chunk) whose rows are a
+// voxel's 16 channels (32 bytes), written with the 32-byte swizzle (the two
+// 16-byte halves of each row swapped where address bit 7 is set); the A
+// operand descriptors use the same swizzle mode, which the tensor core
+// applies to absolute shared-memory addresses, so a brick row shifted by dx
+// voxels is still a plain start-address offset. Half the L2 requests of two
+// 16-byte-row planes, each of which fetched whole 32-byte sectors.
+constexpr int kPStages = 2;
+constexpr int kPThreads = 192;
+constexpr int kSwBrickBytes = kBX * kBY * kBZ * 32;                  // 74,880
+constexpr int kPStageBytes = (kSwBrickBytes + 1023) / 1024 * 1024;   // 75,776: swizzle atoms stay aligned
+static_assert(kPStageBytes % 1024 == 0, "stage bases must keep the swizzle pattern's alignment");
+constexpr int kPSmemLimit = 232448;   // opt-in shared memory per block (227 KB)
+
+template <int COUT>
+struct TcpCfg {
+    static constexpr int WCHUNK = TcCfg<COUT>::WBYTES;
+    static constexpr int TMEM_COLS = 2 * kRows * COUT;   // two accumulator sets: 128 or 256 columns
+    __host__ __device__ static constexpr int smem(int nch) { return kPStages * kPStageBytes + nch * WCHUNK + 1024; }
+};
+
+template <int COUT, bool OUT_F32>
+__global__ void __launch_bounds__(kPThreads, 1)
+conv3d_fwd_tcp(const __grid_constant__ CUtensorMap xmap, int xco, const bf16 *__restrict__ w,
+               const float *__restrict__ bias, void *__restrict__ y, int ycs, int yco, int d, int h, int wd,
+               int cin, int relu, int ntiles, unsigned *err, unsigned long long timeout_ns) {
+    using Cfg = TcpCfg<COUT>;
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char *smem = reinterpret_cast<unsigned char *>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    unsigned char *stage0 = smem;
+    unsigned char *wsm = smem + kPStages * kPStageBytes;
+    __shared__ __align__(8) unsigned long long full[kPStages], empty[kPStages], tfull[2], tempty[2], done_bar;
+    __shared__ unsigned tmem_base;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int nch = cin / 16;
+    const int ntx = wd / 128, nty = h, ntz = d / 4;
+
+    if (tid == 0) {
+        for (int s = 0; s < kPStages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(&tfull[a], 1);
+            mbar_init(&tempty[a], 4);
+        }
+        mbar_init(&done_bar, 1);
+        fence_barrier_init();
+    }
+    // every chunk's weights: w[co][tap][16 ch + i] -> wsm[ch][dy][dx][half][dz][co][8]
+    for (int p = tid; p < nch * 27 * 2 * COUT; p += kPThreads) {
+        const int half = p & 1, co = (p >> 1) % COUT, rest = (p >> 1) / COUT;
+        const int tap = rest % 27, ch = rest / 27;
+        const int dz = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;
+        cp_async16(wsm + ch * Cfg::WCHUNK + ((((dy * 3 + dx) * 2 + half) * 3 + dz) * COUT + co) * 16,
+                   w + ((size_t)co * 27 + tap) * cin + ch * 16 + half * 8);
+    }
+    asm volatile("cp.async.commit_group;\ncp.async.wait_all;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // generic writes -> tensor core reads
+    if (warp == 5) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(s_u32(&tmem_base)),
+                     "r"(Cfg::TMEM_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const unsigned tmem = tmem_base;
+
+    if (warp == 4 && lane == 0) {
+        // ---- producer: bricks by TMA into the two stages
+        int s = 0;
+        unsigned ph = 0;
+        int issued[kPStages];   // parity of the load in flight on each stage, or -1
+        for (int k = 0; k < kPStages; ++k) issued[k] = -1;
+        bool ok = true;
+        for (int tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
+            int t = tile;
+            const int tx = t % ntx;
+            t /= ntx;
+            const int ty = t % nty;
+            t /= nty;
+            const int tz = t % ntz;
+            const int nb = t / ntz;
+            for (int ch = 0; ch < nch; ++ch) {
+                if (!mbar_wait_bounded(&empty[s], ph ^ 1u, timeout_ns)) {
+                    atomicOr(err, DEV_ERR_TIMEOUT);
+                    ok = false;
+                    break;
+                }
+                mbar_arrive_expect_tx(&full[s], (unsigned)kSwBrickBytes);
+                tma_load_5d(stage0 + s * kPStageBytes, &xmap, xco + ch * 16, tx * 128 - 1, ty - 1, tz * 4 - 1, nb,
+                            &full[s]);
+                issued[s] = (int)ph;
+                if (++s == kPStages) {
+                    s = 0;
+                    ph ^= 1u;
+                }
+            }
+        }
+        // loads still in flight must land before the CTA leaves (they complete
+        // on their own; the MMA lane may have consumed some of them already)
+        for (int k = 0; k < kPStages; ++k)
+            if (issued[k] >= 0) mbar_wait_bounded(&full[k], (unsigned)issued[k], timeout_ns);
+    } else if (warp == 5) {
+        // ---- MMA issue. The whole warp runs the loop so that every descriptor
+        // is warp-uniform (computed on the uniform datapath, with the schedule's
+        // offsets folded into constants by the full unroll); lane 0 waits,
+        // issues and commits.
+        const bool leader = lane == 0;
+        int s = 0, a = 0;
+        unsigned ph = 0, aph = 0;
+        // A: 32-byte swizzle (mode 6 in bits 61-63), 8-row groups 256 bytes apart, LBO unused (1)
+        const unsigned long long lbo_sbo_a = (1ull << 16) | ((unsigned long long)(256 >> 4) << 32) | (1ull << 46) |
+                                             (6ull << 61);
+        const unsigned long long lbo_sbo_b =
+            ((unsigned long long)(((3 * COUT * 16) >> 4) & 0x3FFF) << 16) | ((unsigned long long)(128 >> 4) << 32) |
+            (1ull << 46);
+        bool ok = true;
+        for (int tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
+            int okw = leader ? (mbar_wait_bounded(&tempty[a], aph ^ 1u, timeout_ns) ? 1 : 0) : 0;
+            okw = __shfl_sync(0xffffffffu, okw, 0);
+            if (!okw) {
+                if (leader) atomicOr(err, DEV_ERR_TIMEOUT);
+                break;
+            }
+            __syncwarp();
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            const unsigned dbase = tmem + (unsigned)(a * kRows * COUT);
+            for (int ch = 0; ch < nch; ++ch) {
+                okw = leader ? (mbar_wait_bounded(&full[s], ph, timeout_ns) ? 1 : 0) : 0;
+                okw = __shfl_sync(0xffffffffu, okw, 0);
+                if (!okw) {
+                    if (leader) atomicOr(err, DEV_ERR_TIMEOUT);
+                    ok = false;
+                    break;
+                }
+                __syncwarp();
+                asm volatile("tcgen05.fence::after_thread_sync;");
+                const unsigned a0 = s_u32(stage0 + s * kPStageBytes) >> 4;
+                const unsigned b0 = s_u32(wsm + ch * Cfg::WCHUNK) >> 4;
+                const unsigned first_acc = ch > 0 ? 1u : 0u;
+#pragma unroll
+                for (int g = 0; g < 9; ++g) {
+                    const int dy = g / 3, dx = g % 3;
+#pragma unroll
+                    for (int q = 0; q < 6; ++q) {
+                        const int zp = (g == 0) ? (q == 0 ? 3 : q == 1 ? 0 : q - 1 + (q >= 4 ? 1 : 0)) : q;
+                        const int rz_hi = zp < 3 ? zp : 3, rz_lo = zp > 2 ? zp - 2 : 0;
+                        const int nrows = rz_hi - rz_lo + 1;
+                        const unsigned a16 = (unsigned)(2 * ((zp * kBY + dy) * kBX + dx));
+                        const unsigned b16 = (unsigned)(((((dy * 3 + dx) * 2) * 3 + (zp - rz_hi)) * COUT * 16) >> 4);
+                        const unsigned id = (1u << 4) | (1u << 7) | (1u << 10) |
+                                            ((unsigned)((nrows * COUT) >> 3) << 17) | ((unsigned)(128 >> 4) << 24);
+                        const unsigned acc = (g == 0 && q <= 1) ? first_acc : 1u;
+                        const unsigned long long ad = lbo_sbo_a | (unsigned long long)((a0 + a16) & 0x3FFF);
+                        const unsigned long long bd = lbo_sbo_b | (unsigned long long)((b0 + b16) & 0x3FFF);
+                        if (leader)
+                            asm volatile(
+                                "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                                " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(
+                                    dbase + (unsigned)((3 - rz_hi) * COUT)),
+                                "l"(ad), "l"(bd), "r"(id), "r"(acc));
+                    }
+                }
+                // the stage is free once these MMAs have read it
+                if (leader)
+                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                        s_u32(&empty[s])));
+                __syncwarp();
+                if (++s == kPStages) {
+                    s = 0;
+                    ph ^= 1u;
+                }
+            }
+            if (!ok) break;
+            if (leader)
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                    s_u32(&tfull[a])));
+            __syncwarp();
+            if (++a == 2) {
+                a = 0;
+                aph ^= 1u;
+            }
+        }
+        // every MMA issued must be complete before the accumulators are freed
+        if (leader) {
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                s_u32(&done_bar)));
+            if (!mbar_wait_bounded(&done_bar, 0, timeout_ns)) atomicOr(err, DEV_ERR_TIMEOUT);
+        }
+        __syncwarp();
+    } else if (warp < 4) {
+        // ---- epilogue: warp w reads TMEM lanes 32 w .. 32 w + 31 (voxels x0 + 32 w + lane)
+        int a = 0;
+        unsigned aph = 0;
+        for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+            int okw = 0;
+            if (lane == 0) okw = mbar_wait_bounded(&tfull[a], aph, timeout_ns) ? 1 : 0;
+            okw = __shfl_sync(0xffffffffu, okw, 0);
+            if (!okw) {
+                if (lane == 0) atomicOr(err, DEV_ERR_TIMEOUT);
+                break;
+            }
+            __syncwarp();
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            int t = tile;
+            const int tx = t % ntx;
+            t /= ntx;
+            const int ty = t % nty;
+            t /= nty;
+            const int tz = t % ntz;
+            const int nb = t / ntz;
+            const int xx = tx * 128 + warp * 32 + lane;
+#pragma unroll 1
+            for (int r = 0; r < kRows; ++r) {
+                float v[COUT];
+                TmemRow<COUT>::load(tmem + ((unsigned)(warp * 32) << 16) + (unsigned)(a * kRows * COUT + (3 - r) * COUT),
+                                    v);
+                const size_t vox = (((size_t)nb * d + tz * 4 + r) * h + ty) * (size_t)wd + xx;
+#pragma unroll
+                for (int c = 0; c < COUT; ++c) {
+                    const float o = v[c] + (bias ? __ldg(bias + c) : 0.0f);
+                    v[c] = (relu && o < 0.0f) ? 0.0f : o;
+                }
+                if constexpr (OUT_F32) {
+                    float4 *dst = reinterpret_cast<float4 *>(reinterpret_cast<float *>(y) + vox * ycs + yco);
+#pragma unroll
+                    for (int c = 0; c < COUT / 4; ++c)
+                        dst[c] = make_float4(v[4 * c], v[4 * c + 1], v[4 * c + 2], v[4 * c + 3]);
+                } else {
+                    uint4 *dst = reinterpret_cast<uint4 *>(reinterpret_cast<bf16 *>(y) + vox * ycs + yco);
+#pragma unroll
+                    for (int c = 0; c < COUT / 8; ++c) {
+                        uint4 q;
+                        __nv_bfloat162 h0 = __floats2bfloat162_rn(v[8 * c], v[8 * c + 1]);
+                        __nv_bfloat162 h1 = __floats2bfloat162_rn(v[8 * c + 2], v[8 * c + 3]);
+                        __nv_bfloat162 h2 = __floats2bfloat162_rn(v[8 * c + 4], v[8 * c + 5]);
+                        __nv_bfloat162 h3 = __floats2bfloat162_rn(v[8 * c + 6], v[8 * c + 7]);
+                        q.x = *reinterpret_cast<unsigned *>(&h0);
+                        q.y = *reinterpret_cast<unsigned *>(&h1);
+                        q.z = *reinterpret_cast<unsigned *>(&h2);
+                        q.w = *reinterpret_cast<unsigned *>(&h3);
+                        dst[c] = q;
+                    }
+                }
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&tempty[a]);
+            if (++a == 2) {
+                a = 0;
+                aph ^= 1u;
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 5) {
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(Cfg::TMEM_COLS));
+    }
+}
+
 typedef CUresult (*PFN_encode5)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
                                 const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
@@ -301,7 +584,9 @@ __device__ unsigned g_tc_err;
 static std::mutex g_tc_mu;
 static unsigned *g_tc_err_addr[64] = {};
 // 1 (default): tcgen05 wherever its tile applies; 0: mma.sync only
+// 2: the per-tile tcgen05 kernel only (no persistent kernel)
 static int g_tc_mode = 1;
+static int g_num_sms[64] = {};
 
 static cudaError_t tc_err_address(unsigned **out) {
     int dev = -1;
@@ -325,7 +610,7 @@ static cudaError_t tc_err_address(unsigned **out) {
 bool conv_tc_applies(const void *x, int xcs, int xco, const void *w, const void *y, int ycs, int yco, int yf32,
                      int d, int h, int wd, int cin, int cout) {
     (void)yf32;
-    return g_tc_mode == 1 && (cout == 16 || cout == 32) && cin % 16 == 0 && cin > 0 && wd % 128 == 0 && wd > 0 &&
+    return (g_tc_mode == 1 || g_tc_mode == 2) && (cout == 16 || cout == 32) && cin % 16 == 0 && cin > 0 && wd % 128 == 0 && wd > 0 &&
            d % 4 == 0 && h > 0 && d > 0 && xcs % 8 == 0 && xco % 8 == 0 && ycs % 8 == 0 && yco % 8 == 0 &&
            (reinterpret_cast<uintptr_t>(x) & 15) == 0 && (reinterpret_cast<uintptr_t>(w) & 15) == 0 &&
            (reinterpret_cast<uintptr_t>(y) & 15) == 0 && encode_fn() != nullptr;
@@ -351,6 +636,42 @@ cudaError_t conv_fwd_tc(const void *x, int xcs, int xco, const void *w, const fl
     if (nblk <= 0) return cudaSuccess;
     if (nblk > 0x7fffffffLL) return cudaErrorInvalidValue;
     const unsigned long long timeout_ns = 2000000000ull;
+    const int nch = cin / 16;
+    const int psmem = cout == 16 ? TcpCfg<16>::smem(nch) : TcpCfg<32>::smem(nch);
+    if (g_tc_mode == 1 && psmem <= kPSmemLimit) {
+        // rows of 16 channels (32 bytes), 32-byte swizzle
+        cuuint32_t box16[5] = {16, (cuuint32_t)kBX, (cuuint32_t)kBY, (cuuint32_t)kBZ, 1};
+        r = encode_fn()(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<void *>(x), dims, strides, box16, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e != cudaSuccess) return e;
+        if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+        if (!g_num_sms[dev]) {
+            int v = 0;
+            e = cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+            if (e != cudaSuccess) return e;
+            g_num_sms[dev] = v > 0 ? v : 1;
+        }
+        const unsigned grid = (unsigned)(nblk < g_num_sms[dev] ? nblk : g_num_sms[dev]);
+#define TCP_CASE(C, F)                                                                                      \
+    {                                                                                                       \
+        auto k = conv3d_fwd_tcp<C, F>;                                                                      \
+        e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, psmem);                    \
+        if (e != cudaSuccess) return e;                                                                     \
+        k<<<grid, kPThreads, psmem, st>>>(map, xco, (const bf16 *)w, b, y, ycs, yco, d, h, wd, cin, relu,   \
+                                          (int)nblk, err, timeout_ns);                                     \
+        return cudaGetLastError();                                                                          \
+    }
+        if (cout == 16) {
+            if (yf32) TCP_CASE(16, true) else TCP_CASE(16, false)
+        } else {
+            if (yf32) TCP_CASE(32, true) else TCP_CASE(32, false)
+        }
+#undef TCP_CASE
+    }
 #define TC_CASE(C, F)                                                                                        \
     {                                                                                                        \
         auto k = conv3d_fwd_tc<C, F>;                                                                        \
@@ -375,7 +696,7 @@ using namespace bp;
 extern "C" {
 
 bp_status cnn_set_tensor_path(int mode) {
-    if (mode != 0 && mode != 1) return fail(nullptr, BP_ERR_INVALID_ARG, "cnn_set_tensor_path: mode must be 0 or 1");
+    if (mode < 0 || mode > 2) return fail(nullptr, BP_ERR_INVALID_ARG, "cnn_set_tensor_path: mode must be 0, 1 or 2");
     g_tc_mode = mode;
     return BP_OK;
 }

@@ -183,4 +183,5 @@ def run(preset: str = "c5_learned", steps: int = 3000, crops_per_volume: int = 4
 if __name__ == "__main__":
     import sys
     steps = int(sys.argv[1]) if len(sys.argv) > 1 else 3000
-    print(json.dumps(run(steps=steps)))
+    lr = float(sys.argv[2]) if len(sys.argv) > 2 else 1e-3
+    print(json.dumps(run(steps=steps, lr=lr)))
