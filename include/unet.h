@@ -42,6 +42,22 @@ bp_status cnn_conv3d_forward(const void *x, int x_cstride, int x_coff, const voi
                              int n, int d, int h, int wd, int cin, int cout, int relu,
                              void *stream);
 
+/* A convolution followed by the 1x1x1 output head, for inference: the
+ * activation act(b + conv(x)) is rounded to BF16 and projected in the
+ * convolution's epilogue, so it is never written:
+ *   out[v] = res[v] + head_b[0] + sum_co head_w[co] bf16(act(b[co] + conv(x)[v][co]))
+ * (the result cnn_conv3d_forward followed by cnn_head1_forward gives, bit
+ * for bit). head_w FP32 [cout], head_b FP32 [1] (device, may be NULL), res
+ * and out FP32 [N][D][H][W] (res may be NULL). Only the persistent tcgen05
+ * kernel has this epilogue (cnn_set_tensor_path mode 1, Cout 16 or 32,
+ * width a multiple of 128, depth a multiple of 4, 27 Cin Cout x 2 bytes up
+ * to 81 KB); other layers return BP_ERR_UNSUPPORTED and the caller runs
+ * the two calls. */
+bp_status cnn_conv3d_forward_head(const void *x, int x_cstride, int x_coff, const void *w,
+                                  const float *b, const float *head_w, const float *head_b,
+                                  const float *res, float *out, int n, int d, int h, int wd,
+                                  int cin, int cout, int relu, void *stream);
+
 /* Input gradient of the convolution: dx[..., dxoff + ci] = sum_{tap, co}
  * w[co][tap][ci] dy[v - tap][dyoff + co] (BF16 in, BF16 out, FP32
  * accumulation). wt is a caller-owned BF16 buffer of 27*cin*cout elements

@@ -871,7 +871,10 @@ static TileGrid make_grid(int n, int d, int h, int wd, long long *ntiles) {
 bool conv_tc_applies(const void *x, int xcs, int xco, const void *w, const void *y, int ycs, int yco, int yf32,
                      int d, int h, int wd, int cin, int cout);
 cudaError_t conv_fwd_tc(const void *x, int xcs, int xco, const void *w, const float *b, void *y, int ycs, int yco,
-                        int yf32, int n, int d, int h, int wd, int cin, int cout, int relu, cudaStream_t st);
+                        int yf32, int n, int d, int h, int wd, int cin, int cout, int relu, cudaStream_t st,
+                        const float *head_w = nullptr, const float *head_b = nullptr,
+                        const float *head_res = nullptr, float *head_out = nullptr);
+bool conv_tcp_applies(int cin, int cout);
 
 static bp_status conv_fwd(const bf16 *x, int xcs, int xco, const bf16 *w, const float *b, void *y,
                           int ycs, int yco, int yf32, int n, int d, int h, int wd, int cin, int cout,
@@ -948,6 +951,20 @@ bp_status cnn_conv3d_forward(const void *x, int x_cstride, int x_coff, const voi
         return fail(nullptr, BP_ERR_INVALID_ARG, "cnn_conv3d_forward: bad arguments");
     return conv_fwd((const bf16 *)x, x_cstride, x_coff, (const bf16 *)w, b, y, y_cstride, y_coff,
                     y_fp32, n, d, h, wd, cin, cout, relu, (cudaStream_t)stream);
+}
+
+bp_status cnn_conv3d_forward_head(const void *x, int x_cstride, int x_coff, const void *w, const float *b,
+                                  const float *head_w, const float *head_b, const float *res, float *out, int n,
+                                  int d, int h, int wd, int cin, int cout, int relu, void *stream) {
+    if (!x || !w || !head_w || !out || n < 1 || d < 1 || h < 1 || wd < 1 || cin < 16 || cin % 16 ||
+        !conv_args_ok(x_cstride, x_coff, cin) || !al16(x) || !al16(w))
+        return fail(nullptr, BP_ERR_INVALID_ARG, "cnn_conv3d_forward_head: bad arguments");
+    if (!conv_tcp_applies(cin, cout) ||
+        !conv_tc_applies(x, x_cstride, x_coff, w, out, cout, 0, 0, d, h, wd, cin, cout))
+        return fail(nullptr, BP_ERR_UNSUPPORTED, "cnn_conv3d_forward_head: layer outside the persistent tcgen05 kernel");
+    cudaError_t e = conv_fwd_tc(x, x_cstride, x_coff, w, b, nullptr, cout, 0, 0, n, d, h, wd, cin, cout, relu,
+                                (cudaStream_t)stream, head_w, head_b, res, out);
+    return e == cudaSuccess ? BP_OK : cuda_fail(nullptr, e, "conv3d_fwd_tcp (fused head)");
 }
 
 bp_status cnn_conv3d_dgrad(const void *dy, int dy_cstride, int dy_coff, const void *w, void *wt,

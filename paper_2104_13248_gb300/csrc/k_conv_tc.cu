@@ -314,11 +314,20 @@ struct TcpCfg {
     __host__ __device__ static constexpr int smem(int nch) { return kPStages * kPStageBytes + nch * WCHUNK + 1024; }
 };
 
-template <int COUT, bool OUT_F32>
+// Epilogues of the persistent kernel: BF16 or FP32 activations, or the fused
+// 1x1x1 output head (out[v] = res[v] + hb + sum_co hw[co] bf16(act(acc + b)),
+// the same arithmetic and order as cnn_head1_forward on the BF16 activation).
+enum { kEpiBf16 = 0, kEpiF32 = 1, kEpiHead = 2 };
+struct HeadArgs {
+    const float *hw, *hb, *res;
+    float *out;
+};
+
+template <int COUT, int EPI>
 __global__ void __launch_bounds__(kPThreads, 1)
 conv3d_fwd_tcp(const __grid_constant__ CUtensorMap xmap, int xco, const bf16 *__restrict__ w,
                const float *__restrict__ bias, void *__restrict__ y, int ycs, int yco, int d, int h, int wd,
-               int cin, int relu, int ntiles, unsigned *err, unsigned long long timeout_ns) {
+               int cin, int relu, int ntiles, HeadArgs head, unsigned *err, unsigned long long timeout_ns) {
     using Cfg = TcpCfg<COUT>;
     extern __shared__ unsigned char smem_raw[];
     unsigned char *smem = reinterpret_cast<unsigned char *>(
@@ -520,11 +529,17 @@ conv3d_fwd_tcp(const __grid_constant__ CUtensorMap xmap, int xco, const bf16 *__
                     const float o = v[c] + (bias ? __ldg(bias + c) : 0.0f);
                     v[c] = (relu && o < 0.0f) ? 0.0f : o;
                 }
-                if constexpr (OUT_F32) {
+                if constexpr (EPI == kEpiF32) {
                     float4 *dst = reinterpret_cast<float4 *>(reinterpret_cast<float *>(y) + vox * ycs + yco);
 #pragma unroll
                     for (int c = 0; c < COUT / 4; ++c)
                         dst[c] = make_float4(v[4 * c], v[4 * c + 1], v[4 * c + 2], v[4 * c + 3]);
+                } else if constexpr (EPI == kEpiHead) {
+                    float o = 0.0f;
+#pragma unroll
+                    for (int c = 0; c < COUT; ++c)
+                        o = fmaf(__ldg(head.hw + c), __bfloat162float(__float2bfloat16_rn(v[c])), o);
+                    head.out[vox] = o + (head.hb ? __ldg(head.hb) : 0.0f) + (head.res ? head.res[vox] : 0.0f);
                 } else {
                     uint4 *dst = reinterpret_cast<uint4 *>(reinterpret_cast<bf16 *>(y) + vox * ycs + yco);
 #pragma unroll
@@ -616,8 +631,18 @@ bool conv_tc_applies(const void *x, int xcs, int xco, const void *w, const void 
            (reinterpret_cast<uintptr_t>(y) & 15) == 0 && encode_fn() != nullptr;
 }
 
+// Does the persistent kernel take this layer (it alone has the fused head)?
+bool conv_tcp_applies(int cin, int cout) {
+    if (g_tc_mode != 1 || (cout != 16 && cout != 32) || cin % 16 || cin < 16) return false;
+    const int nch = cin / 16;
+    return (cout == 16 ? TcpCfg<16>::smem(nch) : TcpCfg<32>::smem(nch)) <= kPSmemLimit;
+}
+
 cudaError_t conv_fwd_tc(const void *x, int xcs, int xco, const void *w, const float *b, void *y, int ycs, int yco,
-                        int yf32, int n, int d, int h, int wd, int cin, int cout, int relu, cudaStream_t st) {
+                        int yf32, int n, int d, int h, int wd, int cin, int cout, int relu, cudaStream_t st,
+                        const float *head_w, const float *head_b, const float *head_res, float *head_out) {
+    const bool fused_head = head_out != nullptr;
+    if (fused_head && !conv_tcp_applies(cin, cout)) return cudaErrorNotSupported;
     unsigned *err = nullptr;
     cudaError_t ea = tc_err_address(&err);
     if (ea != cudaSuccess) return ea;
@@ -656,19 +681,20 @@ cudaError_t conv_fwd_tc(const void *x, int xcs, int xco, const void *w, const fl
             g_num_sms[dev] = v > 0 ? v : 1;
         }
         const unsigned grid = (unsigned)(nblk < g_num_sms[dev] ? nblk : g_num_sms[dev]);
-#define TCP_CASE(C, F)                                                                                      \
+        const HeadArgs ha{head_w, head_b, head_res, head_out};
+#define TCP_CASE(C, E)                                                                                      \
     {                                                                                                       \
-        auto k = conv3d_fwd_tcp<C, F>;                                                                      \
+        auto k = conv3d_fwd_tcp<C, E>;                                                                      \
         e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, psmem);                    \
         if (e != cudaSuccess) return e;                                                                     \
         k<<<grid, kPThreads, psmem, st>>>(map, xco, (const bf16 *)w, b, y, ycs, yco, d, h, wd, cin, relu,   \
-                                          (int)nblk, err, timeout_ns);                                     \
+                                          (int)nblk, ha, err, timeout_ns);                                 \
         return cudaGetLastError();                                                                          \
     }
         if (cout == 16) {
-            if (yf32) TCP_CASE(16, true) else TCP_CASE(16, false)
+            if (fused_head) TCP_CASE(16, kEpiHead) else if (yf32) TCP_CASE(16, kEpiF32) else TCP_CASE(16, kEpiBf16)
         } else {
-            if (yf32) TCP_CASE(32, true) else TCP_CASE(32, false)
+            if (fused_head) TCP_CASE(32, kEpiHead) else if (yf32) TCP_CASE(32, kEpiF32) else TCP_CASE(32, kEpiBf16)
         }
 #undef TCP_CASE
     }

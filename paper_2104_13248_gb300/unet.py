@@ -207,9 +207,19 @@ class UNet:
         self._conv("d2", B["a2"], 32, 0, B["d2"], 32, 0, l2)
         self._conv("u2", B["d2"], 32, 0, B["r2"], 16, 0, l2)
         check(lib.cnn_upsample2_add_forward(_p(B["r2"]), _p(B["s1"]), 16, 0, _p(B["a1"]), 16, 0, *l2, 16, st))
-        self._conv("d1", B["a1"], 16, 0, B["d1"], 16, 0, l1)
-        check(lib.cnn_head1_forward(_p(B["d1"]), 16, _p(self.head_w()), _p(self.head_b()), _p(x),
-                                    _p(B["out"]), n * d * h * w, HEAD_CIN, st))
+        fused = False
+        if not train:
+            # d1 and the head in one kernel where the persistent tcgen05 convolution takes the layer
+            r = lib.cnn_conv3d_forward_head(_p(B["a1"]), 16, 0, _p(self.w16("d1")), _p(self.bias("d1")),
+                                            _p(self.head_w()), _p(self.head_b()), _p(x), _p(B["out"]),
+                                            n, d, h, w, 16, 16, 1, st)
+            if r != _lib.BP_ERR_UNSUPPORTED:
+                check(r)
+                fused = True
+        if not fused:
+            self._conv("d1", B["a1"], 16, 0, B["d1"], 16, 0, l1)
+            check(lib.cnn_head1_forward(_p(B["d1"]), 16, _p(self.head_w()), _p(self.head_b()), _p(x),
+                                        _p(B["out"]), n * d * h * w, HEAD_CIN, st))
         out = B["out"]
         return out[0] if squeeze else out
 

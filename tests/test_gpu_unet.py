@@ -295,6 +295,33 @@ def test_unet_forward_backward_against_plain_pytorch():
     assert float((a @ b) / (a.norm() * b.norm())) > 0.999
 
 
+def test_fused_head_matches_two_calls():
+    """Inference fuses d1 and the 1x1 head into the persistent tcgen05
+    kernel's epilogue (width 128: that kernel takes the layer); training runs
+    the two calls. The outputs agree bit for bit; with the tensor path forced
+    to mma.sync the fused call reports BP_ERR_UNSUPPORTED and inference falls
+    back to the two calls."""
+    net = UNet(seed=4)
+    with torch.no_grad():
+        net.params[net.head_off:net.head_off + 16] = torch.randn(16, device="cuda") * 0.3
+    x = torch.from_numpy(inputs.uniform_array(21, (1, 8, 12, 128), 0, 1).astype(np.float32)).cuda()
+    a = net.forward(x, train=False).clone()
+    b = net.forward(x, train=True).clone()
+    assert torch.equal(a, b)
+    lib = _lib.load()
+    _lib.check(lib.cnn_set_tensor_path(0))
+    try:
+        B = net._buffers((1, 8, 12, 128), False)
+        r = lib.cnn_conv3d_forward_head(P(B["a1"]), 16, 0, P(net.w16("d1")), P(net.bias("d1")), P(net.head_w()),
+                                        P(net.head_b()), P(x), P(B["out"]), 1, 8, 12, 128, 16, 16, 1, S())
+        assert r == _lib.BP_ERR_UNSUPPORTED
+        c = net.forward(x, train=False)
+        assert torch.isfinite(c).all()
+    finally:
+        _lib.check(lib.cnn_set_tensor_path(1))
+    _lib.check(lib.cnn_device_status(S()))
+
+
 def test_training_reduces_loss_and_checkpoint_resume(tmp_path):
     net = UNet(seed=1)
     x = torch.from_numpy(inputs.uniform_array(1, (2, 16, 16, 16), 0, 1).astype(np.float32)).cuda()
