@@ -40,7 +40,7 @@ def parse_args(argv=None):
     ap.add_argument("--ctas", type=int, default=2, help="CTAs per SM the TK=32 back-projector targets")
     ap.add_argument("--views", type=int, default=0, help="override the number of views (profiling runs)")
     ap.add_argument("--subsets", type=int, default=0, help="view subsets of --op mlem / sart (0 = 1 / 10)")
-    ap.add_argument("--op", choices=["fdk", "fp", "ls", "mlem", "sart"], default="fdk",
+    ap.add_argument("--op", choices=["fdk", "fp", "ls", "mlem", "sart", "unet"], default="fdk",
                     help="fdk: filter + back-projection (the benchmark); fp: matched forward projection "
                          "of the workload's volume(s); ls: least-squares iterations (differentiable workload)")
     ap.add_argument("--grid", nargs="*", default=None,
@@ -53,6 +53,8 @@ def parse_args(argv=None):
                     help="FP32 back-projection without the mid-plane symmetry (Section 3.1.2)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-learned", action="store_true",
+                    help="skip the few-view workload (train the network, held-out RMSE, wall time vs full view)")
     return ap.parse_args(argv)
 
 
@@ -215,6 +217,38 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_unet(args):
+    """Inference of the few-view network on one volume (random weights; the
+    cost does not depend on them): --views sets the edge length (default 256)."""
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2104_13248_gb300.unet import UNet, conv_flops
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    n = args.views or 256
+    net = UNet(seed=0)
+    gen = torch.Generator(device="cuda").manual_seed(0)
+    x = torch.rand((n, n, n), device="cuda", generator=gen)
+    for _ in range(args.warmup):
+        net.forward(x)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(args.steps):
+        net.forward(x)
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / args.steps
+    flops = conv_flops((1, n, n, n))
+    print(json.dumps({"metric": "unet_inference_tflops", "value": flops / (ms * 1e-3) / 1e12, "unit": "TFLOP/s",
+                      "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+                      "higher_is_better": True, "dtype": "bf16", "data": "synthetic",
+                      "config": {"workload": f"few-view U-Net inference, {n}^3 volume",
+                                 "flop_per_step": flops}}), flush=True)
+
+
 def run_op(args):
     """Secondary measurements (forward projector, least squares) in the same JSON form."""
     import torch
@@ -223,6 +257,8 @@ def run_op(args):
     __graft_entry__.build()
     from paper_2104_13248_gb300 import api, autograd, inputs
 
+    if args.op == "unet":
+        return run_unet(args)
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     p = inputs.preset(args.workload)
     g = p["geom"]
@@ -400,6 +436,24 @@ def run_depth_sweep(args):
     ctx.close()
 
 
+def learned_block() -> dict:
+    """The few-view workload (60 of 360 views -> 256^3): train the U-Net on
+    crops of generated pairs, held-out RMSE against the full-view FDK, and the
+    wall time of few-view FDK + network against full-view FDK on this GPU."""
+    from paper_2104_13248_gb300 import learned
+    t0 = time.perf_counter()
+    try:
+        r = learned.run(steps=2000, lr=5e-4, log_every=0)
+    except Exception as e:   # the line keeps the back-projection numbers either way
+        return {"error": f"{type(e).__name__}: {e}"}
+    keys = ("rmse_few_view", "rmse_few_view_plus_net", "rmse_ratio", "ms_full_view_fdk", "ms_few_view_fdk",
+            "ms_net", "speedup_vs_full_view", "net_tflops", "steps", "train_s", "heldout")
+    out = {k: r[k] for k in keys}
+    out["workload"] = "c5: 60 of 360 views, 512x512 detector -> 256^3; 3-level residual U-Net, BF16 tensor cores"
+    out["wall_s"] = time.perf_counter() - t0
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -526,6 +580,11 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(g)
 
+    # the metric's second half: the learned few-view path against the plain full-view FDK
+    learned_res = None
+    if rank == 0 and not args.no_learned and args.workload == "c3_paper" and not args.views:
+        learned_res = learned_block()
+
     # the launches inside the timed region: filter + back-projection per step
     line = {
         "metric": "fdk_backprojection_gups",
@@ -559,6 +618,8 @@ def run_ours(args):
         line["e2e"] = e2e
     if cpu:
         line["cpu_baseline"] = cpu
+    if learned_res:
+        line["learned"] = learned_res
     if rank == 0:
         print(json.dumps(line), flush=True)
     ctx.close()

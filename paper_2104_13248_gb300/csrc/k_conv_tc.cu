@@ -500,6 +500,13 @@ conv3d_fwd_tcp(const __grid_constant__ CUtensorMap xmap, int xco, const bf16 *__
         // ---- epilogue: warp w reads TMEM lanes 32 w .. 32 w + 31 (voxels x0 + 32 w + lane)
         int a = 0;
         unsigned aph = 0;
+        float bv[COUT], hwv[COUT];
+#pragma unroll
+        for (int c = 0; c < COUT; ++c) {
+            bv[c] = bias ? __ldg(bias + c) : 0.0f;
+            hwv[c] = EPI == kEpiHead ? __ldg(head.hw + c) : 0.0f;
+        }
+        const float hb = (EPI == kEpiHead && head.hb) ? __ldg(head.hb) : 0.0f;
         for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
             int okw = 0;
             if (lane == 0) okw = mbar_wait_bounded(&tfull[a], aph, timeout_ns) ? 1 : 0;
@@ -526,7 +533,7 @@ conv3d_fwd_tcp(const __grid_constant__ CUtensorMap xmap, int xco, const bf16 *__
                 const size_t vox = (((size_t)nb * d + tz * 4 + r) * h + ty) * (size_t)wd + xx;
 #pragma unroll
                 for (int c = 0; c < COUT; ++c) {
-                    const float o = v[c] + (bias ? __ldg(bias + c) : 0.0f);
+                    const float o = v[c] + bv[c];
                     v[c] = (relu && o < 0.0f) ? 0.0f : o;
                 }
                 if constexpr (EPI == kEpiF32) {
@@ -537,9 +544,8 @@ conv3d_fwd_tcp(const __grid_constant__ CUtensorMap xmap, int xco, const bf16 *__
                 } else if constexpr (EPI == kEpiHead) {
                     float o = 0.0f;
 #pragma unroll
-                    for (int c = 0; c < COUT; ++c)
-                        o = fmaf(__ldg(head.hw + c), __bfloat162float(__float2bfloat16_rn(v[c])), o);
-                    head.out[vox] = o + (head.hb ? __ldg(head.hb) : 0.0f) + (head.res ? head.res[vox] : 0.0f);
+                    for (int c = 0; c < COUT; ++c) o = fmaf(hwv[c], __bfloat162float(__float2bfloat16_rn(v[c])), o);
+                    head.out[vox] = o + hb + (head.res ? head.res[vox] : 0.0f);
                 } else {
                     uint4 *dst = reinterpret_cast<uint4 *>(reinterpret_cast<bf16 *>(y) + vox * ycs + yco);
 #pragma unroll
