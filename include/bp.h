@@ -137,6 +137,27 @@ bp_status bp_backproject_views(bp_ctx *ctx, const void *proj, bp_dtype t, int vi
                                int batch, float scale, int accumulate, void *stream);
 
 /*
+ * As bp_backproject_views, for the slices z0 .. z0+nz_slab-1 only; every
+ * other voxel of vol is left as it is. With mirror != 0 the call also
+ * computes the mirrored slices nz-z0-nz_slab .. nz-1-z0 (the middle slice
+ * of an odd nz once), in one pass of the mid-plane symmetric kernel
+ * (Section 3.1.2, Algorithm 1) where the geometry has the symmetry and the
+ * projections are FP32; this needs z0 + nz_slab <= (nz + 1) / 2. vol still
+ * points at the whole [batch][nz][ny][nx] volume. A volume computed slab by
+ * slab (the same views each time) equals the one-call result to FP32
+ * rounding, and bit for bit when nz, z0 and nz_slab are multiples of 64
+ * (the slabs then cut along the kernels' z-tiles).
+ * Used to copy finished slabs back to the host while later ones are
+ * computed, and the unit a z-slab split over GPUs would give each GPU.
+ * Errors: BP_ERR_INVALID_ARG for a slice range outside the volume or a
+ * mirrored slab reaching past the lower half; otherwise those of
+ * bp_backproject_views.
+ */
+bp_status bp_backproject_slab(bp_ctx *ctx, const void *proj, bp_dtype t, int view0, int n_views,
+                              long long proj_batch_stride, int z0, int nz_slab, int mirror,
+                              float *vol, int batch, float scale, int accumulate, void *stream);
+
+/*
  * Matched forward projector: the exact transpose of bp_backproject with the
  * same scale (same taps, same bilinear weights, same 1/w^2), so that
  * <bp_backproject(q), x> = <q, fp_project(x)> up to FP32 rounding.

@@ -48,6 +48,7 @@ PROTOTYPES = {
     "bp_filter_views": (_i, [_vp, _vp, _vp, _i, _i, _i, _vp]),
     "bp_backproject": (_i, [_vp, _vp, _i, _vp, _i, _f, _i, _vp]),
     "bp_backproject_views": (_i, [_vp, _vp, _i, _i, _i, _ll, _vp, _i, _f, _i, _vp]),
+    "bp_backproject_slab": (_i, [_vp, _vp, _i, _i, _i, _ll, _i, _i, _i, _vp, _i, _f, _i, _vp]),
     "fp_project": (_i, [_vp, _vp, _vp, _i, _f, _vp]),
     "bp_phantom_project": (_i, [_vp, _dptr, _i, _vp, _vp]),
     "bp_get_matrices": (_i, [_vp, _dptr]),

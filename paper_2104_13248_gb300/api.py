@@ -240,6 +240,28 @@ def bp_backproject_views(ctx: Context, proj: torch.Tensor, view0: int, vol: torc
     return vol
 
 
+def bp_backproject_slab(ctx: Context, proj: torch.Tensor, view0: int, z0: int, nz_slab: int, vol: torch.Tensor,
+                        mirror: bool = False, scale: float = 1.0, accumulate: bool = True) -> torch.Tensor:
+    """Back-project views view0 .. view0+n-1 into slices z0 .. z0+nz_slab-1 of vol
+    (and, with mirror, the mirrored slices nz-z0-nz_slab .. nz-1-z0); the rest
+    of vol is left as it is."""
+    if not proj.is_cuda:
+        raise ValueError("proj must be a CUDA tensor")
+    if proj.dim() == 3:
+        batch, n, bstride = 1, proj.shape[0], 0
+    else:
+        batch, n = proj.shape[0], proj.shape[1]
+        bstride = proj.stride(0)
+    block = proj if proj.dim() == 3 else proj[0]
+    if tuple(proj.shape[-2:]) != (ctx.nv, ctx.nu) or not block.is_contiguous():
+        raise ValueError("each batch entry of proj must be a contiguous (n, nv, nu) block")
+    _need_cuda(vol, "vol")
+    check(_lib.load().bp_backproject_slab(ctx.handle, _ptr(proj), _dtype_code(proj), int(view0), int(n),
+                                          int(bstride), int(z0), int(nz_slab), int(bool(mirror)), _ptr(vol), batch,
+                                          float(scale), int(bool(accumulate)), _stream(proj)), ctx.handle)
+    return vol
+
+
 def fp_project(ctx: Context, vol: torch.Tensor, proj: torch.Tensor | None = None,
                scale: float = 1.0) -> torch.Tensor:
     """Matched forward projection (exact transpose of bp_backproject with the same scale)."""
@@ -270,19 +292,23 @@ def bp_phantom_project(ctx: Context, ellipsoids, out: torch.Tensor | None = None
 
 
 class HostPipeline:
-    """FDK from host memory with the host-to-device copy overlapped.
+    """FDK from host memory with the host-to-device and device-to-host copies
+    overlapped with the computation.
 
-    Views are split into ``chunks`` blocks: block c+1 is copied on a copy
-    stream while block c is filtered and back-projected (accumulating) on
-    the compute stream; the volume is copied back at the end. The first
-    block is small (``first`` of the views), since nothing overlaps its copy;
-    the copy of a view is about 3x faster than its back-projection, so the
-    later, larger blocks always land before they are needed. Device buffers
-    are allocated once, here, and reused by every call.
+    The volume is computed in ``slabs`` parts, each a range of lower slices
+    with its mirror (one pass of the mid-plane symmetric kernel where it
+    applies). Views are split into ``chunks`` blocks: while block c+1 is
+    copied on a copy stream, block c is filtered and back-projected into the
+    first part on the compute stream. The first block is small (``first`` of
+    the views), since nothing overlaps its copy; the copy of a view is about
+    3x faster than its back-projection, so the later blocks land before they
+    are needed. The other parts then back-project every view, each part's
+    slices going back to the host while the next part is computed, so only the
+    last part's copy is exposed. Device buffers are allocated once, here.
     """
 
-    def __init__(self, ctx: Context, chunks: int = 4, dtype: torch.dtype = torch.float32,
-                 first: float = 0.04):
+    def __init__(self, ctx: Context, chunks: int = 8, dtype: torch.dtype = torch.float32,
+                 first: float = 0.04, slabs: int = 4):
         self.ctx = ctx
         self.chunks = max(1, min(int(chunks), ctx.n_views))
         # an optional small first block (fraction ``first`` of the views) shortens
@@ -292,11 +318,28 @@ class HostPipeline:
         rest = np.linspace(n0, ctx.n_views, self.chunks + (0 if n0 else 1)).round().astype(int)
         edges = ([0] if n0 else []) + list(rest)
         self.blocks = [(int(a), int(b)) for a, b in zip(edges[:-1], edges[1:]) if b > a]
+        # parts: lower-slice ranges [z0, z1) of the (nz+1)//2 lower slices, each with its mirror;
+        # edges on multiples of 64 where possible, so the parts cut along the kernels' z-tiles
+        nlow = (ctx.nz + 1) // 2
+        nparts = max(1, min(int(slabs), nlow))
+        zs = [0]
+        for k in range(1, nparts):
+            z = int(round(k * nlow / nparts / 64)) * 64
+            zs.append(z if zs[-1] < z < nlow else int(round(k * nlow / nparts)))
+        zs.append(nlow)
+        self.parts = [(a, b) for a, b in zip(zs[:-1], zs[1:]) if b > a]
         self.raw = torch.empty(ctx.proj_shape(), dtype=torch.float32, device="cuda")
         self.filt = torch.empty(ctx.proj_shape(), dtype=dtype, device="cuda")
         self.vol = torch.empty(ctx.vol_shape(), dtype=torch.float32, device="cuda")
         self.copy_stream = torch.cuda.Stream()
         self.events = [torch.cuda.Event() for _ in self.blocks]
+        self.part_done = [torch.cuda.Event() for _ in self.parts]
+
+    def _ranges(self, z0: int, z1: int):
+        """Slice ranges a part covers: [z0, z1) and its mirror (the middle slice once)."""
+        nz = self.ctx.nz
+        m0, m1 = max(nz - z1, z1), nz - z0
+        return [(z0, z1)] + ([(m0, m1)] if m1 > m0 else [])
 
     def run(self, proj_host: torch.Tensor, vol_host: torch.Tensor) -> torch.Tensor:
         """proj_host: pinned FP32 (np,nv,nu); vol_host: pinned FP32 (nz,ny,nx)."""
@@ -307,11 +350,22 @@ class HostPipeline:
                 self.raw[a:b].copy_(proj_host[a:b], non_blocking=True)
                 ev.record(self.copy_stream)
         scale = math.pi / self.ctx.n_views
+        (p0, p1) = self.parts[0]
         for i, ((a, b), ev) in enumerate(zip(self.blocks, self.events)):
             comp.wait_event(ev)
             bp_filter_views(self.ctx, self.raw[a:b], self.filt[a:b])
-            bp_backproject_views(self.ctx, self.filt[a:b], a, self.vol, scale=scale, accumulate=i > 0)
-        vol_host.copy_(self.vol, non_blocking=True)
+            bp_backproject_slab(self.ctx, self.filt[a:b], a, p0, p1 - p0, self.vol, mirror=True, scale=scale,
+                                accumulate=i > 0)
+        for k, (z0, z1) in enumerate(self.parts):
+            if k > 0:
+                bp_backproject_slab(self.ctx, self.filt, 0, z0, z1 - z0, self.vol, mirror=True, scale=scale,
+                                    accumulate=False)
+            self.part_done[k].record(comp)
+            self.copy_stream.wait_event(self.part_done[k])
+            with torch.cuda.stream(self.copy_stream):
+                for r0, r1 in self._ranges(z0, z1):
+                    vol_host[r0:r1].copy_(self.vol[r0:r1], non_blocking=True)
+        comp.wait_stream(self.copy_stream)
         return vol_host
 
 
@@ -323,6 +377,6 @@ def fdk(ctx: Context, proj: torch.Tensor, out_dtype: torch.dtype = torch.float32
 
 
 __all__ = ["Context", "BPError", "HostPipeline", "bp_filter_views", "bp_create", "bp_create_from_matrices", "bp_destroy", "bp_filter",
-           "bp_backproject", "bp_backproject_views", "fp_project", "bp_phantom_project",
+           "bp_backproject", "bp_backproject_views", "bp_backproject_slab", "fp_project", "bp_phantom_project",
            "bp_get_matrices", "bp_get_plan", "bp_set_tuning", "bp_set_pipeline_depth", "bp_set_symmetry", "bp_set_timeout",
            "bp_test_drop_view", "bp_device_status", "fdk"]

@@ -394,11 +394,8 @@ bp_status bp_filter_views(bp_ctx *ctx, const float *proj, void *out, bp_dtype ou
     return launch_filter(ctx, proj, out, out_t, (long long)batch * n_views, (cudaStream_t)stream);
 }
 
-bp_status bp_backproject_views(bp_ctx *ctx, const void *proj, bp_dtype t, int view0, int n_views,
-                               long long proj_batch_stride, float *vol, int batch, float scale,
-                               int accumulate, void *stream) {
-    if (!ctx) return fail(nullptr, BP_ERR_INVALID_ARG, "bp_backproject: NULL context");
-    ctx->err.clear();
+static bp_status check_bp_args(bp_ctx *ctx, const void *proj, bp_dtype t, int view0, int n_views,
+                               long long proj_batch_stride, const float *vol, int batch, float scale) {
     if (!proj || !vol || batch < 1) return fail(ctx, BP_ERR_INVALID_ARG, "bp_backproject: NULL pointer or batch < 1");
     if (t != BP_F32 && t != BP_F16) return fail(ctx, BP_ERR_INVALID_ARG, "bp_backproject: bad dtype");
     if (view0 < 0 || n_views < 1 || view0 + n_views > ctx->n_views)
@@ -407,8 +404,36 @@ bp_status bp_backproject_views(bp_ctx *ctx, const void *proj, bp_dtype t, int vi
         return fail(ctx, BP_ERR_INVALID_ARG, "bp_backproject: batch stride smaller than one batch entry");
     if (!aligned16(proj) || !aligned16(vol)) return fail(ctx, BP_ERR_INVALID_ARG, "bp_backproject: pointers must be 16-byte aligned");
     if (!std::isfinite(scale)) return fail(ctx, BP_ERR_INVALID_ARG, "bp_backproject: non-finite scale");
+    return BP_OK;
+}
+
+bp_status bp_backproject_views(bp_ctx *ctx, const void *proj, bp_dtype t, int view0, int n_views,
+                               long long proj_batch_stride, float *vol, int batch, float scale,
+                               int accumulate, void *stream) {
+    if (!ctx) return fail(nullptr, BP_ERR_INVALID_ARG, "bp_backproject: NULL context");
+    ctx->err.clear();
+    bp_status s = check_bp_args(ctx, proj, t, view0, n_views, proj_batch_stride, vol, batch, scale);
+    if (s != BP_OK) return s;
+    // the whole volume: the lower half and its mirror where the symmetric kernel applies
+    const bool sym = ctx->zinv && t == BP_F32 && ctx->plan.sym_bu > 0;
     return launch_backproject(ctx, proj, t, view0, n_views, proj_batch_stride, vol, batch, scale,
-                              accumulate ? 1 : 0, (cudaStream_t)stream);
+                              accumulate ? 1 : 0, (cudaStream_t)stream, 0, sym ? (ctx->nz + 1) / 2 : ctx->nz,
+                              sym ? 1 : 0);
+}
+
+bp_status bp_backproject_slab(bp_ctx *ctx, const void *proj, bp_dtype t, int view0, int n_views,
+                              long long proj_batch_stride, int z0, int nz_slab, int mirror, float *vol,
+                              int batch, float scale, int accumulate, void *stream) {
+    if (!ctx) return fail(nullptr, BP_ERR_INVALID_ARG, "bp_backproject_slab: NULL context");
+    ctx->err.clear();
+    bp_status s = check_bp_args(ctx, proj, t, view0, n_views, proj_batch_stride, vol, batch, scale);
+    if (s != BP_OK) return s;
+    if (z0 < 0 || nz_slab < 1 || z0 + nz_slab > ctx->nz)
+        return fail(ctx, BP_ERR_INVALID_ARG, "bp_backproject_slab: slice range outside the volume");
+    if (mirror && z0 + nz_slab > (ctx->nz + 1) / 2)
+        return fail(ctx, BP_ERR_INVALID_ARG, "bp_backproject_slab: a mirrored slab must lie in the lower half");
+    return launch_backproject(ctx, proj, t, view0, n_views, proj_batch_stride, vol, batch, scale,
+                              accumulate ? 1 : 0, (cudaStream_t)stream, z0, nz_slab, mirror ? 1 : 0);
 }
 
 bp_status bp_backproject(bp_ctx *ctx, const void *proj, bp_dtype t, float *vol, int batch,

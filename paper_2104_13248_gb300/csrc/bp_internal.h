@@ -94,9 +94,10 @@ bp_status cuda_fail(bp_ctx *ctx, cudaError_t e, const char *what);
 
 // Kernel launchers (one per translation unit). They validate nothing the
 // API layer already checked; they return BP_ERR_CUDA on a launch failure.
+// Slices [z0, z0 + nzs) and, with mirror, [nz - z0 - nzs, nz - z0).
 bp_status launch_backproject(bp_ctx *ctx, const void *proj, bp_dtype t, int view0, int nviews,
                              long long batch_stride, float *vol, int batch, float scale,
-                             int accumulate, cudaStream_t st);
+                             int accumulate, cudaStream_t st, int z0, int nzs, int mirror);
 bp_status launch_forward(bp_ctx *ctx, const float *vol, float *proj, int batch, float scale,
                          cudaStream_t st);
 bp_status launch_filter(bp_ctx *ctx, const float *proj, void *out, bp_dtype out_t,

@@ -18,6 +18,7 @@
 //                 on k).
 #include "geom_dev.cuh"
 
+#include <algorithm>
 #include <cstdio>
 
 namespace bp {
@@ -268,7 +269,7 @@ __global__ void __launch_bounds__(kThreads, MB)
 bp_zcol_tma(const __grid_constant__ CUtensorMap tmap, const double *__restrict__ P, int view0,
             int nviews, int nx, int ny, int nz, int bv, int align, float *__restrict__ vol,
             float scale, int accumulate, unsigned *err, unsigned long long timeout_ns,
-            int drop_view, int nst) {
+            int drop_view, int nst, int kz0, int kz1) {
     extern __shared__ __align__(128) unsigned char smem[];
     ViewRec *recs = reinterpret_cast<ViewRec *>(smem);
     unsigned long long *full = reinterpret_cast<unsigned long long *>(smem + kBarOffset);
@@ -280,9 +281,9 @@ bp_zcol_tma(const __grid_constant__ CUtensorMap tmap, const double *__restrict__
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int ntx = (nx + kTX - 1) / kTX;
     const int i0 = (blockIdx.x % ntx) * kTX, j0 = (blockIdx.x / ntx) * kTY;
-    const int k0 = blockIdx.y * TK;
+    const int k0 = kz0 + blockIdx.y * TK;   // slices [kz0, kz1) of this call
     const int b = blockIdx.z;
-    const int ex = min(kTX, nx - i0), ey = min(kTY, ny - j0), ez = min(TK, nz - k0);
+    const int ex = min(kTX, nx - i0), ey = min(kTY, ny - j0), ez = min(TK, kz1 - k0);
 
     int di = 0, dj = 0;
     if (warp < kConsumerWarps) consumer_column(warp, lane, &di, &dj);
@@ -409,7 +410,7 @@ __global__ void __launch_bounds__(kThreads, MB)
 bp_zsym_tma(const __grid_constant__ CUtensorMap tmap, const double *__restrict__ P, int view0,
             int nviews, int nx, int ny, int nz, int nv, int bv, int align, float *__restrict__ vol,
             float scale, int accumulate, unsigned *err, unsigned long long timeout_ns, int drop_view,
-            int nst) {
+            int nst, int kz0, int kz1) {
     extern __shared__ __align__(128) unsigned char smem[];
     ViewRec *recs = reinterpret_cast<ViewRec *>(smem);
     unsigned long long *full = reinterpret_cast<unsigned long long *>(smem + kBarOffset);
@@ -422,10 +423,9 @@ bp_zsym_tma(const __grid_constant__ CUtensorMap tmap, const double *__restrict__
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int ntx = (nx + kTX - 1) / kTX;
     const int i0 = (blockIdx.x % ntx) * kTX, j0 = (blockIdx.x / ntx) * kTY;
-    const int nlow = (nz + 1) / 2;
-    const int k0 = blockIdx.y * kTH;
+    const int k0 = kz0 + blockIdx.y * kTH;   // lower slices [kz0, kz1) (kz1 <= (nz + 1) / 2) and their mirrors
     const int b = blockIdx.z;
-    const int ex = min(kTX, nx - i0), ey = min(kTY, ny - j0), ez = min(kTH, nlow - k0);
+    const int ex = min(kTX, nx - i0), ey = min(kTY, ny - j0), ez = min(kTH, kz1 - k0);
 
     int di = 0, dj = 0;
     if (warp < kConsumerWarps) consumer_column(warp, lane, &di, &dj);
@@ -540,14 +540,14 @@ template <typename T, int TK>
 __global__ void __launch_bounds__(kConsumers)
 bp_zcol_ldg(const T *__restrict__ proj, long long batch_stride, const double *__restrict__ P,
             int view0, int nviews, int nu, int nv, int nx, int ny, int nz,
-            float *__restrict__ vol, float scale, int accumulate) {
+            float *__restrict__ vol, float scale, int accumulate, int kz0, int kz1) {
     __shared__ ViewRec recs[128];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int ntx = (nx + kTX - 1) / kTX;
     const int i0 = (blockIdx.x % ntx) * kTX, j0 = (blockIdx.x / ntx) * kTY;
-    const int k0 = blockIdx.y * TK;
+    const int k0 = kz0 + blockIdx.y * TK;   // slices [kz0, kz1) of this call
     const int b = blockIdx.z;
-    const int ex = min(kTX, nx - i0), ey = min(kTY, ny - j0), ez = min(TK, nz - k0);
+    const int ex = min(kTX, nx - i0), ey = min(kTY, ny - j0), ez = min(TK, kz1 - k0);
     int di, dj;
     consumer_column(warp, lane, &di, &dj);
     const bool col_ok = di < ex && dj < ey;
@@ -610,16 +610,16 @@ template <typename T>
 __global__ void __launch_bounds__(256)
 bp_voxel_gen(const T *__restrict__ proj, long long batch_stride, const double *__restrict__ P,
              int view0, int nviews, int nu, int nv, int nx, int ny, int nz,
-             float *__restrict__ vol, float scale, int accumulate) {
+             float *__restrict__ vol, float scale, int accumulate, int kz0, int kz1) {
     __shared__ ViewRecGen recs[64];
     const int tid = threadIdx.x;
     const int ntx = (nx + 7) / 8, nty = (ny + 7) / 8;
     const int t = blockIdx.x;
-    const int i0 = (t % ntx) * 8, j0 = ((t / ntx) % nty) * 8, k0 = (t / (ntx * nty)) * 4;
+    const int i0 = (t % ntx) * 8, j0 = ((t / ntx) % nty) * 8, k0 = kz0 + (t / (ntx * nty)) * 4;
     const int b = blockIdx.z;
     const int di = tid & 7, dj = (tid >> 3) & 7, dk = tid >> 6;
     const int i = i0 + di, j = j0 + dj, k = k0 + dk;
-    const bool ok = i < nx && j < ny && k < nz;
+    const bool ok = i < nx && j < ny && k < kz1;
     const float fdi = (float)di, fdj = (float)dj, fdk = (float)dk;
     const T *pb = proj + (size_t)b * batch_stride;
     float acc = 0.0f;
@@ -706,26 +706,26 @@ int plan_box_width(int need, int elem_bytes) {
 template <typename T, int TK, int BU, int MB>
 static cudaError_t launch_tma_t(const CUtensorMap &map, bp_ctx *ctx, int view0, int nviews,
                                 int bv, int align, float *vol, int batch, float scale,
-                                int accumulate, cudaStream_t st) {
+                                int accumulate, cudaStream_t st, int kz0, int kz1) {
     const int nst = ctx->plan.stages;
     const int smem = kStageOffset + nst * stage_bytes<T>(BU, bv);
     auto kern = bp_zcol_tma<T, TK, BU, MB>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    dim3 grid(((ctx->nx + kTX - 1) / kTX) * ((ctx->ny + kTY - 1) / kTY), (ctx->nz + TK - 1) / TK,
+    dim3 grid(((ctx->nx + kTX - 1) / kTX) * ((ctx->ny + kTY - 1) / kTY), (kz1 - kz0 + TK - 1) / TK,
               batch);
     kern<<<grid, kThreads, smem, st>>>(map, ctx->d_P, view0, nviews, ctx->nx, ctx->ny, ctx->nz, bv,
                                        align, vol, scale, accumulate, ctx->d_err, ctx->timeout_ns,
-                                       ctx->test_drop_view, nst);
+                                       ctx->test_drop_view, nst, kz0, kz1);
     return cudaGetLastError();
 }
 
 template <typename T, int TK, int MB>
 static cudaError_t launch_tma_bu(const CUtensorMap &map, bp_ctx *ctx, int bu, int view0,
                                  int nviews, int bv, int align, float *vol, int batch, float scale,
-                                 int accumulate, cudaStream_t st) {
+                                 int accumulate, cudaStream_t st, int kz0, int kz1) {
 #define BP_TMA_CASE(W) \
-    case W: return launch_tma_t<T, TK, W, MB>(map, ctx, view0, nviews, bv, align, vol, batch, scale, accumulate, st);
+    case W: return launch_tma_t<T, TK, W, MB>(map, ctx, view0, nviews, bv, align, vol, batch, scale, accumulate, st, kz0, kz1);
     if constexpr (sizeof(T) == 2) {
         switch (bu) {
             BP_TMA_CASE(32) BP_TMA_CASE(96) BP_TMA_CASE(160) BP_TMA_CASE(224)
@@ -743,24 +743,25 @@ static cudaError_t launch_tma_bu(const CUtensorMap &map, bp_ctx *ctx, int bu, in
 
 template <int BU>
 static cudaError_t launch_sym_t(const CUtensorMap &map, bp_ctx *ctx, int view0, int nviews, int bv,
-                                float *vol, int batch, float scale, int accumulate, cudaStream_t st) {
+                                float *vol, int batch, float scale, int accumulate, cudaStream_t st, int kz0,
+                                int kz1) {
     const int nst = ctx->plan.stages;
     const int smem = kStageOffset + nst * 2 * stage_bytes<float>(BU, bv);
     auto kern = bp_zsym_tma<BU, 2>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    dim3 grid(((ctx->nx + kTX - 1) / kTX) * ((ctx->ny + kTY - 1) / kTY), ((ctx->nz + 1) / 2 + kTH - 1) / kTH,
-              batch);
+    dim3 grid(((ctx->nx + kTX - 1) / kTX) * ((ctx->ny + kTY - 1) / kTY), (kz1 - kz0 + kTH - 1) / kTH, batch);
     kern<<<grid, kThreads, smem, st>>>(map, ctx->d_P, view0, nviews, ctx->nx, ctx->ny, ctx->nz, ctx->nv, bv, 4,
                                        vol, scale, accumulate, ctx->d_err, ctx->timeout_ns, ctx->test_drop_view,
-                                       nst);
+                                       nst, kz0, kz1);
     return cudaGetLastError();
 }
 
 static cudaError_t launch_sym(const CUtensorMap &map, bp_ctx *ctx, int bu, int view0, int nviews, int bv,
-                              float *vol, int batch, float scale, int accumulate, cudaStream_t st) {
+                              float *vol, int batch, float scale, int accumulate, cudaStream_t st, int kz0,
+                              int kz1) {
 #define BP_SYM_CASE(W) \
-    case W: return launch_sym_t<W>(map, ctx, view0, nviews, bv, vol, batch, scale, accumulate, st);
+    case W: return launch_sym_t<W>(map, ctx, view0, nviews, bv, vol, batch, scale, accumulate, st, kz0, kz1);
     switch (bu) {
         BP_SYM_CASE(48) BP_SYM_CASE(80) BP_SYM_CASE(112) BP_SYM_CASE(144) BP_SYM_CASE(176)
         BP_SYM_CASE(208) BP_SYM_CASE(240)
@@ -769,26 +770,28 @@ static cudaError_t launch_sym(const CUtensorMap &map, bp_ctx *ctx, int bu, int v
 #undef BP_SYM_CASE
 }
 
-bp_status launch_backproject(bp_ctx *ctx, const void *proj, bp_dtype t, int view0, int nviews,
-                             long long batch_stride, float *vol, int batch, float scale,
-                             int accumulate, cudaStream_t st) {
+// One launch over slices [kz0, kz1): the plain kernels, or with sym the
+// mid-plane symmetric kernel over lower slices [kz0, kz1) and their mirrors.
+// Returns BP_ERR_UNSUPPORTED (without launching) when sym is asked for but
+// the projections cannot be staged by TMA.
+static bp_status launch_range(bp_ctx *ctx, const void *proj, bp_dtype t, int view0, int nviews,
+                              long long batch_stride, float *vol, int batch, float scale, int accumulate,
+                              cudaStream_t st, int kz0, int kz1, bool sym) {
     const size_t es = (t == BP_F16) ? 2 : 4;
     const long long view_elems = (long long)ctx->nu * ctx->nv;
-    if (batch_stride == 0) batch_stride = view_elems * nviews;
     cudaError_t e = cudaSuccess;
     if (!ctx->zinv) {
-        dim3 grid(((ctx->nx + 7) / 8) * ((ctx->ny + 7) / 8) * ((ctx->nz + 3) / 4), 1, batch);
+        dim3 grid(((ctx->nx + 7) / 8) * ((ctx->ny + 7) / 8) * ((kz1 - kz0 + 3) / 4), 1, batch);
         if (t == BP_F16)
             bp_voxel_gen<__half><<<grid, 256, 0, st>>>((const __half *)proj, batch_stride,
-                ctx->d_P, view0, nviews, ctx->nu, ctx->nv, ctx->nx, ctx->ny, ctx->nz, vol, scale, accumulate);
+                ctx->d_P, view0, nviews, ctx->nu, ctx->nv, ctx->nx, ctx->ny, ctx->nz, vol, scale, accumulate, kz0, kz1);
         else
             bp_voxel_gen<float><<<grid, 256, 0, st>>>((const float *)proj, batch_stride, ctx->d_P,
-                view0, nviews, ctx->nu, ctx->nv, ctx->nx, ctx->ny, ctx->nz, vol, scale, accumulate);
+                view0, nviews, ctx->nu, ctx->nv, ctx->nx, ctx->ny, ctx->nz, vol, scale, accumulate, kz0, kz1);
         e = cudaGetLastError();
         return e == cudaSuccess ? BP_OK : cuda_fail(ctx, e, "bp_voxel_gen launch");
     }
     const Plan &pl = ctx->plan;
-    const bool sym = t == BP_F32 && pl.sym_bu > 0;
     const int bu = sym ? pl.sym_bu : (t == BP_F16) ? pl.bu16 : pl.bu;
     const int bv = sym ? pl.sym_bv : pl.bv;
     const int align = (t == BP_F16) ? 8 : 4;
@@ -810,38 +813,64 @@ bp_status launch_backproject(bp_ctx *ctx, const void *proj, bp_dtype t, int view
                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (r != CUDA_SUCCESS) tma = false;
         if (tma && sym) {
-            e = launch_sym(map, ctx, bu, view0, nviews, bv, vol, batch, scale, accumulate, st);
+            e = launch_sym(map, ctx, bu, view0, nviews, bv, vol, batch, scale, accumulate, st, kz0, kz1);
             return e == cudaSuccess ? BP_OK : cuda_fail(ctx, e, "bp_zsym_tma launch");
         }
         if (tma) {
             // variants: (voxels per thread along z, CTAs per SM the registers target)
             if (t == BP_F16) {
                 if (pl.tk == 64)
-                    e = launch_tma_bu<__half, 64, 1>(map, ctx, bu, view0, nviews, pl.bv, align, vol, batch, scale, accumulate, st);
+                    e = launch_tma_bu<__half, 64, 1>(map, ctx, bu, view0, nviews, pl.bv, align, vol, batch, scale, accumulate, st, kz0, kz1);
                 else if (pl.ctas == 3)
-                    e = launch_tma_bu<__half, 32, 3>(map, ctx, bu, view0, nviews, pl.bv, align, vol, batch, scale, accumulate, st);
+                    e = launch_tma_bu<__half, 32, 3>(map, ctx, bu, view0, nviews, pl.bv, align, vol, batch, scale, accumulate, st, kz0, kz1);
                 else
-                    e = launch_tma_bu<__half, 32, 2>(map, ctx, bu, view0, nviews, pl.bv, align, vol, batch, scale, accumulate, st);
+                    e = launch_tma_bu<__half, 32, 2>(map, ctx, bu, view0, nviews, pl.bv, align, vol, batch, scale, accumulate, st, kz0, kz1);
             } else {
                 if (pl.tk == 64)
-                    e = launch_tma_bu<float, 64, 1>(map, ctx, bu, view0, nviews, pl.bv, align, vol, batch, scale, accumulate, st);
+                    e = launch_tma_bu<float, 64, 1>(map, ctx, bu, view0, nviews, pl.bv, align, vol, batch, scale, accumulate, st, kz0, kz1);
                 else if (pl.ctas == 3)
-                    e = launch_tma_bu<float, 32, 3>(map, ctx, bu, view0, nviews, pl.bv, align, vol, batch, scale, accumulate, st);
+                    e = launch_tma_bu<float, 32, 3>(map, ctx, bu, view0, nviews, pl.bv, align, vol, batch, scale, accumulate, st, kz0, kz1);
                 else
-                    e = launch_tma_bu<float, 32, 2>(map, ctx, bu, view0, nviews, pl.bv, align, vol, batch, scale, accumulate, st);
+                    e = launch_tma_bu<float, 32, 2>(map, ctx, bu, view0, nviews, pl.bv, align, vol, batch, scale, accumulate, st, kz0, kz1);
             }
             return e == cudaSuccess ? BP_OK : cuda_fail(ctx, e, "bp_zcol_tma launch");
         }
     }
-    dim3 grid(((ctx->nx + kTX - 1) / kTX) * ((ctx->ny + kTY - 1) / kTY), (ctx->nz + 31) / 32, batch);
+    if (sym) return BP_ERR_UNSUPPORTED;
+    dim3 grid(((ctx->nx + kTX - 1) / kTX) * ((ctx->ny + kTY - 1) / kTY), (kz1 - kz0 + 31) / 32, batch);
     if (t == BP_F16)
         bp_zcol_ldg<__half, 32><<<grid, kConsumers, 0, st>>>((const __half *)proj, batch_stride,
-            ctx->d_P, view0, nviews, ctx->nu, ctx->nv, ctx->nx, ctx->ny, ctx->nz, vol, scale, accumulate);
+            ctx->d_P, view0, nviews, ctx->nu, ctx->nv, ctx->nx, ctx->ny, ctx->nz, vol, scale, accumulate, kz0, kz1);
     else
         bp_zcol_ldg<float, 32><<<grid, kConsumers, 0, st>>>((const float *)proj, batch_stride,
-            ctx->d_P, view0, nviews, ctx->nu, ctx->nv, ctx->nx, ctx->ny, ctx->nz, vol, scale, accumulate);
+            ctx->d_P, view0, nviews, ctx->nu, ctx->nv, ctx->nx, ctx->ny, ctx->nz, vol, scale, accumulate, kz0, kz1);
     e = cudaGetLastError();
     return e == cudaSuccess ? BP_OK : cuda_fail(ctx, e, "bp_zcol_ldg launch");
+}
+
+// Slices [z0, z0 + nzs) and, with mirror, the mirrored slices
+// [nz - z0 - nzs, nz - z0) (the caller has checked z0 + nzs <= (nz + 1) / 2):
+// one symmetric launch where the plan has the symmetric kernel and the
+// projections are FP32, else plain launches over the two ranges (the middle
+// slice of an odd nz only once).
+bp_status launch_backproject(bp_ctx *ctx, const void *proj, bp_dtype t, int view0, int nviews,
+                             long long batch_stride, float *vol, int batch, float scale,
+                             int accumulate, cudaStream_t st, int z0, int nzs, int mirror) {
+    const long long view_elems = (long long)ctx->nu * ctx->nv;
+    if (batch_stride == 0) batch_stride = view_elems * nviews;
+    const int z1 = z0 + nzs;
+    if (mirror && ctx->zinv && t == BP_F32 && ctx->plan.sym_bu > 0) {
+        bp_status s = launch_range(ctx, proj, t, view0, nviews, batch_stride, vol, batch, scale, accumulate, st,
+                                   z0, z1, true);
+        if (s != BP_ERR_UNSUPPORTED) return s;
+    }
+    bp_status s = launch_range(ctx, proj, t, view0, nviews, batch_stride, vol, batch, scale, accumulate, st, z0,
+                               z1, false);
+    if (s != BP_OK || !mirror) return s;
+    const int m0 = std::max(ctx->nz - z1, z1), m1 = ctx->nz - z0;
+    if (m1 <= m0) return BP_OK;
+    return launch_range(ctx, proj, t, view0, nviews, batch_stride, vol, batch, scale, accumulate, st, m0, m1,
+                        false);
 }
 
 }  // namespace bp
