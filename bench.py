@@ -158,24 +158,51 @@ class ClockSampler:
 def cpu_baseline(g, budget_s=15.0, max_slices=32, chunk=4):
     """The FP64 oracle back-projecting a z-slab of the workload on the host
     cores (bounded: stops after ~budget_s seconds). Data: seeded uniform
-    projections (the oracle's cost does not depend on the values)."""
+    projections, FP32 values (the oracle's cost does not depend on them).
+    Returns the timing record and (k0, slices, projections, oracle slab) for
+    the parity check of the GPU volume."""
     import numpy as np
 
     import oracle
     from paper_2104_13248_gb300 import inputs
     P = oracle.matrices(g)
-    q = inputs.uniform_array(99, (g["np"], g["nv"], g["nu"]), -1.0, 1.0)
+    q32 = inputs.uniform_array(99, (g["np"], g["nv"], g["nu"]), -1.0, 1.0).astype(np.float32)
+    q = q32.astype(np.float64)
     k0 = g["nz"] // 2 - max_slices // 2
     done, t = 0, 0.0
+    parts = []
     while done < max_slices and t < budget_s:
         t0 = time.perf_counter()
-        oracle.backproject_slab(P, q, g["nx"], g["ny"], k0 + done, chunk, math.pi / g["np"])
+        parts.append(oracle.backproject_slab(P, q, g["nx"], g["ny"], k0 + done, chunk, math.pi / g["np"]))
         t += time.perf_counter() - t0
         done += chunk
     upd = float(g["nx"]) * g["ny"] * done * g["np"]
-    return {"value": upd / t / 1e9, "unit": "GUPS", "cores": oracle.num_threads(), "kind": "oracle",
-            "sample": f"FP64 oracle back-projection of slices {k0}..{k0 + done - 1} "
-                      f"({g['nx']}x{g['ny']}x{done} voxels x {g['np']} views, {upd:.3g} updates, {t:.1f} s)"}
+    rec = {"value": upd / t / 1e9, "unit": "GUPS", "cores": oracle.num_threads(), "kind": "oracle",
+           "sample": f"FP64 oracle back-projection of slices {k0}..{k0 + done - 1} "
+                     f"({g['nx']}x{g['ny']}x{done} voxels x {g['np']} views, {upd:.3g} updates, {t:.1f} s)"}
+    return rec, (k0, done, q32, np.concatenate(parts, axis=0))
+
+
+def slab_parity(ctx, g, sample) -> dict:
+    """Max error of the GPU volume against the oracle's slab (relative to the
+    slab's largest value): the FP32 path the step times, and FP16-stored
+    projections (whose oracle input is the unquantised FP32 values)."""
+    import numpy as np
+    import torch
+
+    from paper_2104_13248_gb300 import api
+    k0, n, q32, ref = sample
+    scale = math.pi / g["np"]
+    out = {"slices": f"{k0}..{k0 + n - 1}", "metric": "max|gpu - oracle| / max|oracle|",
+           "tolerance_f32": 1e-5, "tolerance_f16": 2e-3}
+    dq = torch.from_numpy(q32).cuda()
+    for key, qd in (("f32", dq), ("f16", dq.half())):
+        vol = api.bp_backproject(ctx, qd, scale=scale)
+        got = vol[k0:k0 + n].double().cpu().numpy()
+        out["max_rel_err_" + key] = float(np.abs(got - ref).max() / np.abs(ref).max())
+        del vol
+    api.bp_device_status(ctx)
+    return out
 
 
 def run_reference(args):
@@ -580,9 +607,10 @@ def run_ours(args):
                "ms_per_step": t_e2e * 1e3, "ms_per_step_mean": 1e3 * sum(ts) / len(ts), "steps": n_e2e,
                "pipeline": f"{len(pipe.blocks)} view blocks, {len(pipe.parts)} slab parts with mirrors"}
 
-    cpu = None
+    cpu = parity = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(g)
+        cpu, sample = cpu_baseline(g)
+        parity = slab_parity(ctx, g, sample)
 
     # the metric's second half: the learned few-view path against the plain full-view FDK
     learned_res = None
@@ -622,6 +650,8 @@ def run_ours(args):
         line["e2e"] = e2e
     if cpu:
         line["cpu_baseline"] = cpu
+    if parity:
+        line["parity"] = parity
     if learned_res:
         line["learned"] = learned_res
     if rank == 0:
