@@ -476,6 +476,10 @@ def learned_block() -> dict:
     keys = ("rmse_few_view", "rmse_few_view_plus_net", "rmse_ratio", "ms_full_view_fdk", "ms_few_view_fdk",
             "ms_net", "speedup_vs_full_view", "net_tflops", "steps", "train_s", "heldout")
     out = {k: r[k] for k in keys}
+    peaks, src = measured_peaks()
+    peak = float(peaks.get("bf16_tflops", 1900.0))
+    out["net_frac_of_bf16_peak"] = r["net_tflops"] / peak
+    out["bf16_peak_tflops"] = f"{peak:.1f} ({src}, burst)"
     out["workload"] = "c5: 60 of 360 views, 512x512 detector -> 256^3; 3-level residual U-Net, BF16 tensor cores"
     out["wall_s"] = time.perf_counter() - t0
     return out
