@@ -187,35 +187,44 @@ __device__ __forceinline__ void store_column(float *__restrict__ vol, const floa
 // ---------------------------------------------------------------------------
 constexpr int kTH = 16;   // lower voxels per thread
 
+// Written with the float2 pair intrinsics (__ffma2_rn, __fadd2_rn / _rd;
+// subtraction as addition of the negated pair, exact) for the taps and
+// lerps, while the accumulators stay 64-bit: measured on c3, 1774 GUPS
+// against 1750 with inline f32x2 assembly throughout and 1754 with float2
+// accumulators as well.
 template <int BU>
 __device__ __forceinline__ void accumulate_sym_pairs(const float *__restrict__ lo,
                                                      const float *__restrict__ hi_top, const ColView &c,
                                                      f2 *acc_lo, f2 *acc_hi) {
     // lo = lower box + c.cu; hi_top = mirrored box + (BV-1)*BU + c.cu
-    const f2 M2 = pk(kMagic, kMagic), FU = pk(c.fu, c.fu), WT = pk(c.wt, c.wt);
+    const float2 M2 = make_float2(kMagic, kMagic), NM2 = make_float2(-kMagic, -kMagic);
+    const float2 FU = make_float2(c.fu, c.fu), WT = make_float2(c.wt, c.wt);
 #pragma unroll
     for (int m = 0; m < kTH / 2; ++m) {
-        const float va = fmaf((float)(2 * m), c.dv, c.v0);
-        const float vb = fmaf((float)(2 * m + 1), c.dv, c.v0);
-        const f2 V = pk(va, vb);
-        const f2 TV = add2_rd(V, M2);
-        const f2 FV = sub2(V, sub2(TV, M2));
-        float ta, tb;
-        upk(TV, ta, tb);
-        const int ra = __float_as_int(ta) - kMagicBits, rb = __float_as_int(tb) - kMagicBits;
+        const float2 V = make_float2(fmaf((float)(2 * m), c.dv, c.v0), fmaf((float)(2 * m + 1), c.dv, c.v0));
+        const float2 TV = __fadd2_rd(V, M2);
+        const float2 FL = __fadd2_rn(TV, NM2);
+        const float2 FV = __fadd2_rn(V, make_float2(-FL.x, -FL.y));
+        const int ra = __float_as_int(TV.x) - kMagicBits, rb = __float_as_int(TV.y) - kMagicBits;
         const float *pa = lo + ra * BU, *pb = lo + rb * BU;
-        const f2 Q00 = pk(pa[0], pb[0]), Q01 = pk(pa[1], pb[1]);
-        const f2 Q10 = pk(pa[BU], pb[BU]), Q11 = pk(pa[BU + 1], pb[BU + 1]);
-        const f2 S0 = fma2(FU, sub2(Q01, Q00), Q00);
-        const f2 S1 = fma2(FU, sub2(Q11, Q10), Q10);
-        acc_lo[m] = fma2(WT, fma2(FV, sub2(S1, S0), S0), acc_lo[m]);
+        const float2 Q00 = make_float2(pa[0], pb[0]), Q01 = make_float2(pa[1], pb[1]);
+        const float2 Q10 = make_float2(pa[BU], pb[BU]), Q11 = make_float2(pa[BU + 1], pb[BU + 1]);
+        const float2 S0 = __ffma2_rn(FU, __fadd2_rn(Q01, make_float2(-Q00.x, -Q00.y)), Q00);
+        const float2 S1 = __ffma2_rn(FU, __fadd2_rn(Q11, make_float2(-Q10.x, -Q10.y)), Q10);
+        float2 al;
+        upk(acc_lo[m], al.x, al.y);
+        al = __ffma2_rn(WT, __ffma2_rn(FV, __fadd2_rn(S1, make_float2(-S0.x, -S0.y)), S0), al);
+        acc_lo[m] = pk(al.x, al.y);
         // mirror: row BV-1-r (weight 1-f) and the row above it, BV-2-r (weight f)
         const float *qa = hi_top - ra * BU, *qb = hi_top - rb * BU;
-        const f2 R00 = pk(qa[0], qb[0]), R01 = pk(qa[1], qb[1]);
-        const f2 R10 = pk(qa[-BU], qb[-BU]), R11 = pk(qa[1 - BU], qb[1 - BU]);
-        const f2 T0 = fma2(FU, sub2(R01, R00), R00);
-        const f2 T1 = fma2(FU, sub2(R11, R10), R10);
-        acc_hi[m] = fma2(WT, fma2(FV, sub2(T1, T0), T0), acc_hi[m]);
+        const float2 R00 = make_float2(qa[0], qb[0]), R01 = make_float2(qa[1], qb[1]);
+        const float2 R10 = make_float2(qa[-BU], qb[-BU]), R11 = make_float2(qa[1 - BU], qb[1 - BU]);
+        const float2 T0 = __ffma2_rn(FU, __fadd2_rn(R01, make_float2(-R00.x, -R00.y)), R00);
+        const float2 T1 = __ffma2_rn(FU, __fadd2_rn(R11, make_float2(-R10.x, -R10.y)), R10);
+        float2 ah;
+        upk(acc_hi[m], ah.x, ah.y);
+        ah = __ffma2_rn(WT, __ffma2_rn(FV, __fadd2_rn(T1, make_float2(-T0.x, -T0.y)), T0), ah);
+        acc_hi[m] = pk(ah.x, ah.y);
     }
 }
 
