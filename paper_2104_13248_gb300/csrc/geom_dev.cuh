@@ -95,6 +95,16 @@ __device__ inline void make_rec_gen(const double *P, int i0, int j0, int k0, Vie
     r->pad0 = r->pad1 = 0;
 }
 
+// 1/w for the per-(column, view) setup of the z-column kernels (the
+// back-projectors and their transpose use the same one, so their taps and
+// weights coincide): the hardware approximation, within 1 ulp, instead of the
+// correctly rounded reciprocal's longer sequence. w is near 1 here.
+__device__ __forceinline__ float col_rcp(float w) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(w));
+    return r;
+}
+
 // floor(x) for |x| < 2^22 without a conversion instruction: adding 1.5*2^23
 // with round-toward-minus-infinity leaves floor(x) in the low mantissa bits.
 constexpr float kMagic = 12582912.0f;      // 1.5 * 2^23

@@ -89,7 +89,7 @@ template <int BU>
 __device__ __forceinline__ bool column_view(const ViewRec &r, float fdi, float fdj, int ez, int bv,
                                             unsigned *err, ColView &c) {
     float W = fmaf(r.Wj, fdj, fmaf(r.Wi, fdi, r.W0));
-    float inv = __frcp_rn(W);
+    float inv = col_rcp(W);
     float uL = fmaf(r.Nuj, fdj, fmaf(r.Nui, fdi, r.Nu0)) * inv;
     c.v0 = fmaf(r.Nvj, fdj, fmaf(r.Nvi, fdi, r.Nv0)) * inv;
     c.dv = r.Nvk * inv;
@@ -199,9 +199,10 @@ __device__ __forceinline__ void accumulate_sym_pairs(const float *__restrict__ l
     // lo = lower box + c.cu; hi_top = mirrored box + (BV-1)*BU + c.cu
     const float2 M2 = make_float2(kMagic, kMagic), NM2 = make_float2(-kMagic, -kMagic);
     const float2 FU = make_float2(c.fu, c.fu), WT = make_float2(c.wt, c.wt);
+    const float2 DV2 = make_float2(c.dv, c.dv), V02 = make_float2(c.v0, c.v0);
 #pragma unroll
     for (int m = 0; m < kTH / 2; ++m) {
-        const float2 V = make_float2(fmaf((float)(2 * m), c.dv, c.v0), fmaf((float)(2 * m + 1), c.dv, c.v0));
+        const float2 V = __ffma2_rn(make_float2((float)(2 * m), (float)(2 * m + 1)), DV2, V02);
         const float2 TV = __fadd2_rd(V, M2);
         const float2 FL = __fadd2_rn(TV, NM2);
         const float2 FV = __fadd2_rn(V, make_float2(-FL.x, -FL.y));
@@ -582,7 +583,7 @@ bp_zcol_ldg(const T *__restrict__ proj, long long batch_stride, const double *__
             const ViewRec r = recs[n];
             const T *img = pb + (size_t)(cb + n) * nu * nv;
             float W = fmaf(r.Wj, fdj, fmaf(r.Wi, fdi, r.W0));
-            float inv = __frcp_rn(W);
+            float inv = col_rcp(W);
             float uL = fmaf(r.Nuj, fdj, fmaf(r.Nui, fdi, r.Nu0)) * inv;
             float v0 = fmaf(r.Nvj, fdj, fmaf(r.Nvi, fdi, r.Nv0)) * inv;
             float dv = r.Nvk * inv;

@@ -94,7 +94,7 @@ fp_zcol(const float *__restrict__ vol, const double *__restrict__ P, int nviews,
             float umin = 3e38f, umax = -3e38f, vmin = 3e38f, vmax = -3e38f;
             if (col_ok) {
                 float W = fmaf(r.Wj, fdj, fmaf(r.Wi, fdi, r.W0));
-                float inv = __frcp_rn(W);
+                float inv = col_rcp(W);
                 float uL = fmaf(r.Nuj, fdj, fmaf(r.Nui, fdi, r.Nu0)) * inv;
                 c.v0 = fmaf(r.Nvj, fdj, fmaf(r.Nvi, fdi, r.Nv0)) * inv;
                 c.dv = r.Nvk * inv;
