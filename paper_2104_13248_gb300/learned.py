@@ -146,8 +146,8 @@ def time_paths(maker: PairMaker, net: UNet, seed: int, reps: int = 5):
     return t_full, t_few, t_net
 
 
-def run(preset: str = "c5_learned", steps: int = 3000, crops_per_volume: int = 4, heldout: int | None = None,
-        lr: float = 1e-3, log_every: int = 250) -> dict:
+def run(preset: str = "c5_learned", steps: int = 4000, crops_per_volume: int = 4, heldout: int | None = None,
+        lr: float = 5e-4, log_every: int = 250) -> dict:
     """The few-view workload end to end; returns a JSON-able summary."""
     p = inputs.preset(preset)
     g = p["geom"]
@@ -182,6 +182,6 @@ def run(preset: str = "c5_learned", steps: int = 3000, crops_per_volume: int = 4
 
 if __name__ == "__main__":
     import sys
-    steps = int(sys.argv[1]) if len(sys.argv) > 1 else 3000
-    lr = float(sys.argv[2]) if len(sys.argv) > 2 else 1e-3
+    steps = int(sys.argv[1]) if len(sys.argv) > 1 else 4000
+    lr = float(sys.argv[2]) if len(sys.argv) > 2 else 5e-4
     print(json.dumps(run(steps=steps, lr=lr)))
