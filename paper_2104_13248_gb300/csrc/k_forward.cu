@@ -2,11 +2,12 @@
 // back-projection of Listing 1. Every voxel value, times scale / w^2, is
 // scattered to the same four detector taps with the same bilinear weights
 // the back-projector reads them with. A CTA owns a 32 x 8 x TK tile of
-// voxels (one thread per z-column, the tile's values held in registers);
-// per view it accumulates the tile's detector footprint in a shared-memory
-// box with shared atomics and then adds the box to the projection with one
-// global atomic per touched pixel. Records (geometry relative to the box
-// origin) are the ones the back-projector uses, so the taps coincide.
+// voxels; each warp owns an 8 x 4 patch of its columns, one lane per voxel
+// of a column, the patch's values held in registers. Per view a warp
+// accumulates its patch's detector footprint in a private shared-memory box
+// and then adds the box to the projection with one global reduction per
+// touched pixel. Records (geometry relative to the box origin) are the ones
+// the back-projector uses, so the taps coincide.
 #include "geom_dev.cuh"
 
 namespace bp {
@@ -123,65 +124,90 @@ fp_zcol(const float *__restrict__ vol, const double *__restrict__ P, int nviews,
             const bool fits = any && (__float_as_int(__fadd_rd(umax, kMagic)) - kMagicBits) + 1 - uo <= wbu - 1 &&
                               (__float_as_int(__fadd_rd(vmax, kMagic)) - kMagicBits) + 1 - vo <= wbv - 1;
             if (any && !fits && lane == 0) atomicOr(err, DEV_ERR_FOOTPRINT);
-            if (c.ok) {
-                c.cu -= uo;   // column relative to the warp box
-                if (!(c.dv >= 1.0f)) {
-                    c.ok = 0;   // rows of consecutive voxels could coincide
-                    atomicOr(err, DEV_ERR_FOOTPRINT);
-                }
-            }
+            if (c.ok) c.cu -= uo;   // column relative to the warp box
+            // At least one detector row per voxel in every column: the lanes of a
+            // column then write different rows, so plain read-add-writes are safe;
+            // otherwise the warp adds with shared-memory reductions for this view.
+            const bool rmw = __all_sync(0xffffffffu, !c.ok || fabsf(c.dv) >= 1.0f);
             cols[tid] = c;
             __syncwarp();
             if (any && fits) {
                 const float fl = (float)lane;
-#pragma unroll
-                for (int cix = 0; cix < 32; ++cix) {
-                    const FpCol cc = cols[warp * 32 + cix];
-                    if (!cc.ok) continue;   // uniform across the warp
+                // Lane l adds voxel k0 + l of each column to rows r, r + 1 and
+                // columns cu, cu + 1. With the read-add-write form, the two taps
+                // of one row go together (no other lane touches that row), and a
+                // warp barrier separates them from the next row's taps (lane
+                // l + 1's top row can be lane l's bottom row) and from the next
+                // column.
+                auto scatter = [&](const FpCol &cc, float xv, bool plain) {
                     float v = fmaf(fl, cc.dv, cc.v0);
                     float tv = __fadd_rd(v, kMagic);
                     float fv = v - (tv - kMagic);
                     int row = __float_as_int(tv) - kMagicBits - vo;
-                    float val = cc.wt * x[cix];
+                    float val = cc.wt * xv;
                     float a1 = fv * val, a0 = val - a1;   // (1-fv) val, fv val
-                    const bool act = lane < ez && val != 0.0f;
+                    const bool act = lane < ez;
                     float *p = wbox + row * wpitch + cc.cu;
                     const float gu = 1.0f - cc.fu;
-                    // four phases: within each, the lanes' addresses differ
-                    if (act) p[0] += gu * a0;
-                    __syncwarp();
-                    if (act) p[1] += cc.fu * a0;
-                    __syncwarp();
-                    if (act) p[wpitch] += gu * a1;
-                    __syncwarp();
-                    if (act) p[wpitch + 1] += cc.fu * a1;
+                    if (plain) {
+                        if (act) {
+                            p[0] += gu * a0;
+                            p[1] += cc.fu * a0;
+                        }
+                        __syncwarp();
+                        if (act) {
+                            p[wpitch] += gu * a1;
+                            p[wpitch + 1] += cc.fu * a1;
+                        }
+                        __syncwarp();
+                    } else if (act) {
+                        red_add_shared(p, gu * a0);
+                        red_add_shared(p + 1, cc.fu * a0);
+                        red_add_shared(p + wpitch, gu * a1);
+                        red_add_shared(p + wpitch + 1, cc.fu * a1);
+                    }
+                };
+                if (rmw) {
+#pragma unroll
+                    for (int cix = 0; cix < 32; ++cix) {
+                        const FpCol cc = cols[warp * 32 + cix];
+                        if (cc.ok) scatter(cc, x[cix], true);   // uniform across the warp
+                    }
+                } else {
+#pragma unroll
+                    for (int cix = 0; cix < 32; ++cix) {
+                        const FpCol cc = cols[warp * 32 + cix];
+                        if (cc.ok) scatter(cc, x[cix], false);
+                    }
                     __syncwarp();
                 }
                 // flush the warp's box into the projection (inside the detector only)
                 float *img = pb + (size_t)(cb + n) * nu * nv;
                 const int rows_used = min(wbv, (__float_as_int(__fadd_rd(vmax, kMagic)) - kMagicBits) + 2 - vo);
                 const int cols_used = min(wbu, (__float_as_int(__fadd_rd(umax, kMagic)) - kMagicBits) + 2 - uo);
-                // flattened over the used rows x columns so every lane has work; the
-                // row is (t + 0.5) / cols rounded down in FP32 (within one of the exact
-                // quotient) and corrected by one step. Every value read is zeroed
-                // again, so the box is clean for the next view (the scatter writes
-                // only inside this region).
-                const float inv_cols = 1.0f / (float)cols_used;
-                for (int t = lane; t < rows_used * cols_used; t += 32) {
-                    int rr = (int)(((float)t + 0.5f) * inv_cols), ccol = t - rr * cols_used;
-                    if (ccol < 0) {
-                        --rr;
-                        ccol += cols_used;
-                    } else if (ccol >= cols_used) {
-                        ++rr;
-                        ccol -= cols_used;
+                // Lanes take g rows of cw columns at a time (cw = the used width, at
+                // most 32; G = 32 / cw rows per pass), so narrow boxes keep most lanes
+                // busy. Every value read is zeroed again, so the box is clean for the
+                // next view (the scatter writes only inside this region).
+                const int cw = min(cols_used, 32);
+                const int G = 32 / cw;
+                const int g = lane / cw, cl = lane - g * cw;
+                for (int c0 = 0; c0 < cols_used; c0 += cw) {
+                    const int ccol = c0 + cl;
+                    const int c_ = r.u_box + uo + ccol;
+                    const bool cok = g < G && ccol < cols_used;
+                    const bool cin = cok && c_ >= 0 && c_ < nu;
+                    float *cell = wbox + g * wpitch + ccol;
+                    int r_ = r.v_box + vo + g;
+                    for (int rr = g; rr < rows_used; rr += G) {
+                        if (cok) {
+                            const float val = *cell;
+                            *cell = 0.0f;
+                            if (cin && val != 0.0f && r_ >= 0 && r_ < nv) atomicAdd(img + (size_t)r_ * nu + c_, val);
+                        }
+                        cell += G * wpitch;
+                        r_ += G;
                     }
-                    float *cell = wbox + rr * wpitch + ccol;
-                    const float val = *cell;
-                    *cell = 0.0f;
-                    const int r_ = r.v_box + vo + rr, c_ = r.u_box + uo + ccol;
-                    if (val != 0.0f && r_ >= 0 && r_ < nv && c_ >= 0 && c_ < nu)
-                        atomicAdd(img + (size_t)r_ * nu + c_, val);
                 }
             }
         }

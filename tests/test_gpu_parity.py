@@ -144,6 +144,42 @@ def test_backproject_ragged(dims, dtype):
     assert rel(vol, ref) <= 5e-5
 
 
+FP_GEOMS = {
+    # the ragged tiles of the back-projection tests
+    **{"ragged_%dx%dx%d" % (d["nx"], d["ny"], d["nz"]): dict(
+        sid=600.0, sdd=900.0, du=1.0, dv=1.1, u_off=1.7, v_off=-2.3, sx=1.3, sy=1.2, sz=1.1, ox=0.7, oy=-1.4,
+        oz=2.1, **d) for d in RAGGED},
+    # a short source distance: the depth, and so the rows, of the columns of one
+    # 8 x 4 patch differ enough that many taps fall beyond the lanes' windows
+    "short_sid": dict(sid=120.0, sdd=260.0, du=1.0, dv=1.0, u_off=0.3, v_off=0.4, sx=0.8, sy=0.8, sz=0.8,
+                      ox=0.0, oy=0.0, oz=0.0, nu=120, nv=110, nx=40, ny=36, nz=70),
+    # less than one detector row per slice
+    "dv_below_1": dict(sid=600.0, sdd=900.0, du=1.0, dv=1.2, u_off=0.0, v_off=0.0, sx=1.0, sy=1.0, sz=0.5,
+                       ox=0.0, oy=0.0, oz=0.0, nu=80, nv=60, nx=33, ny=20, nz=70),
+}
+
+
+@pytest.mark.parametrize("name", sorted(FP_GEOMS))
+def test_forward_project_ragged(name):
+    rng = np.random.default_rng(4)
+    g = dict(FP_GEOMS[name], np=7, angles=np.sort(rng.uniform(0, 2 * np.pi, 7)))
+    P = oracle.matrices(g)
+    x = inputs.uniform_array(23, (g["nz"], g["ny"], g["nx"]), 0, 1).astype(np.float32)
+    q = inputs.uniform_array(24, (g["np"], g["nv"], g["nu"]), -1, 1).astype(np.float32)
+    ref = oracle.forward_project(P, x, g["nu"], g["nv"], 0.5)
+    with api.bp_create(g) as ctx:
+        xd = torch.from_numpy(x).cuda()
+        fx = api.fp_project(ctx, xd, scale=0.5)
+        bq = api.bp_backproject(ctx, torch.from_numpy(q).cuda(), scale=0.5)
+        api.bp_device_status(ctx)
+        lhs = torch.dot(bq.double().flatten(), xd.double().flatten()).item()
+        rhs = torch.dot(torch.from_numpy(q).cuda().double().flatten(), fx.double().flatten()).item()
+        norm = bq.double().norm().item() * float(np.linalg.norm(x))
+    # FP32 positions and reductions in another order: the back-projection's ragged bound
+    assert rel(fx.cpu().numpy(), ref) <= 5e-5
+    assert abs(lhs - rhs) <= 1e-6 * norm
+
+
 def test_backproject_batch_accumulate_and_view_chunks(c1):
     g = c1["g"]
     q = c1["q"]
