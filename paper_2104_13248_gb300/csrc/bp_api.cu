@@ -193,19 +193,12 @@ static void make_plan(bp_ctx *ctx) {
             pl.sym_bv = sbv;
         }
     }
-    // forward projector: per-warp boxes of an 8 x 4 column patch, 32 voxels deep
-    // (+1 column and row of slack for the FP32 corner rounding)
+    // forward projector: lane windows as wide as the u footprint of an 8 x 4
+    // column patch (+1 column of slack for the FP32 corner rounding)
     int wbu, wbv;
     max_footprint(ctx, 8, 4, 32, 1, &wbu, &wbv);
     wbu += 1;
-    wbv += 1;
-    const int fp_smem = 256 * 48 + 256 * 32 + 8 * (wbu | 1) * wbv * 4;
-    if (pl.bu > 0 && fp_smem <= 227 * 1024) {
-        pl.fp_wbu = wbu;
-        pl.fp_wbv = wbv;
-    } else {
-        pl.fp_wbu = pl.fp_wbv = -1;
-    }
+    pl.fp_wbu = (pl.bu > 0 && fp_smem_bytes(wbu) <= 227 * 1024) ? wbu : -1;
 }
 
 // Ramp filter tables: real spectrum of the circularly embedded Ram-Lak

@@ -53,7 +53,7 @@ struct Plan {
     int stages;              // pipeline depth (views in flight), <= the requested depth
     int sym_bu, sym_bv;      // mid-plane symmetry kernel: staged box (16-voxel half columns), -1 if off
     int ctas;                // CTAs per SM the TK=32 kernel's register budget targets (2 or 3)
-    int fp_wbu, fp_wbv;      // forward projector: per-warp box (8 x 4 columns x 32 voxels), -1 if unusable
+    int fp_wbu;              // forward projector: window width in columns (8 x 4 column patch), -1 if unusable
 };
 
 }  // namespace bp
@@ -100,6 +100,8 @@ bp_status launch_backproject(bp_ctx *ctx, const void *proj, bp_dtype t, int view
                              int accumulate, cudaStream_t st, int z0, int nzs, int mirror);
 bp_status launch_forward(bp_ctx *ctx, const float *vol, float *proj, int batch, float scale,
                          cudaStream_t st);
+// Dynamic shared memory of the forward projector for windows wc columns wide.
+int fp_smem_bytes(int wc);
 bp_status launch_filter(bp_ctx *ctx, const float *proj, void *out, bp_dtype out_t,
                         long long n_views_total, cudaStream_t st);
 bp_status launch_phantom(bp_ctx *ctx, const double *d_ell, int n_ell, float *proj,

@@ -1,49 +1,72 @@
 // Matched voxel-driven forward projector: the exact transpose of the
 // back-projection of Listing 1. Every voxel value, times scale / w^2, is
 // scattered to the same four detector taps with the same bilinear weights
-// the back-projector reads them with. A CTA owns a 32 x 8 x TK tile of
+// the back-projector reads them with. A CTA owns a 32 x 8 x 32 tile of
 // voxels; each warp owns an 8 x 4 patch of its columns, one lane per voxel
-// of a column, the patch's values held in registers. Per view a warp
-// accumulates its patch's detector footprint in a private shared-memory box
-// and then adds the box to the projection with one global reduction per
-// touched pixel. Records (geometry relative to the box origin) are the ones
-// the back-projector uses, so the taps coincide.
+// of a column, the patch's values held in registers. Records (geometry
+// relative to the box origin) are the ones the back-projector uses, so the
+// taps coincide.
+//
+// Per view, each lane accumulates its voxels' taps in a private window of
+// kFpWinRows detector rows in shared memory: within a small patch the
+// columns' depths differ by well under one percent, so the rows lane l's
+// voxel reaches in the patch's 32 columns stay within two rows of a common
+// lower bound. Private windows keep the scatter free of bank conflicts and
+// of hazards between lanes (no warp barriers), where one box shared by the
+// warp folds the column's ~2 x 32 rows onto 32 banks. The windows then go
+// to the projection with one global reduction per window cell, so the
+// overlapping windows add up there. A tap beyond its lane's window
+// (columns whose rows drift further apart) is added to the projection
+// directly.
 #include "geom_dev.cuh"
 
 namespace bp {
 
 constexpr int kFpTX = 32, kFpTY = 8, kFpTK = 32;
-
-// Shared-memory reduction without a return value (red.shared.add.f32): the
-// plain atomicAdd on a float in shared memory can come out as a
-// compare-and-swap loop.
-__device__ __forceinline__ void red_add_shared(float *p, float v) {
-    asm volatile("red.shared.add.f32 [%0], %1;" ::"r"(smem_addr(p)), "f"(v) : "memory");
-}
 constexpr int kFpThreads = kFpTX * kFpTY;
+constexpr int kFpWinRows = 3;     // detector rows of a lane's window
+constexpr int kFpRecChunk = 64;   // view records staged per pass
 
 // Per (column, view) quantities shared by the 32 lanes that scatter the
 // column's voxels (computed once per view by the thread owning the column).
 struct __align__(16) FpCol {
-    float v0, dv, wt, fu;
-    int cu, ok, pad0, pad1;
+    float v0, dv, wt, fu;   // v of the first voxel and per voxel (box-relative), 1 / W^2, u fraction
+    float gu;               // 1 - fu
+    int cw32, cwG, cwG1;    // window column * 32, window column * G and (column + 1) * G, G the
+                            // windows a flush pass reads; wt = 0 marks a column without voxels
 };
 
+// Window layout of one warp: row dr (0..kFpWinRows-1), column c (0..wc-1)
+// and lane l at word (dr * wc + c) * 32 + ((l + c * G) & 31), with G the
+// number of windows the flush reads per pass (32 / used width, or 1). A
+// scatter (one column, 32 lanes) touches 32 different banks, and so do the
+// live lanes of a flush pass (G windows of cw consecutive columns,
+// G * cw <= 32).
+int fp_smem_bytes(int wc) {
+    return kFpRecChunk * (int)sizeof(ViewRec) + kFpThreads * (int)sizeof(FpCol) +
+           (kFpThreads / 32) * kFpWinRows * wc * 32 * (int)sizeof(float);
+}
+
+__device__ __forceinline__ void fp_tap(float *img, int nu, int nv, int row, int col, float a) {
+    if (a != 0.0f && (unsigned)row < (unsigned)nv && (unsigned)col < (unsigned)nu)
+        atomicAdd(img + (size_t)row * nu + col, a);
+}
+
+__device__ __forceinline__ int floor_bits(float v) { return __float_as_int(__fadd_rd(v, kMagic)); }
+
 template <int TK>
-__global__ void __launch_bounds__(kFpThreads)
+__global__ void __launch_bounds__(kFpThreads, 3)
 fp_zcol(const float *__restrict__ vol, const double *__restrict__ P, int nviews, int nu, int nv,
-        int nx, int ny, int nz, int bu, int bv, int wbu, int wbv, float scale,
-        float *__restrict__ proj, unsigned *err) {
+        int nx, int ny, int nz, int bu, int bv, int wc, float scale, float *__restrict__ proj,
+        unsigned *err) {
     static_assert(TK == 32, "one lane per voxel of a 32-voxel column chunk");
     extern __shared__ __align__(16) unsigned char smem[];
     ViewRec *recs = reinterpret_cast<ViewRec *>(smem);
-    FpCol *cols = reinterpret_cast<FpCol *>(smem + kRecChunk * sizeof(ViewRec));
-    // one private box per warp, odd row pitch: the lanes of a column walk
-    // down the rows at one column, which an odd pitch spreads over the banks
-    const int wpitch = wbu | 1;
-    const int wbox_n = wpitch * wbv;
-    float *wbox = reinterpret_cast<float *>(smem + kRecChunk * sizeof(ViewRec) + kFpThreads * sizeof(FpCol)) +
-                  (threadIdx.x >> 5) * wbox_n;
+    FpCol *cols = reinterpret_cast<FpCol *>(smem + kFpRecChunk * sizeof(ViewRec));
+    const int wwords = kFpWinRows * wc * 32;   // one warp's windows
+    const int rstride = wc * 32;               // words between window rows
+    float *win = reinterpret_cast<float *>(smem + kFpRecChunk * sizeof(ViewRec) + kFpThreads * sizeof(FpCol)) +
+                 (threadIdx.x >> 5) * wwords;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int ntx = (nx + kFpTX - 1) / kFpTX;
@@ -57,11 +80,7 @@ fp_zcol(const float *__restrict__ vol, const double *__restrict__ P, int nviews,
     const bool col_ok = di < ex && dj < ey;
     const float fdi = (float)di, fdj = (float)dj;
 
-    // Scatter mapping: warp w handles the 32 columns of its patch one at a
-    // time; lane l holds voxel k0 + l of each of them. The v step per voxel
-    // is at least one pixel (checked per column), so within one scatter
-    // instruction the lanes of a column write 32 different rows of the
-    // warp's own box: plain read-add-write, no atomics.
+    // lane l holds voxel k0 + l of each of the warp's 32 columns
     float x[32];
     {
         const size_t plane = (size_t)nx * ny;
@@ -75,10 +94,10 @@ fp_zcol(const float *__restrict__ vol, const double *__restrict__ P, int nviews,
         }
     }
     float *pb = proj + (size_t)b * nviews * nu * nv;
-    for (int t = lane; t < wbox_n; t += 32) wbox[t] = 0.0f;   // the flush keeps it clean from here on
+    for (int t = 4 * lane; t < wwords; t += 128) *reinterpret_cast<float4 *>(win + t) = make_float4(0.f, 0.f, 0.f, 0.f);
 
-    for (int cb = 0; cb < nviews; cb += kRecChunk) {
-        const int cn = min(kRecChunk, nviews - cb);
+    for (int cb = 0; cb < nviews; cb += kFpRecChunk) {
+        const int cn = min(kFpRecChunk, nviews - cb);
         __syncthreads();
         for (int n = tid; n < cn; n += kFpThreads) {
             ViewRec r;
@@ -90,126 +109,144 @@ fp_zcol(const float *__restrict__ vol, const double *__restrict__ P, int nviews,
             __syncthreads();   // records ready; previous view's column setup consumed
             const ViewRec r = recs[n];
             FpCol c;
-            c.ok = 0;
-            c.pad0 = c.pad1 = 0;
-            float umin = 3e38f, umax = -3e38f, vmin = 3e38f, vmax = -3e38f;
+            float uL = 0.0f, cv0 = 0.0f, cdv = 0.0f, cwt = 0.0f, cfu = 0.0f;
+            int cu = 0;
+            bool cok = false;
+            float umin = 3e38f, umax = -3e38f, v0min = 3e38f, dvmin = 3e38f;
             if (col_ok) {
                 float W = fmaf(r.Wj, fdj, fmaf(r.Wi, fdi, r.W0));
                 float inv = col_rcp(W);
-                float uL = fmaf(r.Nuj, fdj, fmaf(r.Nui, fdi, r.Nu0)) * inv;
-                c.v0 = fmaf(r.Nvj, fdj, fmaf(r.Nvi, fdi, r.Nv0)) * inv;
-                c.dv = r.Nvk * inv;
-                c.wt = inv * inv;
+                uL = fmaf(r.Nuj, fdj, fmaf(r.Nui, fdi, r.Nu0)) * inv;
+                cv0 = fmaf(r.Nvj, fdj, fmaf(r.Nvi, fdi, r.Nv0)) * inv;
+                cdv = r.Nvk * inv;
+                cwt = inv * inv;
                 float tu = __fadd_rd(uL, kMagic);
-                c.cu = __float_as_int(tu) - kMagicBits;
-                c.fu = uL - (tu - kMagic);
-                float vlast = fmaf((float)(ez - 1), c.dv, c.v0);
-                if (uL == uL && c.v0 == c.v0) {
-                    c.ok = 1;
-                    umin = umax = uL;
-                    vmin = fminf(c.v0, vlast);
-                    vmax = fmaxf(c.v0, vlast);
+                cu = __float_as_int(tu) - kMagicBits;
+                cfu = uL - (tu - kMagic);
+                if (uL == uL && cv0 == cv0) {
+                    // every coordinate stays far inside the range of the round-to-integer trick
+                    if (fabsf(cdv) < 1e4f && fabsf(cv0) < 1e6f && fabsf(uL) < 1e6f) {
+                        cok = true;
+                        umin = umax = uL;
+                        v0min = cv0;
+                        dvmin = cdv;
+                    } else {
+                        atomicOr(err, DEV_ERR_FOOTPRINT);
+                    }
                 }
             }
-            // the warp's box: floor of the smallest column / row its lanes touch
             for (int o = 16; o > 0; o >>= 1) {
                 umin = fminf(umin, __shfl_xor_sync(0xffffffffu, umin, o));
                 umax = fmaxf(umax, __shfl_xor_sync(0xffffffffu, umax, o));
-                vmin = fminf(vmin, __shfl_xor_sync(0xffffffffu, vmin, o));
-                vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
+                v0min = fminf(v0min, __shfl_xor_sync(0xffffffffu, v0min, o));
+                dvmin = fminf(dvmin, __shfl_xor_sync(0xffffffffu, dvmin, o));
             }
             const bool any = umin <= umax;
-            const int uo = any ? __float_as_int(__fadd_rd(umin, kMagic)) - kMagicBits : 0;
-            const int vo = any ? __float_as_int(__fadd_rd(vmin, kMagic)) - kMagicBits : 0;
-            const bool fits = any && (__float_as_int(__fadd_rd(umax, kMagic)) - kMagicBits) + 1 - uo <= wbu - 1 &&
-                              (__float_as_int(__fadd_rd(vmax, kMagic)) - kMagicBits) + 1 - vo <= wbv - 1;
+            const int uo = any ? floor_bits(umin) - kMagicBits : 0;
+            const int cols_used = any ? floor_bits(umax) - kMagicBits + 2 - uo : 0;
+            const bool fits = any && cols_used <= wc;
             if (any && !fits && lane == 0) atomicOr(err, DEV_ERR_FOOTPRINT);
-            if (c.ok) c.cu -= uo;   // column relative to the warp box
-            // At least one detector row per voxel in every column: the lanes of a
-            // column then write different rows, so plain read-add-writes are safe;
-            // otherwise the warp adds with shared-memory reductions for this view.
-            const bool rmw = __all_sync(0xffffffffu, !c.ok || fabsf(c.dv) >= 1.0f);
+            const int cwid = max(1, min(cols_used, 32));
+            const int G = 32 / cwid;
+            // A column outside the patch or without a usable geometry scatters
+            // zeros at window row 0, column 0 (no branch in the scatter loop).
+            c.v0 = cok ? cv0 : v0min;
+            c.dv = cok ? cdv : dvmin;
+            c.wt = cok ? cwt : 0.0f;
+            c.fu = cok ? cfu : 0.0f;
+            c.gu = 1.0f - c.fu;
+            const int cwin = cok ? cu - uo : 0;
+            c.cw32 = cwin * 32;
+            c.cwG = cwin * G;
+            c.cwG1 = c.cwG + G;
             cols[tid] = c;
             __syncwarp();
-            if (any && fits) {
-                const float fl = (float)lane;
-                // Lane l adds voxel k0 + l of each column to rows r, r + 1 and
-                // columns cu, cu + 1. With the read-add-write form, the two taps
-                // of one row go together (no other lane touches that row), and a
-                // warp barrier separates them from the next row's taps (lane
-                // l + 1's top row can be lane l's bottom row) and from the next
-                // column.
-                auto scatter = [&](const FpCol &cc, float xv, bool plain) {
-                    float v = fmaf(fl, cc.dv, cc.v0);
-                    float tv = __fadd_rd(v, kMagic);
-                    float fv = v - (tv - kMagic);
-                    int row = __float_as_int(tv) - kMagicBits - vo;
-                    float val = cc.wt * xv;
-                    float a1 = fv * val, a0 = val - a1;   // (1-fv) val, fv val
-                    const bool act = lane < ez;
-                    float *p = wbox + row * wpitch + cc.cu;
-                    const float gu = 1.0f - cc.fu;
-                    if (plain) {
-                        if (act) {
-                            p[0] += gu * a0;
-                            p[1] += cc.fu * a0;
-                        }
-                        __syncwarp();
-                        if (act) {
-                            p[wpitch] += gu * a1;
-                            p[wpitch + 1] += cc.fu * a1;
-                        }
-                        __syncwarp();
-                    } else if (act) {
-                        red_add_shared(p, gu * a0);
-                        red_add_shared(p + 1, cc.fu * a0);
-                        red_add_shared(p + wpitch, gu * a1);
-                        red_add_shared(p + wpitch + 1, cc.fu * a1);
-                    }
-                };
-                if (rmw) {
+            if (!(any && fits)) continue;   // uniform across the warp
+
+            // Lane l's window starts at row floor(v0min + l * dvmin): every
+            // column's row floor(v0 + l * dv) is at or above it (v0 >= v0min,
+            // dv >= dvmin, l >= 0, and fmaf and the floor are monotone).
+            const float fl = (float)lane;
+            const int tb = floor_bits(fmaf(fl, dvmin, v0min));
+            const int base = tb - kMagicBits;
+            float *img = pb + (size_t)(cb + n) * nu * nv;
+            unsigned dmax = 0;
 #pragma unroll
-                    for (int cix = 0; cix < 32; ++cix) {
-                        const FpCol cc = cols[warp * 32 + cix];
-                        if (cc.ok) scatter(cc, x[cix], true);   // uniform across the warp
-                    }
-                } else {
+            for (int cix = 0; cix < 32; ++cix) {
+                const FpCol cc = cols[warp * 32 + cix];
+                const float v = fmaf(fl, cc.dv, cc.v0);
+                const float tv = __fadd_rd(v, kMagic);
+                const float fv = v - (tv - kMagic);
+                const unsigned udr = (unsigned)(__float_as_int(tv) - tb);   // >= 0 as a signed value
+                dmax = max(dmax, udr);
+                const bool in = udr <= (unsigned)(kFpWinRows - 2);
+                const int drc = in ? (int)udr : 0;
+                const float val = in ? cc.wt * x[cix] : 0.0f;   // beyond the window: the pass below
+                const float a1 = fv * val, a0 = val - a1;       // (1-fv) val, fv val
+                const int w0 = drc * rstride + cc.cw32 + ((lane + cc.cwG) & 31);
+                const int w1 = drc * rstride + cc.cw32 + 32 + ((lane + cc.cwG1) & 31);
+                win[w0] += cc.gu * a0;
+                win[w1] += cc.fu * a0;
+                win[w0 + rstride] += cc.gu * a1;
+                win[w1 + rstride] += cc.fu * a1;
+            }
+            if (__any_sync(0xffffffffu, lane < ez && dmax > (unsigned)(kFpWinRows - 2))) {
+                // taps beyond a lane's window go straight to the projection
 #pragma unroll
-                    for (int cix = 0; cix < 32; ++cix) {
-                        const FpCol cc = cols[warp * 32 + cix];
-                        if (cc.ok) scatter(cc, x[cix], false);
-                    }
-                    __syncwarp();
-                }
-                // flush the warp's box into the projection (inside the detector only)
-                float *img = pb + (size_t)(cb + n) * nu * nv;
-                const int rows_used = min(wbv, (__float_as_int(__fadd_rd(vmax, kMagic)) - kMagicBits) + 2 - vo);
-                const int cols_used = min(wbu, (__float_as_int(__fadd_rd(umax, kMagic)) - kMagicBits) + 2 - uo);
-                // Lanes take g rows of cw columns at a time (cw = the used width, at
-                // most 32; G = 32 / cw rows per pass), so narrow boxes keep most lanes
-                // busy. Every value read is zeroed again, so the box is clean for the
-                // next view (the scatter writes only inside this region).
-                const int cw = min(cols_used, 32);
-                const int G = 32 / cw;
-                const int g = lane / cw, cl = lane - g * cw;
-                for (int c0 = 0; c0 < cols_used; c0 += cw) {
-                    const int ccol = c0 + cl;
-                    const int c_ = r.u_box + uo + ccol;
-                    const bool cok = g < G && ccol < cols_used;
-                    const bool cin = cok && c_ >= 0 && c_ < nu;
-                    float *cell = wbox + g * wpitch + ccol;
-                    int r_ = r.v_box + vo + g;
-                    for (int rr = g; rr < rows_used; rr += G) {
-                        if (cok) {
-                            const float val = *cell;
-                            *cell = 0.0f;
-                            if (cin && val != 0.0f && r_ >= 0 && r_ < nv) atomicAdd(img + (size_t)r_ * nu + c_, val);
-                        }
-                        cell += G * wpitch;
-                        r_ += G;
+                for (int cix = 0; cix < 32; ++cix) {
+                    const FpCol cc = cols[warp * 32 + cix];
+                    if (cc.wt == 0.0f) continue;   // uniform across the warp
+                    const float v = fmaf(fl, cc.dv, cc.v0);
+                    const float tv = __fadd_rd(v, kMagic);
+                    const float fv = v - (tv - kMagic);
+                    const unsigned udr = (unsigned)(__float_as_int(tv) - tb);
+                    const float val = cc.wt * x[cix];
+                    if (udr > (unsigned)(kFpWinRows - 2) && val != 0.0f) {
+                        const float a1 = fv * val, a0 = val - a1;
+                        const int rr = r.v_box + base + (int)udr, c0 = r.u_box + uo + (cc.cw32 >> 5);
+                        fp_tap(img, nu, nv, rr, c0, cc.gu * a0);
+                        fp_tap(img, nu, nv, rr, c0 + 1, cc.fu * a0);
+                        fp_tap(img, nu, nv, rr + 1, c0, cc.gu * a1);
+                        fp_tap(img, nu, nv, rr + 1, c0 + 1, cc.fu * a1);
                     }
                 }
             }
+            __syncwarp();
+
+            // Flush: lane (g, cl) reads window it * G + g, column c0 + cl, and adds
+            // its rows to the projection (windows overlap in rows; the global
+            // reductions sum them).
+            const int g = lane / cwid, cl = lane - g * cwid;
+            // the window bases are monotone in the lane: the end lanes bound the rows
+            const int bf = __shfl_sync(0xffffffffu, base, 0), bl31 = __shfl_sync(0xffffffffu, base, 31);
+            const bool rows_in = r.v_box + min(bf, bl31) >= 0 && r.v_box + max(bf, bl31) + kFpWinRows - 1 < nv;
+            const int nit = (32 + G - 1) / G;
+            for (int c0 = 0; c0 < cols_used; c0 += cwid) {
+                const int cidx = c0 + cl;
+                const int gc = r.u_box + uo + cidx;
+                const bool live = g < G && cidx < cols_used && gc >= 0 && gc < nu;
+                const float *wcol = win + (live ? cidx : 0) * 32;
+                const int cG = cidx * G;
+                for (int it = 0; it < nit; ++it) {
+                    const int l = it * G + g;
+                    const int bl = __shfl_sync(0xffffffffu, base, l & 31);
+                    const bool lok = live && l < 32;
+                    const int slot = (l + cG) & 31;
+                    const float e0 = wcol[slot], e1 = wcol[rstride + slot], e2 = wcol[2 * rstride + slot];
+                    const int row = r.v_box + bl;
+                    const long long idx = (long long)row * nu + gc;
+                    if (lok && e0 != 0.0f && (rows_in || (unsigned)row < (unsigned)nv)) atomicAdd(img + idx, e0);
+                    if (lok && e1 != 0.0f && (rows_in || (unsigned)(row + 1) < (unsigned)nv))
+                        atomicAdd(img + idx + nu, e1);
+                    if (lok && e2 != 0.0f && (rows_in || (unsigned)(row + 2) < (unsigned)nv))
+                        atomicAdd(img + idx + 2 * nu, e2);
+                }
+            }
+            __syncwarp();
+            // clear the columns the scatter used, for the next view
+            for (int dr = 0; dr < kFpWinRows; ++dr)
+                for (int t = 4 * lane; t < cols_used * 32; t += 128)
+                    *reinterpret_cast<float4 *>(win + dr * rstride + t) = make_float4(0.f, 0.f, 0.f, 0.f);
         }
     }
 }
@@ -267,7 +304,7 @@ bp_status launch_forward(bp_ctx *ctx, const float *vol, float *proj, int batch, 
     cudaError_t e = cudaMemsetAsync(proj, 0, bytes, st);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "fp_project: clear");
     if (!ctx->zinv || ctx->plan.bu <= 0 || ctx->plan.fp_wbu <= 0) {
-        // general matrices, or a footprint too large for the shared box
+        // general matrices, or patches too wide for the windows
         dim3 grid(((ctx->nx + 7) / 8) * ((ctx->ny + 7) / 8) * ((ctx->nz + 3) / 4), 1, batch);
         fp_voxel_gen<<<grid, 256, 0, st>>>(vol, ctx->d_P, ctx->n_views, ctx->nu, ctx->nv, ctx->nx,
                                            ctx->ny, ctx->nz, scale, proj);
@@ -276,17 +313,15 @@ bp_status launch_forward(bp_ctx *ctx, const float *vol, float *proj, int batch, 
     }
     // FP tiles are 32 x 8 x 32, the same shape the plan's TK=32 box covers;
     // with TK=64 plans the box is at least as large, so it still covers.
-    const int bu = ctx->plan.bu, bv = ctx->plan.bv;
-    const int wbu = ctx->plan.fp_wbu, wbv = ctx->plan.fp_wbv;
-    const int smem = kRecChunk * (int)sizeof(ViewRec) + kFpThreads * (int)sizeof(FpCol) +
-                     (kFpThreads / 32) * (wbu | 1) * wbv * (int)sizeof(float);
+    const int bu = ctx->plan.bu, bv = ctx->plan.bv, wc = ctx->plan.fp_wbu;
+    const int smem = fp_smem_bytes(wc);
     e = cudaFuncSetAttribute(fp_zcol<kFpTK>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "fp_zcol attribute");
     dim3 grid(((ctx->nx + kFpTX - 1) / kFpTX) * ((ctx->ny + kFpTY - 1) / kFpTY),
               (ctx->nz + kFpTK - 1) / kFpTK, batch);
     fp_zcol<kFpTK><<<grid, kFpThreads, smem, st>>>(vol, ctx->d_P, ctx->n_views, ctx->nu, ctx->nv,
-                                                  ctx->nx, ctx->ny, ctx->nz, bu, bv, wbu, wbv, scale,
-                                                  proj, ctx->d_err);
+                                                  ctx->nx, ctx->ny, ctx->nz, bu, bv, wc, scale, proj,
+                                                  ctx->d_err);
     e = cudaGetLastError();
     return e == cudaSuccess ? BP_OK : cuda_fail(ctx, e, "fp_zcol launch");
 }

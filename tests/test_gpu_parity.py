@@ -180,6 +180,22 @@ def test_forward_project_ragged(name):
     assert abs(lhs - rhs) <= 1e-6 * norm
 
 
+def test_flipped_detector_rows():
+    """Matrices whose detector rows run against z (v -> nv - 1 - v): the row
+    step per slice is negative; both operators follow the oracle."""
+    g = dict(FP_GEOMS["ragged_37x29x45"], np=7, angles=np.sort(np.random.default_rng(5).uniform(0, 2 * np.pi, 7)))
+    P = oracle.matrices(g)
+    P[:, 1, :] = (g["nv"] - 1) * P[:, 2, :] - P[:, 1, :]
+    x = inputs.uniform_array(25, (g["nz"], g["ny"], g["nx"]), 0, 1).astype(np.float32)
+    q = inputs.uniform_array(26, (g["np"], g["nv"], g["nu"]), -1, 1).astype(np.float32)
+    with api.bp_create_from_matrices(P, g["nu"], g["nv"], g["nx"], g["ny"], g["nz"]) as ctx:
+        fx = api.fp_project(ctx, torch.from_numpy(x).cuda()).cpu().numpy()
+        bq = api.bp_backproject(ctx, torch.from_numpy(q).cuda()).cpu().numpy()
+        api.bp_device_status(ctx)
+    assert rel(fx, oracle.forward_project(P, x, g["nu"], g["nv"])) <= 5e-5
+    assert rel(bq, oracle.backproject(P, q, g["nx"], g["ny"], g["nz"])) <= 5e-5
+
+
 def test_backproject_batch_accumulate_and_view_chunks(c1):
     g = c1["g"]
     q = c1["q"]
