@@ -227,20 +227,35 @@ fp_zcol(const float *__restrict__ vol, const double *__restrict__ P, int nviews,
                 const bool live = g < G && cidx < cols_used && gc >= 0 && gc < nu;
                 const float *wcol = win + (live ? cidx : 0) * 32;
                 const int cG = cidx * G;
-                for (int it = 0; it < nit; ++it) {
-                    const int l = it * G + g;
-                    const int bl = __shfl_sync(0xffffffffu, base, l & 31);
-                    const bool lok = live && l < 32;
-                    const int slot = (l + cG) & 31;
-                    const float e0 = wcol[slot], e1 = wcol[rstride + slot], e2 = wcol[2 * rstride + slot];
-                    const int row = r.v_box + bl;
-                    const long long idx = (long long)row * nu + gc;
-                    if (lok && e0 != 0.0f && (rows_in || (unsigned)row < (unsigned)nv)) atomicAdd(img + idx, e0);
-                    if (lok && e1 != 0.0f && (rows_in || (unsigned)(row + 1) < (unsigned)nv))
-                        atomicAdd(img + idx + nu, e1);
-                    if (lok && e2 != 0.0f && (rows_in || (unsigned)(row + 2) < (unsigned)nv))
-                        atomicAdd(img + idx + 2 * nu, e2);
-                }
+                float *gcol = img + (live ? gc : 0);
+                // all rows inside the detector (the common case): no row checks,
+                // and zero cells are added too (cheaper than testing them)
+                auto pass = [&](bool checked) {
+                    for (int it = 0; it < nit; ++it) {
+                        const int l = it * G + g;
+                        const int bl = __shfl_sync(0xffffffffu, base, l & 31);
+                        const bool lok = live && l < 32;
+                        const int slot = (l + cG) & 31;
+                        const float e0 = wcol[slot], e1 = wcol[rstride + slot], e2 = wcol[2 * rstride + slot];
+                        const int row = r.v_box + bl;
+                        float *d = gcol + (long long)row * nu;
+                        if (!checked) {
+                            if (lok) {
+                                atomicAdd(d, e0);
+                                atomicAdd(d + nu, e1);
+                                atomicAdd(d + 2 * nu, e2);
+                            }
+                        } else {
+                            if (lok && e0 != 0.0f && (unsigned)row < (unsigned)nv) atomicAdd(d, e0);
+                            if (lok && e1 != 0.0f && (unsigned)(row + 1) < (unsigned)nv) atomicAdd(d + nu, e1);
+                            if (lok && e2 != 0.0f && (unsigned)(row + 2) < (unsigned)nv) atomicAdd(d + 2 * nu, e2);
+                        }
+                    }
+                };
+                if (rows_in)
+                    pass(false);
+                else
+                    pass(true);
             }
             __syncwarp();
             // clear the columns the scatter used, for the next view
