@@ -12,6 +12,7 @@ What pins what:
   bp_linear               bilinear sampling reproduces linear data exactly
   bp_fp_hat_matrix        BP and FP vs a dense matrix built from hat functions
                           (bilinear weight = tent(u-c)*tent(v-r)), zero padding included
+  bp_slab_points          slab and point back-projections vs that hat matrix and the whole loop
   adjoint_dot             <BP q, x> = <q, FP x>
   symmetry                v(nz-1-k) = nv-1-v(k) for a centred geometry (Section 3.1.2)
   filter_impulse          cosine weight from the 3-D ray angle, centre tap 1/(4 dp)
@@ -158,9 +159,7 @@ def bp_fp_hat_matrix():
     # The volume overhangs the detector so that zero padding is exercised,
     # and some projections land at negative coordinates (floor vs truncation).
     rng = np.random.default_rng(11)
-    g = dict(sid=300.0, sdd=450.0, np=4, angles=np.array([0.1, 1.3, 2.9, 4.4]), nu=16, nv=14,
-             du=1.3, dv=1.1, u_off=2.2, v_off=-1.6, nx=8, ny=7, nz=6, sx=2.0, sy=2.1, sz=2.4,
-             ox=1.0, oy=0.5, oz=-0.7)
+    g = _hat_geom()
     scale = 0.8
     A = _hat_matrix(g, scale)
     P = oracle.matrices(g)
@@ -175,6 +174,49 @@ def bp_fp_hat_matrix():
     assert np.max(np.abs(fp - ref_fp)) <= 1e-12 * np.abs(ref_fp).max()
     # some voxels fall (partly) off the detector: padding must have mattered
     assert (np.abs(A).sum(axis=0) == 0).any() or (A > 0).sum() < 4 * g["np"] * A.shape[1]
+
+
+def _hat_geom():
+    return dict(sid=300.0, sdd=450.0, np=4, angles=np.array([0.1, 1.3, 2.9, 4.4]), nu=16, nv=14,
+                du=1.3, dv=1.1, u_off=2.2, v_off=-1.6, nx=8, ny=7, nz=6, sx=2.0, sy=2.1, sz=2.4,
+                ox=1.0, oy=0.5, oz=-0.7)
+
+
+def bp_slab_points():
+    """The slab and point versions of Listing 1 (the references for sampled and
+    slab parity) against the dense hat matrix, slice range by slice range and
+    voxel by voxel, and against the whole-volume loop on a second geometry."""
+    g = _hat_geom()
+    scale = 0.8
+    A = _hat_matrix(g, scale)
+    P = oracle.matrices(g)
+    rng = np.random.default_rng(12)
+    q = rng.normal(size=(g["np"], g["nv"], g["nu"]))
+    ref = (A.T @ q.reshape(-1)).reshape(g["nz"], g["ny"], g["nx"])
+    tol = 1e-12 * np.abs(ref).max()
+    nz = g["nz"]
+    for k0, nks in [(0, nz), (0, 1), (nz - 1, 1), (2, 3), (1, nz - 2)]:
+        slab = oracle.backproject_slab(P, q, g["nx"], g["ny"], k0, nks, scale)
+        assert slab.shape == (nks, g["ny"], g["nx"])
+        assert np.max(np.abs(slab - ref[k0:k0 + nks])) <= tol, (k0, nks)
+    ijk = np.stack([rng.integers(0, g["nx"], 60), rng.integers(0, g["ny"], 60),
+                    rng.integers(0, nz, 60)], axis=1)
+    ijk[:4] = [[0, 0, 0], [g["nx"] - 1, g["ny"] - 1, nz - 1], [0, g["ny"] - 1, 0], [g["nx"] - 1, 0, nz - 1]]
+    pts = oracle.backproject_points(P, q, ijk, scale)
+    assert np.max(np.abs(pts - ref[ijk[:, 2], ijk[:, 1], ijk[:, 0]])) <= tol
+    # second geometry, larger, against the whole-volume loop
+    g = _geom_offsets()
+    P = oracle.matrices(g)
+    q = rng.normal(size=(g["np"], g["nv"], g["nu"]))
+    full = oracle.backproject(P, q, g["nx"], g["ny"], g["nz"], 0.45)
+    tol = 1e-14 * np.abs(full).max()
+    for k0, nks in [(0, g["nz"]), (g["nz"] - 1, 1), (3, 2)]:
+        slab = oracle.backproject_slab(P, q, g["nx"], g["ny"], k0, nks, 0.45)
+        assert np.max(np.abs(slab - full[k0:k0 + nks])) <= tol, (k0, nks)
+    ijk = np.stack(np.meshgrid(np.arange(g["nx"]), np.arange(g["ny"]), np.arange(g["nz"]),
+                               indexing="ij"), axis=-1).reshape(-1, 3)
+    pts = oracle.backproject_points(P, q, ijk, 0.45)
+    assert np.max(np.abs(pts - full[ijk[:, 2], ijk[:, 1], ijk[:, 0]])) <= tol
 
 
 def adjoint_dot():
@@ -489,7 +531,7 @@ def iter_convergence():
     assert np.abs(oracle.sart(P, p, *n, iters=1) - xt).max() > 1e-2
 
 
-ALL = [matrix_vs_ray, z_invariance, bp_constant, bp_linear, bp_fp_hat_matrix, adjoint_dot,
+ALL = [matrix_vs_ray, z_invariance, bp_constant, bp_linear, bp_fp_hat_matrix, bp_slab_points, adjoint_dot,
        symmetry, filter_impulse, filter_frequency, phantom_sphere, phantom_ray_integral,
        phantom_siddon, fdk_sphere, fdk_offcentre, fdk_ellipsoids, conv_vs_scipy, conv_adjoints,
        mlem_counts, mlem_likelihood, iter_fixed_points, sart_constant_step, iter_convergence]

@@ -51,6 +51,11 @@ MUTANTS = [
     ("mlem_no_sensitivity", "if (sens[j] > eps) x[j] = x[j] * b[j] / sens[j];", "if (sens[j] > eps) x[j] = x[j] * b[j];"),
     ("mlem_ratio_inverted", "y[i] = (y[i] > eps) ? pt[i] / y[i] : 0.0;", "y[i] = (y[i] > eps) ? y[i] / pt[i] : 0.0;"),
     ("sart_no_ray_norm", "(pt[i] - y[i]) / ray[i] : 0.0;", "(pt[i] - y[i]) : 0.0;"),
+    ("slab_slice_offset", "const int k = k0 + kk;", "const int k = kk;"),
+    ("slab_weight_f", "bilinear(im, nu, nv, x, y) * f * f;", "bilinear(im, nu, nv, x, y) * f;"),
+    ("points_no_scale", "out[t] = acc * scale;", "out[t] = acc;"),
+    ("points_ij_swapped", "double i = ijk[3 * t], j = ijk[3 * t + 1], k = ijk[3 * t + 2];",
+     "double j = ijk[3 * t], i = ijk[3 * t + 1], k = ijk[3 * t + 2];"),
     ("sart_sign", "if (sens[j] > eps) x[j] += lambda * b[j] / sens[j];", "if (sens[j] > eps) x[j] -= lambda * b[j] / sens[j];"),
 ]
 
