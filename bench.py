@@ -53,6 +53,11 @@ def parse_args(argv=None):
                     help="FP32 back-projection without the mid-plane symmetry (Section 3.1.2)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the forward projector / least-squares / MLEM / SART timings of the default line")
+    ap.add_argument("--oracle-table", action="store_true",
+                    help="time the FP64 oracle on c1 and c2 in full and on the c3 slab, one thread and all "
+                         "threads (one JSON line per case; no GPU)")
     ap.add_argument("--no-learned", action="store_true",
                     help="skip the few-view workload (train the network, held-out RMSE, wall time vs full view)")
     return ap.parse_args(argv)
@@ -155,12 +160,46 @@ class ClockSampler:
         return out
 
 
-def cpu_baseline(g, budget_s=15.0, max_slices=32, chunk=4):
-    """The FP64 oracle back-projecting a z-slab of the workload on the host
-    cores (bounded: stops after ~budget_s seconds). Data: seeded uniform
-    projections, FP32 values (the oracle's cost does not depend on them).
-    Returns the timing record and (k0, slices, projections, oracle slab) for
-    the parity check of the GPU volume."""
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part")):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
+
+def _oracle_slab_rate(oracle, P, q, g, k0, max_slices, chunk, budget_s):
+    """Back-project chunks of slices from k0 until max_slices or budget_s;
+    returns (GUPS, slices done, seconds, slab)."""
+    import numpy as np
+    done, t, parts = 0, 0.0, []
+    while done < max_slices and t < budget_s:
+        n = min(chunk, max_slices - done)
+        t0 = time.perf_counter()
+        parts.append(oracle.backproject_slab(P, q, g["nx"], g["ny"], k0 + done, n, math.pi / g["np"]))
+        t += time.perf_counter() - t0
+        done += n
+    upd = float(g["nx"]) * g["ny"] * done * g["np"]
+    return upd / t / 1e9, done, t, np.concatenate(parts, axis=0)
+
+
+def cpu_baseline(g, budget_s=12.0, max_slices=32, budget_1t_s=6.0):
+    """The FP64 oracle back-projecting a central z-slab of the workload on the
+    host cores (bounded in time), on all threads and on one. The slab is
+    split over (slice, row) pairs, so every thread works even on a thin slab.
+    Data: seeded uniform projections, FP32 values (the oracle's cost does not
+    depend on them). Returns the timing record and (k0, slices, projections,
+    oracle slab) for the parity check of the GPU volume."""
     import numpy as np
 
     import oracle
@@ -169,18 +208,22 @@ def cpu_baseline(g, budget_s=15.0, max_slices=32, chunk=4):
     q32 = inputs.uniform_array(99, (g["np"], g["nv"], g["nu"]), -1.0, 1.0).astype(np.float32)
     q = q32.astype(np.float64)
     k0 = g["nz"] // 2 - max_slices // 2
-    done, t = 0, 0.0
-    parts = []
-    while done < max_slices and t < budget_s:
-        t0 = time.perf_counter()
-        parts.append(oracle.backproject_slab(P, q, g["nx"], g["ny"], k0 + done, chunk, math.pi / g["np"]))
-        t += time.perf_counter() - t0
-        done += chunk
+    threads = oracle.num_threads()
+    rate, done, t, slab = _oracle_slab_rate(oracle, P, q, g, k0, max_slices, 2, budget_s)
+    oracle.set_threads(1)
+    try:
+        rate1, done1, t1, _ = _oracle_slab_rate(oracle, P, q, g, k0, max_slices, 1, budget_1t_s)
+    finally:
+        oracle.set_threads(threads)
     upd = float(g["nx"]) * g["ny"] * done * g["np"]
-    rec = {"value": upd / t / 1e9, "unit": "GUPS", "cores": oracle.num_threads(), "kind": "oracle",
+    rec = {"value": rate, "unit": "GUPS", "cores": threads, "kind": "oracle",
+           "single_thread": {"value": rate1, "unit": "GUPS", "cores": 1,
+                             "sample": f"slices {k0}..{k0 + done1 - 1}, {t1:.1f} s"},
+           "nproc": os.cpu_count(), "cpu_model": cpu_model(),
            "sample": f"FP64 oracle back-projection of slices {k0}..{k0 + done - 1} "
-                     f"({g['nx']}x{g['ny']}x{done} voxels x {g['np']} views, {upd:.3g} updates, {t:.1f} s)"}
-    return rec, (k0, done, q32, np.concatenate(parts, axis=0))
+                     f"({g['nx']}x{g['ny']}x{done} voxels x {g['np']} views, {upd:.3g} updates, {t:.1f} s) "
+                     f"on {threads} OpenMP threads over (slice, row) pairs"}
+    return rec, (k0, done, q32, slab)
 
 
 def slab_parity(ctx, g, sample) -> dict:
@@ -232,14 +275,15 @@ def run_reference(args):
     t = statistics.mean(times)
     val = upd / t / 1e9
     sample = (f"each step: FP64 oracle back-projection of a {g['nx']}x{g['ny']}x{nks} slab "
-              f"({g['np']} views, {upd:.3g} updates) of the {args.workload} workload")
+              f"({g['np']} views, {upd:.3g} updates) of the {args.workload} workload, "
+              f"{oracle.num_threads()} OpenMP threads over (slice, row) pairs")
     line = {"impl": "reference", "metric": "fdk_backprojection_gups", "value": val, "unit": "GUPS",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic",
             "config": {"workload": args.workload, "sample": sample},
             "cpu_baseline": {"value": val, "unit": "GUPS", "cores": oracle.num_threads(), "kind": "oracle",
-                             "sample": sample},
+                             "sample": sample, "nproc": os.cpu_count(), "cpu_model": cpu_model()},
             "e2e": {"value": val, "unit": "GUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -276,21 +320,18 @@ def run_unet(args):
                                  "flop_per_step": flops}}), flush=True)
 
 
-def run_op(args):
-    """Secondary measurements (forward projector, least squares) in the same JSON form."""
+def measure_op(op, workload, steps, warmup, views=0, subsets=0) -> dict:
+    """One secondary operator on a workload (forward projection, a least-squares
+    iteration, an MLEM or SART pass), timed with CUDA events; the record of the
+    JSON line of ``--op`` and of the main line's ``variants``."""
     import torch
 
-    import __graft_entry__
-    __graft_entry__.build()
     from paper_2104_13248_gb300 import api, autograd, inputs
 
-    if args.op == "unet":
-        return run_unet(args)
-    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-    p = inputs.preset(args.workload)
+    p = inputs.preset(workload)
     g = p["geom"]
-    if args.views:
-        g = inputs.scaled_geom(g, np=args.views)
+    if views:
+        g = inputs.scaled_geom(g, np=views)
     batch = p.get("batch", 1)
     ctx = api.bp_create(g)
     U = float(g["nx"]) * g["ny"] * g["nz"] * g["np"] * batch
@@ -300,24 +341,24 @@ def run_op(args):
     x = torch.rand((batch,) + ctx.vol_shape(), device="cuda", generator=gen)
     proj = torch.empty_like(raws)
     sub = None
-    if args.op == "fp":
+    if op == "fp":
         def step():
             api.fp_project(ctx, x, proj=proj)
         upd, unit_desc = U, "forward-projection"
-    elif args.op in ("mlem", "sart"):
+    elif op in ("mlem", "sart"):
         from paper_2104_13248_gb300 import iterative
-        nsub = args.subsets or (1 if args.op == "mlem" else 10)
-        sub = iterative.Subsets(ctx, nsub, need_rays=args.op == "sart")
+        nsub = subsets or (1 if op == "mlem" else 10)
+        sub = iterative.Subsets(ctx, nsub, need_rays=op == "sart")
         state = {"x": x[0].clone()}
 
         def step():
-            if args.op == "mlem":
+            if op == "mlem":
                 state["x"] = iterative.mlem(ctx, raws[0], iters=1, x0=state["x"], sub=sub)
             else:
                 state["x"] = iterative.sart(ctx, raws[0], iters=1, x0=state["x"], sub=sub, nonneg=True)
         U = U / batch
         upd = 2 * U
-        unit_desc = (f"one {args.op.upper()} pass over {nsub} view subset(s): a forward and a back-projection "
+        unit_desc = (f"one {op.upper()} pass over {nsub} view subset(s): a forward and a back-projection "
                      f"of every view plus the element-wise steps (batch 1)")
     else:
         L = autograd.lipschitz(ctx, iters=5)
@@ -325,25 +366,56 @@ def run_op(args):
         def step():
             autograd.least_squares(ctx, raws, iters=1, x0=x, L=L)
         upd, unit_desc = 2 * U, "least-squares iteration (one forward + one back-projection)"
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         step()
     torch.cuda.synchronize()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     a.record()
-    for _ in range(args.steps):
+    for _ in range(steps):
         step()
     b.record()
     torch.cuda.synchronize()
-    ms = a.elapsed_time(b) / args.steps
+    ms = a.elapsed_time(b) / steps
     api.bp_device_status(ctx)
-    print(json.dumps({"metric": f"{args.op}_gups", "value": upd / (ms * 1e-3) / 1e9, "unit": "GUPS",
-                      "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
-                      "higher_is_better": True, "dtype": "f32", "data": "synthetic",
-                      "config": {"workload": args.workload, "batch": 1 if sub else batch, "step": unit_desc}}),
-          flush=True)
     if sub is not None:
         sub.close()
     ctx.close()
+    del raws, x, proj
+    torch.cuda.empty_cache()
+    return {"value": upd / (ms * 1e-3) / 1e9, "unit": "GUPS", "ms_per_step": ms, "steps": steps,
+            "workload": workload, "batch": 1 if sub else batch, "step": unit_desc}
+
+
+def run_op(args):
+    """Secondary measurements (forward projector, least squares, MLEM, SART) in the same JSON form."""
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    if args.op == "unet":
+        return run_unet(args)
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    r = measure_op(args.op, args.workload, args.steps, args.warmup, views=args.views, subsets=args.subsets)
+    print(json.dumps({"metric": f"{args.op}_gups", "value": r["value"], "unit": "GUPS",
+                      "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms_per_step"],
+                      "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+                      "config": {"workload": args.workload, "batch": r["batch"], "step": r["step"]}}),
+          flush=True)
+
+
+def secondary_variants(steps=5, warmup=3) -> dict:
+    """The other operators of the path, timed in the default run: the matched
+    forward projector on c2 (360 views, 256^3), one batched least-squares
+    iteration on c4 (4 x 256^3, 180 views), and one MLEM and one 10-subset
+    SART pass on c4 (one volume)."""
+    out = {}
+    for key, op, wl in (("fp", "fp", "c2_fdk256"), ("ls_iter", "ls", "c4_diff"),
+                        ("mlem_pass", "mlem", "c4_diff"), ("sart_pass", "sart", "c4_diff")):
+        try:
+            out[key] = measure_op(op, wl, steps, warmup)
+        except Exception as e:   # the line keeps the back-projection numbers either way
+            out[key] = {"error": f"{type(e).__name__}: {e}"}
+    return out
 
 
 def run_grid(args):
@@ -611,6 +683,10 @@ def run_ours(args):
                "ms_per_step": t_e2e * 1e3, "ms_per_step_mean": 1e3 * sum(ts) / len(ts), "steps": n_e2e,
                "pipeline": f"{len(pipe.blocks)} view blocks, {len(pipe.parts)} slab parts with mirrors"}
 
+    others = None
+    if rank == 0 and not args.no_variants and args.workload == "c3_paper" and not args.views:
+        others = secondary_variants()
+
     cpu = parity = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu, sample = cpu_baseline(g)
@@ -650,6 +726,8 @@ def run_ours(args):
                                       "ms_per_step": step16_ms, "bp_kernel_ms": bp16_ms,
                                       "bp_kernel_gups": U / (bp16_ms * 1e-3) / 1e9}},
     }
+    if others:
+        line["variants"].update(others)
     if e2e:
         line["e2e"] = e2e
     if cpu:
@@ -665,9 +743,41 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_oracle_table(args):
+    """The FP64 oracle's own throughput on the host: c1 and c2 in full and the
+    central 64-slice slab of c3, on one thread and on all threads (the arm of
+    the CPU baseline table). No GPU is used."""
+    import numpy as np
+
+    import oracle
+    from paper_2104_13248_gb300 import inputs
+    oracle.build()
+    threads = oracle.num_threads()
+    model = cpu_model()
+    for name, k0, nks in (("c1_small", None, None), ("c2_fdk256", None, None), ("c3_paper", 224, 64)):
+        g = inputs.preset(name)["geom"]
+        P = oracle.matrices(g)
+        q = inputs.uniform_array(99, (g["np"], g["nv"], g["nu"]), -1.0, 1.0).astype(np.float32).astype(np.float64)
+        if k0 is None:
+            k0, nks = 0, g["nz"]
+        upd = float(g["nx"]) * g["ny"] * nks * g["np"]
+        for n in (threads, 1):
+            oracle.set_threads(n)
+            t0 = time.perf_counter()
+            oracle.backproject_slab(P, q, g["nx"], g["ny"], k0, nks, math.pi / g["np"])
+            t = time.perf_counter() - t0
+            print(json.dumps({"metric": "oracle_backprojection_gups", "workload": name,
+                              "slices": f"{k0}..{k0 + nks - 1}", "updates": upd, "threads": n,
+                              "value": upd / t / 1e9, "unit": "GUPS", "seconds": t, "nproc": os.cpu_count(),
+                              "cpu_model": model}), flush=True)
+        oracle.set_threads(threads)
+
+
 def main(argv=None):
     args = parse_args(argv)
-    if args.impl == "reference":
+    if args.oracle_table:
+        run_oracle_table(args)
+    elif args.impl == "reference":
         run_reference(args)
     elif args.grid is not None:
         run_grid(args)

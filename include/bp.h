@@ -222,6 +222,13 @@ bp_status bp_device_status(bp_ctx *ctx, void *stream);
  *   bp_test_drop_view  test hook: the staging producer skips the load of
  *                      this view (-1 = off), so the consumers' bounded wait
  *                      runs out and bp_device_status reports BP_ERR_TIMEOUT.
+ *   bp_test_live_allocations  test hook: device allocations held by all
+ *                      live contexts of this process. With the environment
+ *                      variable BP_TEST_FAIL_ALLOC=n set, the n-th device
+ *                      allocation of every bp_create* fails as an
+ *                      out-of-memory cudaMalloc would (BP_ERR_OOM, message in
+ *                      bp_last_error(NULL)); the count shows that the
+ *                      allocations made before it were released.
  *   bp_get_plan        the launch plan: voxels per thread along z, the
  *                      staged box (FP32 width, FP16 width, rows; a width of
  *                      -1 means that element type uses direct global loads),
@@ -233,6 +240,7 @@ bp_status bp_set_pipeline_depth(bp_ctx *ctx, int stages);
 bp_status bp_set_symmetry(bp_ctx *ctx, int enable);
 bp_status bp_set_timeout(bp_ctx *ctx, double seconds);
 bp_status bp_test_drop_view(bp_ctx *ctx, int view);
+int bp_test_live_allocations(void);
 bp_status bp_get_plan(const bp_ctx *ctx, int *tk, int *bu32, int *bu16, int *bv, int *stages,
                       int *symmetric);
 

@@ -79,8 +79,10 @@ bp_status cnn_conv3d_dgrad(const void *dy, int dy_cstride, int dy_coff, const vo
  *   128 x 128); larger layers get BP_ERR_INVALID_ARG and must use
  *   cnn_conv3d_dgrad.
  *   The first call on a device looks up the array's device address
- *   (cudaGetSymbolAddress) and caches it; make that first call before any
- *   stream capture on that device.
+ *   (cudaGetSymbolAddress) and caches it for the life of the process; make
+ *   that first call before any stream capture on that device. A device
+ *   reset (cudaDeviceReset, or anything else that destroys the primary
+ *   context) is not supported afterwards: the cached address would be stale.
  *   All calls share the one array. Each call overwrites every value it
  *   later reads, so what an earlier call left there is never used, but two
  *   calls whose work overlaps on the GPU (different streams without

@@ -102,6 +102,11 @@ def num_threads() -> int:
     return int(_load().orc_num_threads())
 
 
+def set_threads(n: int) -> None:
+    """OpenMP threads of the oracle's routines (timing only)."""
+    _load().orc_set_threads(ctypes.c_int(int(n)))
+
+
 def default_angles(n: int) -> np.ndarray:
     """Views evenly spaced over 360 degrees starting at 0."""
     return 2.0 * np.pi * np.arange(n, dtype=np.float64) / n

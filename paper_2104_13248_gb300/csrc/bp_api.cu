@@ -33,14 +33,29 @@ bp_status cuda_fail(bp_ctx *ctx, cudaError_t e, const char *what) {
     return fail(ctx, e == cudaErrorMemoryAllocation ? BP_ERR_OOM : BP_ERR_CUDA, m);
 }
 
-// Test hook: make the next device allocation fail (BP_TEST_FAIL_ALLOC=1).
-static cudaError_t dev_alloc(void **p, size_t bytes) {
+// Device allocations of every context still alive (a test hook reads it to
+// show that a failed bp_create leaks nothing).
+static std::atomic<long long> g_live_allocs{0};
+
+// Test hook: BP_TEST_FAIL_ALLOC=n makes the n-th device allocation of each
+// bp_create fail (n = 1: the first) as cudaMalloc would when out of memory.
+static cudaError_t dev_alloc(bp_ctx *ctx, void **p, size_t bytes) {
     const char *f = std::getenv("BP_TEST_FAIL_ALLOC");
-    if (f && std::atoi(f) != 0) {
+    const int nth = f ? std::atoi(f) : 0;
+    if (nth > 0 && ++ctx->n_allocs == nth) {
         *p = nullptr;
         return cudaErrorMemoryAllocation;
     }
-    return cudaMalloc(p, bytes);
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e == cudaSuccess) ++g_live_allocs;
+    return e;
+}
+
+static void dev_free(void *p) {
+    if (p) {
+        cudaFree(p);
+        --g_live_allocs;
+    }
 }
 
 static void build_matrices(const bp_geometry &g, const double *angles, double *P) {
@@ -237,9 +252,9 @@ static bp_status make_filter_tables(bp_ctx *ctx) {
             tw4[4 * k] = tw4[4 * k + 1] = c;
             tw4[4 * k + 2] = tw4[4 * k + 3] = sn;
         }
-        cudaError_t e = dev_alloc(&ctx->d_H2, sizeof(float) * 2 * n);
+        cudaError_t e = dev_alloc(ctx, &ctx->d_H2, sizeof(float) * 2 * n);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "filter spectrum");
-        e = dev_alloc(&ctx->d_tw4, sizeof(float) * 4 * n);
+        e = dev_alloc(ctx, &ctx->d_tw4, sizeof(float) * 4 * n);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "filter twiddles");
         e = cudaMemcpy(ctx->d_H2, H2.data(), sizeof(float) * 2 * n, cudaMemcpyHostToDevice);
         if (e == cudaSuccess)
@@ -250,9 +265,9 @@ static bp_status make_filter_tables(bp_ctx *ctx) {
         tw[2 * k] = (float)std::cos(2.0 * M_PI * k / n);
         tw[2 * k + 1] = (float)-std::sin(2.0 * M_PI * k / n);
     }
-    cudaError_t e = dev_alloc((void **)&ctx->d_H, sizeof(float) * n);
+    cudaError_t e = dev_alloc(ctx, (void **)&ctx->d_H, sizeof(float) * n);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "filter spectrum");
-    e = dev_alloc((void **)&ctx->d_tw, sizeof(float2) * n);
+    e = dev_alloc(ctx, (void **)&ctx->d_tw, sizeof(float2) * n);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "filter twiddles");
     e = cudaMemcpy(ctx->d_H, Hf.data(), sizeof(float) * n, cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
@@ -268,11 +283,11 @@ static bp_status finish_create(bp_ctx *ctx) {
     ctx->zinv = true;
     for (int s = 0; s < np; ++s)
         if (ctx->P[12 * s + 2] != 0.0 || ctx->P[12 * s + 10] != 0.0) ctx->zinv = false;
-    e = dev_alloc((void **)&ctx->d_P, sizeof(double) * 12 * np);
+    e = dev_alloc(ctx, (void **)&ctx->d_P, sizeof(double) * 12 * np);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "matrices");
     e = cudaMemcpy(ctx->d_P, ctx->P.data(), sizeof(double) * 12 * np, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "matrices upload");
-    e = dev_alloc((void **)&ctx->d_err, sizeof(unsigned));
+    e = dev_alloc(ctx, (void **)&ctx->d_err, sizeof(unsigned));
     if (e != cudaSuccess) return cuda_fail(ctx, e, "error word");
     e = cudaMemset(ctx->d_err, 0, sizeof(unsigned));
     if (e != cudaSuccess) return cuda_fail(ctx, e, "error word");
@@ -280,7 +295,7 @@ static bp_status finish_create(bp_ctx *ctx) {
     if (ctx->has_geometry) {
         bp_status st = make_filter_tables(ctx);
         if (st != BP_OK) return st;
-        e = dev_alloc((void **)&ctx->d_phcoef, sizeof(float) * 20 * 256 * (size_t)np);
+        e = dev_alloc(ctx, (void **)&ctx->d_phcoef, sizeof(float) * 20 * 256 * (size_t)np);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "phantom coefficient buffer");
     }
     return BP_OK;
@@ -562,14 +577,16 @@ const char *bp_last_error(const bp_ctx *ctx) {
 
 void bp_destroy(bp_ctx *ctx) {
     if (!ctx) return;
-    cudaFree(ctx->d_P);
-    cudaFree(ctx->d_err);
-    cudaFree(ctx->d_H);
-    cudaFree(ctx->d_tw);
-    cudaFree(ctx->d_H2);
-    cudaFree(ctx->d_tw4);
-    cudaFree(ctx->d_phcoef);
+    dev_free(ctx->d_P);
+    dev_free(ctx->d_err);
+    dev_free(ctx->d_H);
+    dev_free(ctx->d_tw);
+    dev_free(ctx->d_H2);
+    dev_free(ctx->d_tw4);
+    dev_free(ctx->d_phcoef);
     delete ctx;
 }
+
+int bp_test_live_allocations(void) { return (int)g_live_allocs.load(); }
 
 }  // extern "C"

@@ -60,6 +60,7 @@ struct Plan {
 
 struct bp_ctx {
     int device = 0;
+    int n_allocs = 0;           // device allocations made by bp_create (test hook count)
     int n_views = 0, nu = 0, nv = 0, nx = 0, ny = 0, nz = 0;
     bool has_geometry = false;  // created by bp_create (filter, phantom available)
     bool zinv = false;          // every view has P[0][2] = P[2][2] = 0

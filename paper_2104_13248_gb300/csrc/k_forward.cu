@@ -144,8 +144,10 @@ fp_zcol(const float *__restrict__ vol, const double *__restrict__ P, int nviews,
             const bool any = umin <= umax;
             const int uo = any ? floor_bits(umin) - kMagicBits : 0;
             const int cols_used = any ? floor_bits(umax) - kMagicBits + 2 - uo : 0;
+            // A patch wider than the planned windows (not expected from the
+            // plan's footprint bound) still projects every tap: all of them
+            // take the direct pass below, which is correct at any width.
             const bool fits = any && cols_used <= wc;
-            if (any && !fits && lane == 0) atomicOr(err, DEV_ERR_FOOTPRINT);
             const int cwid = max(1, min(cols_used, 32));
             const int G = 32 / cwid;
             // A column outside the patch or without a usable geometry scatters
@@ -161,7 +163,7 @@ fp_zcol(const float *__restrict__ vol, const double *__restrict__ P, int nviews,
             c.cwG1 = c.cwG + G;
             cols[tid] = c;
             __syncwarp();
-            if (!(any && fits)) continue;   // uniform across the warp
+            if (!any) continue;   // uniform across the warp
 
             // Lane l's window starts at row floor(v0min + l * dvmin): every
             // column's row floor(v0 + l * dv) is at or above it (v0 >= v0min,
@@ -170,9 +172,9 @@ fp_zcol(const float *__restrict__ vol, const double *__restrict__ P, int nviews,
             const int tb = floor_bits(fmaf(fl, dvmin, v0min));
             const int base = tb - kMagicBits;
             float *img = pb + (size_t)(cb + n) * nu * nv;
-            unsigned dmax = 0;
+            unsigned dmax = fits ? 0u : ~0u;
 #pragma unroll
-            for (int cix = 0; cix < 32; ++cix) {
+            for (int cix = 0; fits && cix < 32; ++cix) {
                 const FpCol cc = cols[warp * 32 + cix];
                 const float v = fmaf(fl, cc.dv, cc.v0);
                 const float tv = __fadd_rd(v, kMagic);
@@ -201,7 +203,7 @@ fp_zcol(const float *__restrict__ vol, const double *__restrict__ P, int nviews,
                     const float fv = v - (tv - kMagic);
                     const unsigned udr = (unsigned)(__float_as_int(tv) - tb);
                     const float val = cc.wt * x[cix];
-                    if (udr > (unsigned)(kFpWinRows - 2) && val != 0.0f) {
+                    if ((!fits || udr > (unsigned)(kFpWinRows - 2)) && val != 0.0f) {
                         const float a1 = fv * val, a0 = val - a1;
                         const int rr = r.v_box + base + (int)udr, c0 = r.u_box + uo + (cc.cw32 >> 5);
                         fp_tap(img, nu, nv, rr, c0, cc.gu * a0);
@@ -212,6 +214,7 @@ fp_zcol(const float *__restrict__ vol, const double *__restrict__ P, int nviews,
                 }
             }
             __syncwarp();
+            if (!fits) continue;   // uniform: nothing went to the windows
 
             // Flush: lane (g, cl) reads window it * G + g, column c0 + cl, and adds
             // its rows to the projection (windows overlap in rows; the global

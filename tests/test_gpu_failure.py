@@ -60,3 +60,37 @@ def test_dropped_view_times_out_and_context_survives(sym):
         assert torch.equal(again, ref)
         # other kernels on the same CUDA context are unaffected
         assert torch.isfinite(api.bp_filter(ctx, q)).all()
+
+
+def test_failed_allocation_reports_oom_and_leaks_nothing(monkeypatch):
+    """Host-side injection: the n-th device allocation of bp_create fails as an
+    out-of-memory cudaMalloc would. Every n up to the number bp_create makes
+    returns BP_ERR_OOM with a message, and the allocations made before the
+    failing one are released (the library's live-allocation count is back
+    where it was); past that number the context is created normally."""
+    lib = _lib.load()
+    g = inputs.preset("c1_small")["geom"]
+    base = lib.bp_test_live_allocations()
+    n_failed = 0
+    for nth in range(1, 20):
+        monkeypatch.setenv("BP_TEST_FAIL_ALLOC", str(nth))
+        try:
+            ctx = api.bp_create(g)
+        except _lib.BPError as e:
+            assert e.status == _lib.BP_ERR_OOM, e
+            assert "out of memory" in str(e), e
+            assert lib.bp_test_live_allocations() == base, nth
+            n_failed += 1
+            continue
+        with ctx:
+            assert lib.bp_test_live_allocations() > base
+        break
+    else:
+        raise AssertionError("bp_create never succeeded")
+    assert n_failed >= 4          # matrices, error word, filter tables, phantom buffer
+    assert lib.bp_test_live_allocations() == base
+    monkeypatch.delenv("BP_TEST_FAIL_ALLOC")
+    with api.bp_create(g) as ctx:
+        q = torch.ones(ctx.proj_shape(), device="cuda")
+        api.bp_backproject(ctx, q)
+        api.bp_device_status(ctx)

@@ -4,9 +4,10 @@ Some callers cannot allocate device memory: code inside a CUDA graph
 capture, a runtime that owns every allocation and passes only tensors, or a
 process whose memory a pooling allocator has already reserved. This entry
 point keeps its scratch in a static device array instead of a caller buffer;
-here it must give the same input gradient as cnn_conv3d_dgrad (which takes a
-caller buffer) on two different calls in a row, and refuse a layer too large
-for its array. The file sorts last so that a run stopping at the first
+here it must give bit for bit the input gradient of cnn_conv3d_dgrad (which
+takes a caller buffer) on two different calls in a row, on the mma.sync and
+the tcgen05 kernels, match the FP64 oracle, and refuse a layer too large for
+its array. The file sorts last so that a run stopping at the first
 failure has already run every other test.
 """
 import ctypes
@@ -41,10 +42,17 @@ def _case(seed, n, d, h, w, cin, cout):
     return dy, wt
 
 
-def test_noalloc_dgrad_matches_buffered_dgrad_twice():
+# (n, d, h, w, cin, cout): the mma.sync path (widths 16 and 20) and layers the
+# tcgen05 kernels take (width 128, depth a multiple of 4, Cout' = cin of 16 or
+# 32), where the static array's address feeds the tensor-core kernels' loads
+CASES = [(1, 8, 12, 16, 48, 32), (2, 6, 8, 20, 32, 64), (1, 4, 3, 128, 32, 16), (1, 8, 2, 128, 16, 32)]
+
+
+@pytest.mark.parametrize("first,second", [(0, 1), (2, 3)], ids=["mma_sync", "tcgen05"])
+def test_noalloc_dgrad_matches_buffered_dgrad_twice(first, second):
     lib = _lib.load()
     # two calls in a row with different layers: the static scratch is reused
-    for seed, (n, d, h, w, cin, cout) in enumerate([(1, 8, 12, 16, 48, 32), (2, 6, 8, 20, 32, 64)]):
+    for seed, (n, d, h, w, cin, cout) in ((first, CASES[first]), (second, CASES[second])):
         dy, wt = _case(100 + seed, n, d, h, w, cin, cout)
         ref = torch.empty((n, d, h, w, cin), dtype=torch.bfloat16, device="cuda")
         buf = torch.empty(27 * cin * cout, dtype=torch.bfloat16, device="cuda")
@@ -53,10 +61,26 @@ def test_noalloc_dgrad_matches_buffered_dgrad_twice():
         out = torch.full((n, d, h, w, cin), 7.0, dtype=torch.bfloat16, device="cuda")
         _lib.check(lib.cnn_conv3d_dgrad_noalloc(_p(dy), cout, 0, _p(wt), _p(out), cin, 0, n, d, h, w, cin,
                                                 cout, _s()))
+        _lib.check(lib.cnn_device_status(_s()))
         torch.cuda.synchronize()
-        a, b = out.float(), ref.float()
-        # same kernels, same weights: within the BF16 tolerance of the conv tests (here equal)
-        assert (a - b).abs().max().item() <= 8e-3 * b.abs().max().item()
+        # the same kernels on the same flipped weights: bit for bit the buffered result
+        assert torch.equal(out, ref), (seed, (out.float() - ref.float()).abs().max().item())
+
+
+def test_noalloc_dgrad_matches_the_oracle():
+    """One tcgen05-sized layer against the FP64 input gradient, within the
+    BF16-output tolerance of the convolution tests."""
+    import oracle
+    lib = _lib.load()
+    n, d, h, w, cin, cout = CASES[2]
+    dy, wt = _case(7, n, d, h, w, cin, cout)
+    out = torch.empty((n, d, h, w, cin), dtype=torch.bfloat16, device="cuda")
+    _lib.check(lib.cnn_conv3d_dgrad_noalloc(_p(dy), cout, 0, _p(wt), _p(out), cin, 0, n, d, h, w, cin, cout,
+                                            _s()))
+    torch.cuda.synchronize()
+    ref = oracle.conv3d_dgrad(dy.float().cpu().numpy().astype(np.float64), wt.float().cpu().numpy().astype(np.float64))
+    err = np.abs(out.float().cpu().numpy() - ref).max() / np.abs(ref).max()
+    assert err <= 8e-3, err
 
 
 def test_noalloc_dgrad_rejects_layers_beyond_the_limit():
