@@ -193,7 +193,7 @@ def _oracle_slab_rate(oracle, P, q, g, k0, max_slices, chunk, budget_s):
     return upd / t / 1e9, done, t, np.concatenate(parts, axis=0)
 
 
-def cpu_baseline(g, budget_s=12.0, max_slices=32, budget_1t_s=6.0):
+def cpu_baseline(g, budget_s=12.0, max_slices=64, budget_1t_s=6.0):
     """The FP64 oracle back-projecting a central z-slab of the workload on the
     host cores (bounded in time), on all threads and on one. The slab is
     split over (slice, row) pairs, so every thread works even on a thin slab.

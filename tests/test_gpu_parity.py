@@ -1,10 +1,10 @@
 """CUDA path vs the FP64 oracle, element by element, on the same seeded inputs.
 
-Tolerances (max |gpu - oracle| / max |oracle|): 1e-5 for FP32 back-projection
-and forward projection, 2e-3 for FP16-stored projections (against the
-unquantised input), 2e-5 for the FFT ramp filter (FP32 FFT rounding grows
-with log2 N; the filter output is not a target of its own), 1e-4 for the
-FP32 phantom generator (input data only).
+Tolerances (max |gpu - oracle| / max |oracle|): 1e-5 for every FP32 path
+(back-projection, forward projection, the FFT ramp filter and FDK end to end;
+on uniform noise as well as on phantom data), 2e-3 for FP16-stored
+projections (against the unquantised input), 1e-4 for the FP32 phantom
+generator (input data only).
 """
 import math
 
@@ -58,7 +58,7 @@ def test_filter_c1(c1):
         out = api.bp_filter(ctx, torch.from_numpy(c1["raw"]).cuda()).cpu().numpy()
         out16 = api.bp_filter(ctx, torch.from_numpy(c1["raw"]).cuda(), out_dtype=torch.float16).cpu().numpy()
     print(f"filter c1 rel err {rel(out, ref):.2e}")
-    assert rel(out, ref) <= 2e-5
+    assert rel(out, ref) <= TOL32
     # FP16 output = round-to-nearest of the FP32 result
     assert rel(out16.astype(np.float64), ref) <= 1e-3
 
@@ -76,7 +76,7 @@ def test_filter_sizes(nu):
         out = api.bp_filter(ctx, torch.from_numpy(raw).cuda()).cpu().numpy()
         out16 = api.bp_filter(ctx, torch.from_numpy(raw).cuda(), out_dtype=torch.float16).cpu().numpy()
     print(f"filter nu={nu} rel err {rel(out, ref):.2e}")
-    assert rel(out, ref) <= 2e-5
+    assert rel(out, ref) <= TOL32
     assert rel(out16.astype(np.float64), ref) <= 1e-3
 
 
@@ -100,7 +100,7 @@ def test_fdk_end_to_end_c1(c1):
     with api.bp_create(g) as ctx:
         vol = api.fdk(ctx, torch.from_numpy(c1["raw"]).cuda()).cpu().numpy()
     print(f"FDK c1 rel err {rel(vol, ref):.2e}")
-    assert rel(vol, ref) <= 2e-5
+    assert rel(vol, ref) <= TOL32
 
 
 def test_backproject_fp16_c1(c1):
@@ -144,8 +144,9 @@ def test_backproject_ragged(dims, dtype):
         vol = api.bp_backproject(ctx, torch.from_numpy(q).cuda(), scale=0.5).cpu().numpy()
         api.bp_device_status(ctx)
     print(f"ragged {dims} {dtype} uniform-noise rel err {rel(vol, ref):.2e}")
-    # uniform noise is the worst case for FP32 position rounding: 5e-5
-    assert rel(vol, ref) <= 5e-5
+    # uniform noise is the hardest case for FP32 position rounding (steep data,
+    # small max|vol| from cancellation); FP16 values are exact inputs here
+    assert rel(vol, ref) <= TOL32
 
 
 FP_GEOMS = {
@@ -180,8 +181,7 @@ def test_forward_project_ragged(name):
         rhs = torch.dot(torch.from_numpy(q).cuda().double().flatten(), fx.double().flatten()).item()
         norm = bq.double().norm().item() * float(np.linalg.norm(x))
     print(f"fp {name} rel err {rel(fx.cpu().numpy(), ref):.2e}")
-    # FP32 positions and reductions in another order: the back-projection's ragged bound
-    assert rel(fx.cpu().numpy(), ref) <= 5e-5
+    assert rel(fx.cpu().numpy(), ref) <= TOL32
     assert abs(lhs - rhs) <= 1e-6 * norm
 
 
@@ -199,8 +199,8 @@ def test_flipped_detector_rows():
         api.bp_device_status(ctx)
     print(f"flipped rows: fp rel err {rel(fx, oracle.forward_project(P, x, g['nu'], g['nv'])):.2e}, "
           f"bp {rel(bq, oracle.backproject(P, q, g['nx'], g['ny'], g['nz'])):.2e}")
-    assert rel(fx, oracle.forward_project(P, x, g["nu"], g["nv"])) <= 5e-5
-    assert rel(bq, oracle.backproject(P, q, g["nx"], g["ny"], g["nz"])) <= 5e-5
+    assert rel(fx, oracle.forward_project(P, x, g["nu"], g["nv"])) <= TOL32
+    assert rel(bq, oracle.backproject(P, q, g["nx"], g["ny"], g["nz"])) <= TOL32
 
 
 def test_backproject_batch_accumulate_and_view_chunks(c1):
@@ -238,8 +238,8 @@ def test_backproject_general_matrices():
         fp = api.fp_project(ctx, torch.from_numpy(ref.astype(np.float32)).cuda()).cpu().numpy()
     fref = oracle.forward_project(P, ref.astype(np.float32), g["nu"], g["nv"])
     print(f"general matrices uniform-noise: bp rel err {rel(vol, ref):.2e}, fp {rel(fp, fref):.2e}")
-    assert rel(vol, ref) <= 5e-5
-    assert rel(fp, fref) <= 5e-5
+    assert rel(vol, ref) <= TOL32
+    assert rel(fp, fref) <= TOL32
 
 
 def test_forward_project_and_adjoint(c1):
@@ -382,7 +382,6 @@ def test_offcentre_phantom_fp32_fp16(offc, name):
     with api.bp_create(g) as ctx:
         plan = api.bp_get_plan(ctx)
         assert not plan["symmetric"]
-        assert (plan["bu32"] > 0) == (name == "tma_128")
         vol = api.bp_backproject(ctx, torch.from_numpy(c["q"]).cuda(), scale=c["scale"]).cpu().numpy()
         vol16 = api.bp_backproject(ctx, torch.from_numpy(q16).cuda(), scale=c["scale"]).cpu().numpy()
         api.bp_device_status(ctx)
