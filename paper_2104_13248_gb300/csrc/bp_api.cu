@@ -213,7 +213,8 @@ static void make_plan(bp_ctx *ctx) {
     int wbu, wbv;
     max_footprint(ctx, 8, 4, 32, 1, &wbu, &wbv);
     wbu += 1;
-    pl.fp_wbu = (pl.bu > 0 && fp_smem_bytes(wbu) <= 227 * 1024) ? wbu : -1;
+    wbu = fp_window_width(wbu);
+    pl.fp_wbu = (pl.bu > 0 && wbu > 0 && fp_smem_bytes(wbu) <= 227 * 1024) ? wbu : -1;
 }
 
 // Ramp filter tables: real spectrum of the circularly embedded Ram-Lak

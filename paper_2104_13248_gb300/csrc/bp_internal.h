@@ -103,6 +103,7 @@ bp_status launch_forward(bp_ctx *ctx, const float *vol, float *proj, int batch, 
                          cudaStream_t st);
 // Dynamic shared memory of the forward projector for windows wc columns wide.
 int fp_smem_bytes(int wc);
+int fp_window_width(int need);   // smallest window width the forward projector is built for, or -1
 bp_status launch_filter(bp_ctx *ctx, const float *proj, void *out, bp_dtype out_t,
                         long long n_views_total, cudaStream_t st);
 bp_status launch_phantom(bp_ctx *ctx, const double *d_ell, int n_ell, float *proj,

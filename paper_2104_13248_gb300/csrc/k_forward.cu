@@ -18,6 +18,17 @@
 // overlapping windows add up there. A tap beyond its lane's window
 // (columns whose rows drift further apart) is added to the projection
 // directly.
+//
+// Window layout (one warp): row plane dr (0..2) of kPlane words, then
+// column c at a pitch of 33 words, then lane l at slot (l * cw) mod 32, cw
+// the odd flush width of the view. Word dr * kPlane + 33 c + ((l cw) & 31)
+// is distinct for every (dr, c, l) and sits in bank (c + l cw) mod 32:
+//   - a scatter (one column, 32 lanes) touches 32 banks, since cw is odd;
+//   - the flush reads cell l * cw + c of a row plane with lane (l cw + c)
+//     mod 32, so 32 consecutive cells are 32 banks, and consecutive lanes
+//     add consecutive detector columns (coalesced reductions);
+//   - a voxel's four taps are one address plus immediate offsets (+33 for
+//     the next column, +kPlane for the next row).
 #include "geom_dev.cuh"
 
 namespace bp {
@@ -25,26 +36,40 @@ namespace bp {
 constexpr int kFpTX = 32, kFpTY = 8, kFpTK = 32;
 constexpr int kFpThreads = kFpTX * kFpTY;
 constexpr int kFpWinRows = 3;     // detector rows of a lane's window
-constexpr int kFpRecChunk = 64;   // view records staged per pass
+constexpr int kFpRecChunk = 32;   // view records staged per pass
+constexpr int kFpColPitch = 33;   // words between window columns
 
-// Per (column, view) quantities shared by the 32 lanes that scatter the
-// column's voxels (computed once per view by the thread owning the column).
-struct __align__(16) FpCol {
-    float v0, dv, wt, fu;   // v of the first voxel and per voxel (box-relative), 1 / W^2, u fraction
-    float gu;               // 1 - fu
-    int cw32, cwG, cwG1;    // window column * 32, window column * G and (column + 1) * G, G the
-                            // windows a flush pass reads; wt = 0 marks a column without voxels
+template <int WC>
+struct FpWin {
+    static_assert(WC % 2 == 1, "odd window widths: any used width rounds up to an odd flush width");
+    static constexpr int kPlane = (WC * kFpColPitch + 31) / 32 * 32;   // a multiple of 32 words
+    static constexpr int kWarpWords = kFpWinRows * kPlane;
 };
 
-// Window layout of one warp: row dr (0..kFpWinRows-1), column c (0..wc-1)
-// and lane l at word (dr * wc + c) * 32 + ((l + c * G) & 31), with G the
-// number of windows the flush reads per pass (32 / used width, or 1). A
-// scatter (one column, 32 lanes) touches 32 different banks, and so do the
-// live lanes of a flush pass (G windows of cw consecutive columns,
-// G * cw <= 32).
+// Per (column pair, view) quantities of the two columns 2p, 2p+1 of a warp's
+// patch, written by the threads owning the columns and read by every lane.
+struct __align__(16) FpPair {
+    float2 v0, dv;   // v of the first voxel and per voxel (box-relative)
+    float2 wt, fu;   // 1 / W^2 (0: a column without voxels), u fraction
+    int2 cw;         // window column * 33
+    int2 pad;
+};
+
+// Window widths the kernel is built for (odd; the plan takes the smallest
+// that holds the widest u footprint of a patch).
+constexpr int kFpWidths[] = {17, 21, 25, 33, 49};
+
+int fp_window_width(int need) {
+    for (int w : kFpWidths)
+        if (need <= w) return w;
+    return -1;
+}
+
+static int fp_plane_words(int wc) { return (wc * kFpColPitch + 31) / 32 * 32; }
+
 int fp_smem_bytes(int wc) {
-    return kFpRecChunk * (int)sizeof(ViewRec) + kFpThreads * (int)sizeof(FpCol) +
-           (kFpThreads / 32) * kFpWinRows * wc * 32 * (int)sizeof(float);
+    return kFpRecChunk * (int)sizeof(ViewRec) + (kFpThreads / 32) * 16 * (int)sizeof(FpPair) +
+           (kFpThreads / 32) * kFpWinRows * fp_plane_words(wc) * (int)sizeof(float);
 }
 
 __device__ __forceinline__ void fp_tap(float *img, int nu, int nv, int row, int col, float a) {
@@ -54,34 +79,141 @@ __device__ __forceinline__ void fp_tap(float *img, int nu, int nv, int row, int 
 
 __device__ __forceinline__ int floor_bits(float v) { return __float_as_int(__fadd_rd(v, kMagic)); }
 
-template <int TK>
+// Order-preserving map of a float to a signed int, so warp min / max run as
+// one integer reduction (redux.sync).
+__device__ __forceinline__ int fkey(float f) {
+    const int b = __float_as_int(f);
+    return b >= 0 ? b : b ^ 0x7fffffff;
+}
+__device__ __forceinline__ float fkey_inv(int k) { return __int_as_float(k >= 0 ? k : k ^ 0x7fffffff); }
+__device__ __forceinline__ float warp_fmin(float f) { return fkey_inv(__reduce_min_sync(0xffffffffu, fkey(f))); }
+__device__ __forceinline__ float warp_fmax(float f) { return fkey_inv(__reduce_max_sync(0xffffffffu, fkey(f))); }
+
+// Flush: each row plane of a warp's windows holds 32 windows x cw columns;
+// lane t takes cells it * 32 + t (window l = cell / cw, column c = cell mod
+// cw) and adds rows b_l, b_l + 1 and b_l + 2 of detector column ucol0 + c to
+// the projection. Consecutive lanes hold consecutive columns of a window,
+// so the reductions coalesce; the windows overlap in rows, and the global
+// reductions sum them.
+template <int kPlane>
+__device__ __forceinline__ void fp_flush(const float *win, float *img, int nu, int nv, int cw, int cols_used,
+                                         int base, int vbox, int ucol0, int lane) {
+    // the window bases are monotone in the lane: the end lanes bound the rows
+    const int bf = __shfl_sync(0xffffffffu, base, 0), bl = __shfl_sync(0xffffffffu, base, 31);
+    const bool rows_in = vbox + min(bf, bl) >= 0 && vbox + max(bf, bl) + kFpWinRows - 1 < nv;
+    // l = lane / cw and c = lane mod cw, and the step of 32 cells as q windows
+    // plus rem columns: exact, since a quotient below 33 that is not an
+    // integer lies at least 1 / cw from the next one, far beyond the rounding
+    const float rcw = __frcp_rn((float)cw);
+    int l = __float2int_rz(fmaf((float)lane, rcw, 0.01f));
+    int c = lane - l * cw;
+    const int q = __float2int_rz(fmaf(32.0f, rcw, 0.01f));
+    const int rem = 32 - q * cw;
+    for (int it = 0; it < cw; ++it) {
+        const int rowb = __shfl_sync(0xffffffffu, base, l & 31);
+        const int word = c * kFpColPitch + ((l * cw) & 31);
+        const float e0 = win[word], e1 = win[word + kPlane], e2 = win[word + 2 * kPlane];
+        const int gc = ucol0 + c, row = vbox + rowb;
+        const bool live = c < cols_used && (unsigned)gc < (unsigned)nu;
+        float *d = img + ((long long)row * nu + gc);
+        if (rows_in) {
+            // all rows inside the detector (the common case): no row checks,
+            // and zero cells are added too (cheaper than testing them)
+            if (live) {
+                atomicAdd(d, e0);
+                atomicAdd(d + nu, e1);
+                atomicAdd(d + 2 * nu, e2);
+            }
+        } else if (live) {
+            if (e0 != 0.0f && (unsigned)row < (unsigned)nv) atomicAdd(d, e0);
+            if (e1 != 0.0f && (unsigned)(row + 1) < (unsigned)nv) atomicAdd(d + nu, e1);
+            if (e2 != 0.0f && (unsigned)(row + 2) < (unsigned)nv) atomicAdd(d + 2 * nu, e2);
+        }
+        c += rem;
+        l += q;
+        if (c >= cw) {
+            c -= cw;
+            ++l;
+        }
+    }
+}
+
+// The taps of lane l's voxel in columns 2p and 2p+1 of the warp's patch:
+// v, its floor and fraction for both columns as f32x2 pairs (each lane of a
+// pair computed exactly as the scalar back-projector does), then the value
+// times scale / W^2 split between rows floor(v) and floor(v) + 1.
+struct FpTaps {
+    float2 fu, gu, a0, a1;   // u fraction, 1 - fu, (1 - fv) val, fv val
+    int ra, rb;              // window rows floor(v) - lane base (columns 2p, 2p+1)
+};
+
+__device__ __forceinline__ FpTaps fp_taps(const FpPair &pr, float2 x, float2 fl2, int tb) {
+    const float2 M2 = make_float2(kMagic, kMagic), NM2 = make_float2(-kMagic, -kMagic);
+    const float2 V = __ffma2_rn(fl2, pr.dv, pr.v0);
+    const float2 TV = __fadd2_rd(V, M2);
+    const float2 FL = __fadd2_rn(TV, NM2);
+    const float2 FV = __fadd2_rn(V, make_float2(-FL.x, -FL.y));
+    const float2 VAL = __fmul2_rn(pr.wt, x);
+    FpTaps t;
+    t.a1 = __fmul2_rn(FV, VAL);
+    t.a0 = __fadd2_rn(VAL, make_float2(-t.a1.x, -t.a1.y));
+    t.fu = pr.fu;
+    t.gu = __fadd2_rn(make_float2(1.0f, 1.0f), make_float2(-pr.fu.x, -pr.fu.y));
+    t.ra = __float_as_int(TV.x) - tb;
+    t.rb = __float_as_int(TV.y) - tb;
+    return t;
+}
+
+// Read-add-write of one voxel's four taps at window word w (rows drc and
+// drc + 1, columns cwin and cwin + 1).
+template <int kPlane>
+__device__ __forceinline__ void fp_add4(float *w, float gu, float fu, float a0, float a1) {
+    w[0] = fmaf(gu, a0, w[0]);
+    w[kFpColPitch] = fmaf(fu, a0, w[kFpColPitch]);
+    w[kPlane] = fmaf(gu, a1, w[kPlane]);
+    w[kPlane + kFpColPitch] = fmaf(fu, a1, w[kPlane + kFpColPitch]);
+}
+
+// Taps straight to the projection (global reductions): every tap of the
+// voxel when `all`, else only a voxel whose rows lie beyond its window.
+__device__ __forceinline__ void fp_direct(float *img, int nu, int nv, int row0, int col0, float gu, float fu,
+                                          float a0, float a1, int dr, bool all) {
+    if (all || (unsigned)dr > (unsigned)(kFpWinRows - 2)) {
+        const int rr = row0 + dr;
+        fp_tap(img, nu, nv, rr, col0, gu * a0);
+        fp_tap(img, nu, nv, rr, col0 + 1, fu * a0);
+        fp_tap(img, nu, nv, rr + 1, col0, gu * a1);
+        fp_tap(img, nu, nv, rr + 1, col0 + 1, fu * a1);
+    }
+}
+
+template <int WC>
 __global__ void __launch_bounds__(kFpThreads, 3)
-fp_zcol(const float *__restrict__ vol, const double *__restrict__ P, int nviews, int nu, int nv,
-        int nx, int ny, int nz, int bu, int bv, int wc, float scale, float *__restrict__ proj,
-        unsigned *err) {
-    static_assert(TK == 32, "one lane per voxel of a 32-voxel column chunk");
+fp_zwin(const float *__restrict__ vol, const double *__restrict__ P, int nviews, int nu, int nv,
+        int nx, int ny, int nz, int bu, int bv, float scale, float *__restrict__ proj, unsigned *err) {
+    constexpr int kPlane = FpWin<WC>::kPlane;
+    constexpr int kWarpWords = FpWin<WC>::kWarpWords;
     extern __shared__ __align__(16) unsigned char smem[];
     ViewRec *recs = reinterpret_cast<ViewRec *>(smem);
-    FpCol *cols = reinterpret_cast<FpCol *>(smem + kFpRecChunk * sizeof(ViewRec));
-    const int wwords = kFpWinRows * wc * 32;   // one warp's windows
-    const int rstride = wc * 32;               // words between window rows
-    float *win = reinterpret_cast<float *>(smem + kFpRecChunk * sizeof(ViewRec) + kFpThreads * sizeof(FpCol)) +
-                 (threadIdx.x >> 5) * wwords;
-
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    FpPair *pairs = reinterpret_cast<FpPair *>(smem + kFpRecChunk * sizeof(ViewRec)) + warp * 16;
+    float *win = reinterpret_cast<float *>(smem + kFpRecChunk * sizeof(ViewRec) +
+                                           (kFpThreads / 32) * 16 * sizeof(FpPair)) +
+                 warp * kWarpWords;
+
     const int ntx = (nx + kFpTX - 1) / kFpTX;
     const int i0 = (blockIdx.x % ntx) * kFpTX, j0 = (blockIdx.x / ntx) * kFpTY;
-    const int k0 = blockIdx.y * TK;
+    const int k0 = blockIdx.y * kFpTK;
     const int b = blockIdx.z;
-    const int ex = min(kFpTX, nx - i0), ey = min(kFpTY, ny - j0), ez = min(TK, nz - k0);
+    const int ex = min(kFpTX, nx - i0), ey = min(kFpTY, ny - j0), ez = min(kFpTK, nz - k0);
     // column owned by this thread for the per-view setup (8 x 4 patch per warp)
     const int wx = warp % (kFpTX / 8), wy = warp / (kFpTX / 8);
     const int di = wx * 8 + (lane & 7), dj = wy * 4 + (lane >> 3);
     const bool col_ok = di < ex && dj < ey;
     const float fdi = (float)di, fdj = (float)dj;
 
-    // lane l holds voxel k0 + l of each of the warp's 32 columns
-    float x[32];
+    // lane l holds voxel k0 + l of columns 2p and 2p + 1 in x2[p]
+    float2 x2[16];
     {
         const size_t plane = (size_t)nx * ny;
         const bool kin = lane < ez;
@@ -89,30 +221,33 @@ fp_zcol(const float *__restrict__ vol, const double *__restrict__ P, int nviews,
         for (int c = 0; c < 32; ++c) {
             const int cdi = wx * 8 + (c & 7), cdj = wy * 4 + (c >> 3);
             const bool ok = kin && cdi < ex && cdj < ey;
-            x[c] = ok ? scale * vol[((size_t)b * nz + k0 + lane) * plane + (size_t)(j0 + cdj) * nx + (i0 + cdi)]
-                      : 0.0f;
+            const float xv = ok ? scale * vol[((size_t)b * nz + k0 + lane) * plane + (size_t)(j0 + cdj) * nx + (i0 + cdi)]
+                                : 0.0f;
+            if (c & 1) x2[c >> 1].y = xv;
+            else x2[c >> 1].x = xv;
         }
     }
     float *pb = proj + (size_t)b * nviews * nu * nv;
-    for (int t = 4 * lane; t < wwords; t += 128) *reinterpret_cast<float4 *>(win + t) = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int t = 4 * lane; t < kWarpWords; t += 128) *reinterpret_cast<float4 *>(win + t) = make_float4(0.f, 0.f, 0.f, 0.f);
+    const float fl = (float)lane;
+    const float2 fl2 = make_float2(fl, fl);
+    float *pf = reinterpret_cast<float *>(pairs) + (lane >> 1) * (int)(sizeof(FpPair) / 4) + (lane & 1);
 
     for (int cb = 0; cb < nviews; cb += kFpRecChunk) {
         const int cn = min(kFpRecChunk, nviews - cb);
-        __syncthreads();
+        __syncthreads();   // every warp is done with the previous chunk's records
         for (int n = tid; n < cn; n += kFpThreads) {
             ViewRec r;
             if (!make_rec(P + 12 * (size_t)(cb + n), i0, j0, k0, ex, ey, ez, 4, bu, bv, &r))
                 atomicOr(err, DEV_ERR_FOOTPRINT);
             recs[n] = r;
         }
+        __syncthreads();
         for (int n = 0; n < cn; ++n) {
-            __syncthreads();   // records ready; previous view's column setup consumed
             const ViewRec r = recs[n];
-            FpCol c;
             float uL = 0.0f, cv0 = 0.0f, cdv = 0.0f, cwt = 0.0f, cfu = 0.0f;
             int cu = 0;
             bool cok = false;
-            float umin = 3e38f, umax = -3e38f, v0min = 3e38f, dvmin = 3e38f;
             if (col_ok) {
                 float W = fmaf(r.Wj, fdj, fmaf(r.Wi, fdi, r.W0));
                 float inv = col_rcp(W);
@@ -125,146 +260,95 @@ fp_zcol(const float *__restrict__ vol, const double *__restrict__ P, int nviews,
                 cfu = uL - (tu - kMagic);
                 if (uL == uL && cv0 == cv0) {
                     // every coordinate stays far inside the range of the round-to-integer trick
-                    if (fabsf(cdv) < 1e4f && fabsf(cv0) < 1e6f && fabsf(uL) < 1e6f) {
-                        cok = true;
-                        umin = umax = uL;
-                        v0min = cv0;
-                        dvmin = cdv;
-                    } else {
-                        atomicOr(err, DEV_ERR_FOOTPRINT);
-                    }
+                    if (fabsf(cdv) < 1e4f && fabsf(cv0) < 1e6f && fabsf(uL) < 1e6f) cok = true;
+                    else atomicOr(err, DEV_ERR_FOOTPRINT);
                 }
             }
-            for (int o = 16; o > 0; o >>= 1) {
-                umin = fminf(umin, __shfl_xor_sync(0xffffffffu, umin, o));
-                umax = fmaxf(umax, __shfl_xor_sync(0xffffffffu, umax, o));
-                v0min = fminf(v0min, __shfl_xor_sync(0xffffffffu, v0min, o));
-                dvmin = fminf(dvmin, __shfl_xor_sync(0xffffffffu, dvmin, o));
-            }
-            const bool any = umin <= umax;
-            const int uo = any ? floor_bits(umin) - kMagicBits : 0;
-            const int cols_used = any ? floor_bits(umax) - kMagicBits + 2 - uo : 0;
-            // A patch wider than the planned windows (not expected from the
-            // plan's footprint bound) still projects every tap: all of them
-            // take the direct pass below, which is correct at any width.
-            const bool fits = any && cols_used <= wc;
-            const int cwid = max(1, min(cols_used, 32));
-            const int G = 32 / cwid;
-            // A column outside the patch or without a usable geometry scatters
-            // zeros at window row 0, column 0 (no branch in the scatter loop).
-            c.v0 = cok ? cv0 : v0min;
-            c.dv = cok ? cdv : dvmin;
-            c.wt = cok ? cwt : 0.0f;
-            c.fu = cok ? cfu : 0.0f;
-            c.gu = 1.0f - c.fu;
+            const float umin = warp_fmin(cok ? uL : 3e38f), umax = warp_fmax(cok ? uL : -3e38f);
+            if (!(umin <= umax)) continue;   // no column with voxels: uniform across the warp
+            const float v0min = warp_fmin(cok ? cv0 : 3e38f), v0max = warp_fmax(cok ? cv0 : -3e38f);
+            const float dvmin = warp_fmin(cok ? cdv : 3e38f), dvmax = warp_fmax(cok ? cdv : -3e38f);
+            const int uo = floor_bits(umin) - kMagicBits;
+            const int cols_used = floor_bits(umax) - kMagicBits + 2 - uo;
+            // A column outside the patch or without a usable geometry adds zeros
+            // at window row 0, column 0.
             const int cwin = cok ? cu - uo : 0;
-            c.cw32 = cwin * 32;
-            c.cwG = cwin * G;
-            c.cwG1 = c.cwG + G;
-            cols[tid] = c;
+            pf[0] = cok ? cv0 : v0min;
+            pf[2] = cok ? cdv : dvmin;
+            pf[4] = cok ? cwt : 0.0f;
+            pf[6] = cok ? cfu : 0.0f;
+            reinterpret_cast<int *>(pf)[8] = cwin * kFpColPitch;
+            reinterpret_cast<int *>(pf)[10] = cwin;
             __syncwarp();
-            if (!any) continue;   // uniform across the warp
 
             // Lane l's window starts at row floor(v0min + l * dvmin): every
-            // column's row floor(v0 + l * dv) is at or above it (v0 >= v0min,
-            // dv >= dvmin, l >= 0, and fmaf and the floor are monotone).
-            const float fl = (float)lane;
+            // column's row floor(v0 + l * dv) is at or above it and at or below
+            // floor(v0max + l * dvmax) (v0min <= v0 <= v0max, dvmin <= dv <= dvmax,
+            // l >= 0, and fmaf and the floor are monotone).
             const int tb = floor_bits(fmaf(fl, dvmin, v0min));
             const int base = tb - kMagicBits;
             float *img = pb + (size_t)(cb + n) * nu * nv;
-            unsigned dmax = fits ? 0u : ~0u;
+            const int row0 = r.v_box + base, ucol0 = r.u_box + uo;
+            const bool fits = cols_used <= WC;
+            if (fits) {
+                const int cw = cols_used | 1;   // odd flush width
+                float *wl = win + ((lane * cw) & 31);
+                const int th = floor_bits(fmaf(fl, dvmax, v0max));
+                if (__all_sync(0xffffffffu, th - tb <= 1)) {
+                    // every row of every lane is inside its window: no checks
 #pragma unroll
-            for (int cix = 0; fits && cix < 32; ++cix) {
-                const FpCol cc = cols[warp * 32 + cix];
-                const float v = fmaf(fl, cc.dv, cc.v0);
-                const float tv = __fadd_rd(v, kMagic);
-                const float fv = v - (tv - kMagic);
-                const unsigned udr = (unsigned)(__float_as_int(tv) - tb);   // >= 0 as a signed value
-                dmax = max(dmax, udr);
-                const bool in = udr <= (unsigned)(kFpWinRows - 2);
-                const int drc = in ? (int)udr : 0;
-                const float val = in ? cc.wt * x[cix] : 0.0f;   // beyond the window: the pass below
-                const float a1 = fv * val, a0 = val - a1;       // (1-fv) val, fv val
-                const int w0 = drc * rstride + cc.cw32 + ((lane + cc.cwG) & 31);
-                const int w1 = drc * rstride + cc.cw32 + 32 + ((lane + cc.cwG1) & 31);
-                win[w0] += cc.gu * a0;
-                win[w1] += cc.fu * a0;
-                win[w0 + rstride] += cc.gu * a1;
-                win[w1 + rstride] += cc.fu * a1;
-            }
-            if (__any_sync(0xffffffffu, lane < ez && dmax > (unsigned)(kFpWinRows - 2))) {
-                // taps beyond a lane's window go straight to the projection
-#pragma unroll
-                for (int cix = 0; cix < 32; ++cix) {
-                    const FpCol cc = cols[warp * 32 + cix];
-                    if (cc.wt == 0.0f) continue;   // uniform across the warp
-                    const float v = fmaf(fl, cc.dv, cc.v0);
-                    const float tv = __fadd_rd(v, kMagic);
-                    const float fv = v - (tv - kMagic);
-                    const unsigned udr = (unsigned)(__float_as_int(tv) - tb);
-                    const float val = cc.wt * x[cix];
-                    if ((!fits || udr > (unsigned)(kFpWinRows - 2)) && val != 0.0f) {
-                        const float a1 = fv * val, a0 = val - a1;
-                        const int rr = r.v_box + base + (int)udr, c0 = r.u_box + uo + (cc.cw32 >> 5);
-                        fp_tap(img, nu, nv, rr, c0, cc.gu * a0);
-                        fp_tap(img, nu, nv, rr, c0 + 1, cc.fu * a0);
-                        fp_tap(img, nu, nv, rr + 1, c0, cc.gu * a1);
-                        fp_tap(img, nu, nv, rr + 1, c0 + 1, cc.fu * a1);
+                    for (int p = 0; p < 16; ++p) {
+                        const FpPair pr = pairs[p];
+                        const FpTaps t = fp_taps(pr, x2[p], fl2, tb);
+                        fp_add4<kPlane>(wl + t.ra * kPlane + pr.cw.x, t.gu.x, t.fu.x, t.a0.x, t.a1.x);
+                        fp_add4<kPlane>(wl + t.rb * kPlane + pr.cw.y, t.gu.y, t.fu.y, t.a0.y, t.a1.y);
                     }
-                }
-            }
-            __syncwarp();
-            if (!fits) continue;   // uniform: nothing went to the windows
-
-            // Flush: lane (g, cl) reads window it * G + g, column c0 + cl, and adds
-            // its rows to the projection (windows overlap in rows; the global
-            // reductions sum them).
-            const int g = lane / cwid, cl = lane - g * cwid;
-            // the window bases are monotone in the lane: the end lanes bound the rows
-            const int bf = __shfl_sync(0xffffffffu, base, 0), bl31 = __shfl_sync(0xffffffffu, base, 31);
-            const bool rows_in = r.v_box + min(bf, bl31) >= 0 && r.v_box + max(bf, bl31) + kFpWinRows - 1 < nv;
-            const int nit = (32 + G - 1) / G;
-            for (int c0 = 0; c0 < cols_used; c0 += cwid) {
-                const int cidx = c0 + cl;
-                const int gc = r.u_box + uo + cidx;
-                const bool live = g < G && cidx < cols_used && gc >= 0 && gc < nu;
-                const float *wcol = win + (live ? cidx : 0) * 32;
-                const int cG = cidx * G;
-                float *gcol = img + (live ? gc : 0);
-                // all rows inside the detector (the common case): no row checks,
-                // and zero cells are added too (cheaper than testing them)
-                auto pass = [&](bool checked) {
-                    for (int it = 0; it < nit; ++it) {
-                        const int l = it * G + g;
-                        const int bl = __shfl_sync(0xffffffffu, base, l & 31);
-                        const bool lok = live && l < 32;
-                        const int slot = (l + cG) & 31;
-                        const float e0 = wcol[slot], e1 = wcol[rstride + slot], e2 = wcol[2 * rstride + slot];
-                        const int row = r.v_box + bl;
-                        float *d = gcol + (long long)row * nu;
-                        if (!checked) {
-                            if (lok) {
-                                atomicAdd(d, e0);
-                                atomicAdd(d + nu, e1);
-                                atomicAdd(d + 2 * nu, e2);
-                            }
-                        } else {
-                            if (lok && e0 != 0.0f && (unsigned)row < (unsigned)nv) atomicAdd(d, e0);
-                            if (lok && e1 != 0.0f && (unsigned)(row + 1) < (unsigned)nv) atomicAdd(d + nu, e1);
-                            if (lok && e2 != 0.0f && (unsigned)(row + 2) < (unsigned)nv) atomicAdd(d + 2 * nu, e2);
+                } else {
+                    unsigned dmax = 0;
+#pragma unroll
+                    for (int p = 0; p < 16; ++p) {
+                        const FpPair pr = pairs[p];
+                        FpTaps t = fp_taps(pr, x2[p], fl2, tb);
+                        dmax = max(dmax, max((unsigned)t.ra, (unsigned)t.rb));
+                        const bool ina = (unsigned)t.ra <= (unsigned)(kFpWinRows - 2);
+                        const bool inb = (unsigned)t.rb <= (unsigned)(kFpWinRows - 2);
+                        // beyond the window: zeros here, the pass below adds them
+                        fp_add4<kPlane>(wl + (ina ? t.ra : 0) * kPlane + pr.cw.x, t.gu.x, t.fu.x,
+                                        ina ? t.a0.x : 0.0f, ina ? t.a1.x : 0.0f);
+                        fp_add4<kPlane>(wl + (inb ? t.rb : 0) * kPlane + pr.cw.y, t.gu.y, t.fu.y,
+                                        inb ? t.a0.y : 0.0f, inb ? t.a1.y : 0.0f);
+                    }
+                    if (__any_sync(0xffffffffu, lane < ez && dmax > (unsigned)(kFpWinRows - 2))) {
+#pragma unroll
+                        for (int p = 0; p < 16; ++p) {
+                            const FpPair pr = pairs[p];
+                            const FpTaps t = fp_taps(pr, x2[p], fl2, tb);
+                            fp_direct(img, nu, nv, row0, ucol0 + pr.pad.x, t.gu.x, t.fu.x, t.a0.x, t.a1.x, t.ra, false);
+                            fp_direct(img, nu, nv, row0, ucol0 + pr.pad.y, t.gu.y, t.fu.y, t.a0.y, t.a1.y, t.rb, false);
                         }
                     }
-                };
-                if (rows_in)
-                    pass(false);
-                else
-                    pass(true);
+                }
+                __syncwarp();
+                fp_flush<kPlane>(win, img, nu, nv, cw, cols_used, base, row0 - base, ucol0, lane);
+                __syncwarp();
+                // clear the cells the scatter used, for the next view
+                const int used = (cw * kFpColPitch + 3) & ~3;
+#pragma unroll
+                for (int dr = 0; dr < kFpWinRows; ++dr)
+                    for (int t = 4 * lane; t < used; t += 128)
+                        *reinterpret_cast<float4 *>(win + dr * kPlane + t) = make_float4(0.f, 0.f, 0.f, 0.f);
+            } else {
+                // a patch wider than the planned windows (not expected from the
+                // plan's footprint bound): every tap straight to the projection
+#pragma unroll
+                for (int p = 0; p < 16; ++p) {
+                    const FpPair pr = pairs[p];
+                    const FpTaps t = fp_taps(pr, x2[p], fl2, tb);
+                    fp_direct(img, nu, nv, row0, ucol0 + pr.pad.x, t.gu.x, t.fu.x, t.a0.x, t.a1.x, t.ra, true);
+                    fp_direct(img, nu, nv, row0, ucol0 + pr.pad.y, t.gu.y, t.fu.y, t.a0.y, t.a1.y, t.rb, true);
+                }
             }
-            __syncwarp();
-            // clear the columns the scatter used, for the next view
-            for (int dr = 0; dr < kFpWinRows; ++dr)
-                for (int t = 4 * lane; t < cols_used * 32; t += 128)
-                    *reinterpret_cast<float4 *>(win + dr * rstride + t) = make_float4(0.f, 0.f, 0.f, 0.f);
+            __syncwarp();   // the pair records are rewritten for the next view
         }
     }
 }
@@ -333,15 +417,24 @@ bp_status launch_forward(bp_ctx *ctx, const float *vol, float *proj, int batch, 
     // with TK=64 plans the box is at least as large, so it still covers.
     const int bu = ctx->plan.bu, bv = ctx->plan.bv, wc = ctx->plan.fp_wbu;
     const int smem = fp_smem_bytes(wc);
-    e = cudaFuncSetAttribute(fp_zcol<kFpTK>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "fp_zcol attribute");
     dim3 grid(((ctx->nx + kFpTX - 1) / kFpTX) * ((ctx->ny + kFpTY - 1) / kFpTY),
               (ctx->nz + kFpTK - 1) / kFpTK, batch);
-    fp_zcol<kFpTK><<<grid, kFpThreads, smem, st>>>(vol, ctx->d_P, ctx->n_views, ctx->nu, ctx->nv,
-                                                  ctx->nx, ctx->ny, ctx->nz, bu, bv, wc, scale, proj,
-                                                  ctx->d_err);
-    e = cudaGetLastError();
-    return e == cudaSuccess ? BP_OK : cuda_fail(ctx, e, "fp_zcol launch");
+    auto run = [&](auto kern) -> cudaError_t {
+        cudaError_t e2 = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e2 != cudaSuccess) return e2;
+        kern<<<grid, kFpThreads, smem, st>>>(vol, ctx->d_P, ctx->n_views, ctx->nu, ctx->nv, ctx->nx, ctx->ny,
+                                            ctx->nz, bu, bv, scale, proj, ctx->d_err);
+        return cudaGetLastError();
+    };
+    switch (wc) {
+    case 17: e = run(fp_zwin<17>); break;
+    case 21: e = run(fp_zwin<21>); break;
+    case 25: e = run(fp_zwin<25>); break;
+    case 33: e = run(fp_zwin<33>); break;
+    case 49: e = run(fp_zwin<49>); break;
+    default: return fail(ctx, BP_ERR_UNSUPPORTED, "fp_project: no window width for this plan");
+    }
+    return e == cudaSuccess ? BP_OK : cuda_fail(ctx, e, "fp_zwin launch");
 }
 
 }  // namespace bp
