@@ -232,8 +232,12 @@ bp_status bp_device_status(bp_ctx *ctx, void *stream);
  *   bp_get_plan        the launch plan: voxels per thread along z, the
  *                      staged box (FP32 width, FP16 width, rows; a width of
  *                      -1 means that element type uses direct global loads),
- *                      the pipeline depth in use and whether FP32 calls use
- *                      the mid-plane symmetry. Any pointer may be NULL.
+ *                      the pipeline depth in use, whether FP32 calls use
+ *                      the mid-plane symmetry, and the depth FP16 calls use
+ *                      (an FP16 stage also holds the box's shifted pair copy:
+ *                      without an explicit bp_set_pipeline_depth, FP16 runs
+ *                      fewer stages where two CTAs would not fit an SM).
+ *                      Any pointer may be NULL.
  */
 bp_status bp_set_tuning(bp_ctx *ctx, int tk, int ctas_per_sm);
 bp_status bp_set_pipeline_depth(bp_ctx *ctx, int stages);
@@ -242,7 +246,7 @@ bp_status bp_set_timeout(bp_ctx *ctx, double seconds);
 bp_status bp_test_drop_view(bp_ctx *ctx, int view);
 int bp_test_live_allocations(void);
 bp_status bp_get_plan(const bp_ctx *ctx, int *tk, int *bu32, int *bu16, int *bv, int *stages,
-                      int *symmetric);
+                      int *symmetric, int *stages16);
 
 /* Message of the last failed call on ctx (never NULL; "" after success).
  * With ctx == NULL: the last failure of bp_create* in this thread. */

@@ -51,6 +51,7 @@ struct Plan {
     int bu, bv;              // staged detector box (columns, rows), per dtype below
     int bu16;                // box width for FP16 (multiple of 8)
     int stages;              // pipeline depth (views in flight), <= the requested depth
+    int stages16;            // the same for FP16 projections (their stages also hold a pair copy)
     int sym_bu, sym_bv;      // mid-plane symmetry kernel: staged box (16-voxel half columns), -1 if off
     int ctas;                // CTAs per SM the TK=32 kernel's register budget targets (2 or 3)
     int fp_wbu;              // forward projector: window width in columns (8 x 4 column patch), -1 if unusable
@@ -71,6 +72,7 @@ struct bp_ctx {
     unsigned *d_err = nullptr;  // device error word
     // ramp filter
     int stages_req = 4;         // requested back-projector pipeline depth (bp_set_pipeline_depth)
+    bool stages_set = false;    // the depth was set explicitly (else FP16 may run fewer stages)
     int sym_enable = 1;         // mid-plane symmetry allowed (bp_set_symmetry; used when the matrices have it)
     int fft_n = 0, fft_log2 = 0;
     float *d_H = nullptr;       // [fft_n] real spectrum (times dp, times 1/N), natural order

@@ -37,9 +37,19 @@ __host__ __device__ constexpr int stage_bytes(int bu, int bv) {
     return align_up(bu * bv * (int)sizeof(T), 128);
 }
 
+// FP16 stages hold the TMA box A (rows of BU halves) and, 32 bytes past its
+// 128-byte-rounded end, a copy B shifted by one half: word m of a B row is
+// (half 2m+1, half 2m+2) of the A row, so the horizontal tap pair (c, c+1) of
+// any column is one aligned 32-bit word, of A for even c and of B for odd c.
+template <typename T>
+__host__ __device__ constexpr int stage_stride(int bu, int bv) {
+    return sizeof(T) == 2 ? 2 * stage_bytes<T>(bu, bv) + 128 : stage_bytes<T>(bu, bv);
+}
+constexpr int kPairShiftBytes = 32;   // B starts 8 banks after A's rounded end
+
 constexpr int kRecBytes = kRecChunk * (int)sizeof(ViewRec);
 constexpr int kBarOffset = kRecBytes;
-constexpr int kStageOffset = align_up(kRecBytes + 2 * kMaxStages * 8, 128);
+constexpr int kStageOffset = align_up(kRecBytes + 3 * kMaxStages * 8, 128);   // full, empty, ready
 
 // Thread -> column within the CTA tile: each warp owns an 8 x 4 patch.
 __device__ __forceinline__ void consumer_column(int warp, int lane, int *di, int *dj) {
@@ -156,6 +166,77 @@ __device__ __forceinline__ void accumulate_pairs(const float *__restrict__ tile,
         const f2 S1 = fma2(FU, sub2(Q11, Q10), Q10);
         const f2 VAL = fma2(FV, sub2(S1, S0), S0);
         acc2[m] = fma2(WT, VAL, acc2[m]);
+    }
+}
+
+// FP16 taps as horizontal pairs: W points at the stage's A words (even cu)
+// or B words (odd cu) of the column's staged box column cu / 2; a row is
+// BU / 2 words. Per voxel two 32-bit shared loads give q00, q01 and q10,
+// q11; the arithmetic after the conversion is that of accumulate_pairs.
+__device__ __forceinline__ float h_lo(unsigned w) { return __half2float(__ushort_as_half((unsigned short)(w & 0xffffu))); }
+__device__ __forceinline__ float h_hi(unsigned w) { return __half2float(__ushort_as_half((unsigned short)(w >> 16))); }
+
+template <int TK, int BU>
+__device__ __forceinline__ void accumulate_h2_pairs(const unsigned *__restrict__ W, const ColView &c, f2 *acc2) {
+    constexpr int RW = BU / 2;
+    const float2 M2 = make_float2(kMagic, kMagic), NM2 = make_float2(-kMagic, -kMagic);
+    const float2 FU = make_float2(c.fu, c.fu), WT = make_float2(c.wt, c.wt);
+    const float2 DV2 = make_float2(c.dv, c.dv), V02 = make_float2(c.v0, c.v0);
+#pragma unroll
+    for (int m = 0; m < TK / 2; ++m) {
+        const float2 V = __ffma2_rn(make_float2((float)(2 * m), (float)(2 * m + 1)), DV2, V02);
+        const float2 TV = __fadd2_rd(V, M2);
+        const float2 FL = __fadd2_rn(TV, NM2);
+        const float2 FV = __fadd2_rn(V, make_float2(-FL.x, -FL.y));
+        const int ra = __float_as_int(TV.x) - kMagicBits, rb = __float_as_int(TV.y) - kMagicBits;
+        const unsigned *pa = W + ra * RW, *pb = W + rb * RW;
+        const unsigned a0 = pa[0], a1 = pa[RW], b0 = pb[0], b1 = pb[RW];
+        const float2 Q00 = make_float2(h_lo(a0), h_lo(b0)), Q01 = make_float2(h_hi(a0), h_hi(b0));
+        const float2 Q10 = make_float2(h_lo(a1), h_lo(b1)), Q11 = make_float2(h_hi(a1), h_hi(b1));
+        const float2 S0 = __ffma2_rn(FU, __fadd2_rn(Q01, make_float2(-Q00.x, -Q00.y)), Q00);
+        const float2 S1 = __ffma2_rn(FU, __fadd2_rn(Q11, make_float2(-Q10.x, -Q10.y)), Q10);
+        float2 a;
+        upk(acc2[m], a.x, a.y);
+        a = __ffma2_rn(WT, __ffma2_rn(FV, __fadd2_rn(S1, make_float2(-S0.x, -S0.y)), S0), a);
+        acc2[m] = pk(a.x, a.y);
+    }
+}
+
+template <int TK, int BU>
+__device__ __forceinline__ void accumulate_h2_scalar(const unsigned *__restrict__ W, const ColView &c, int ez,
+                                                     float *acc) {
+    constexpr int RW = BU / 2;
+#pragma unroll
+    for (int kk = 0; kk < TK; ++kk) {
+        if (kk >= ez) continue;
+        float v = fmaf((float)kk, c.dv, c.v0);
+        float tv = __fadd_rd(v, kMagic);
+        float fv = v - (tv - kMagic);
+        const unsigned *p = W + (__float_as_int(tv) - kMagicBits) * RW;
+        const unsigned w0 = p[0], w1 = p[RW];
+        float q00 = h_lo(w0), q01 = h_hi(w0), q10 = h_lo(w1), q11 = h_hi(w1);
+        float s0 = fmaf(c.fu, q01 - q00, q00);
+        float s1 = fmaf(c.fu, q11 - q10, q10);
+        float val = fmaf(fv, s1 - s0, s0);
+        acc[kk] = fmaf(c.wt, val, acc[kk]);
+    }
+}
+
+// The producer warp's step after an FP16 box has landed: write its shifted
+// copy B (four words per lane and pass; the last word of a row takes the
+// first half of the next row, which no tap reads).
+__device__ __forceinline__ void make_pair_copy(unsigned char *stage, int a_bytes, int words, int lane) {
+    const unsigned *A = reinterpret_cast<const unsigned *>(stage);
+    unsigned *B = reinterpret_cast<unsigned *>(stage + a_bytes + kPairShiftBytes);
+    for (int t = 4 * lane; t < words; t += 128) {
+        const uint4 a = *reinterpret_cast<const uint4 *>(A + t);
+        const unsigned nx = (t + 4 < words) ? A[t + 4] : 0u;
+        uint4 o;
+        o.x = __byte_perm(a.x, a.y, 0x5432);
+        o.y = __byte_perm(a.y, a.z, 0x5432);
+        o.z = __byte_perm(a.z, a.w, 0x5432);
+        o.w = __byte_perm(a.w, nx, 0x5432);
+        *reinterpret_cast<uint4 *>(B + t) = o;
     }
 }
 
@@ -284,9 +365,12 @@ bp_zcol_tma(const __grid_constant__ CUtensorMap tmap, const double *__restrict__
     ViewRec *recs = reinterpret_cast<ViewRec *>(smem);
     unsigned long long *full = reinterpret_cast<unsigned long long *>(smem + kBarOffset);
     unsigned long long *empty = full + kMaxStages;
+    unsigned long long *ready = empty + kMaxStages;   // FP16: the pair copy of a stage is written
     unsigned char *stages = smem + kStageOffset;
-    const int sbytes = stage_bytes<T>(BU, bv);
+    constexpr bool kH2 = sizeof(T) == 2;
+    const int sbytes = stage_stride<T>(BU, bv);
     const unsigned box_bytes = (unsigned)(BU * bv * sizeof(T));
+    const int a_bytes = stage_bytes<T>(BU, bv);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int ntx = (nx + kTX - 1) / kTX;
@@ -304,28 +388,25 @@ bp_zcol_tma(const __grid_constant__ CUtensorMap tmap, const double *__restrict__
         for (int s = 0; s < nst; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], kConsumerWarps);
+            mbar_init(&ready[s], 32);
         }
         fence_barrier_init();
         prefetch_tmap(&tmap);
     }
     __syncthreads();
 
-    // accumulators: FP32 pairs (kk, kk+1) for FP32 taps, scalars otherwise
-    constexpr bool kPairs = sizeof(T) == 4;
+    // accumulators: FP32 pairs (kk, kk+1)
     f2 acc2[TK / 2];
-    float acc[kPairs ? 1 : TK];
 #pragma unroll
     for (int m = 0; m < TK / 2; ++m) acc2[m] = 0ull;
-#pragma unroll
-    for (int kk = 0; kk < (kPairs ? 1 : TK); ++kk) acc[kk] = 0.0f;
 
     __shared__ unsigned arms[kMaxStages];   // producer: armings of each full barrier
     if (tid < kMaxStages) arms[tid] = 0;
     bool alive = true;
     // pipeline position of the current view g: slot g % nst, phase (g / nst) & 1,
     // advanced per view (no division)
-    int slot = 0;
-    unsigned phase = 0, g = 0;
+    int slot = 0, cslot = 0;   // cslot, cphase: the FP16 producer's pair-copy position
+    unsigned phase = 0, g = 0, cphase = 0;
     for (int cb = 0; cb < nviews; cb += kRecChunk) {
         const int cn = min(kRecChunk, nviews - cb);
         __syncthreads();
@@ -335,38 +416,98 @@ bp_zcol_tma(const __grid_constant__ CUtensorMap tmap, const double *__restrict__
                 atomicOr(err, DEV_ERR_FOOTPRINT);
         __syncthreads();
         if (warp == kConsumerWarps) {
-            // ---- producer: one elected lane issues the TMA loads ----
-            if (lane == 0 && alive) {
-                for (int n = 0; n < cn; ++n, ++g) {
-                    if (g >= (unsigned)nst && !mbar_wait_bounded(&empty[slot], phase ^ 1u, timeout_ns)) {
-                        atomicOr(err, DEV_ERR_TIMEOUT);
-                        alive = false;
-                        break;
+            if constexpr (!kH2) {
+                // ---- producer: one elected lane issues the TMA loads ----
+                if (lane == 0 && alive) {
+                    for (int n = 0; n < cn; ++n, ++g) {
+                        if (g >= (unsigned)nst && !mbar_wait_bounded(&empty[slot], phase ^ 1u, timeout_ns)) {
+                            atomicOr(err, DEV_ERR_TIMEOUT);
+                            alive = false;
+                            break;
+                        }
+                        if (view0 + cb + n != drop_view) {   // test hook: skip this view's load
+                            mbar_arrive_expect_tx(&full[slot], box_bytes);
+                            tma_load_4d(stages + slot * sbytes, &tmap, recs[n].u_box, recs[n].v_box,
+                                        cb + n, b, &full[slot]);
+                            ++arms[slot];
+                        }
+                        if (++slot == nst) {
+                            slot = 0;
+                            phase ^= 1u;
+                        }
                     }
-                    if (view0 + cb + n != drop_view) {   // test hook: skip this view's load
-                        mbar_arrive_expect_tx(&full[slot], box_bytes);
-                        tma_load_4d(stages + slot * sbytes, &tmap, recs[n].u_box, recs[n].v_box,
-                                    cb + n, b, &full[slot]);
-                        ++arms[slot];
+                }
+            } else {
+                // ---- producer (FP16): lane 0 issues the loads; the whole warp
+                // writes each landed box's shifted pair copy, nst - 1 views behind
+                // the issue so that loads stay in flight ----
+                const int lag = nst - 1;
+                for (int n = 0; n < cn + lag && alive; ++n) {
+                    if (n < cn) {
+                        bool ok = true;
+                        if (lane == 0) {
+                            if (g >= (unsigned)nst && !mbar_wait_bounded(&empty[slot], phase ^ 1u, timeout_ns)) {
+                                atomicOr(err, DEV_ERR_TIMEOUT);
+                                ok = false;
+                            } else if (view0 + cb + n != drop_view) {   // test hook: skip this view's load
+                                mbar_arrive_expect_tx(&full[slot], box_bytes);
+                                tma_load_4d(stages + slot * sbytes, &tmap, recs[n].u_box, recs[n].v_box,
+                                            cb + n, b, &full[slot]);
+                                ++arms[slot];
+                            }
+                        }
+                        if (!__shfl_sync(0xffffffffu, ok, 0)) {
+                            alive = false;
+                            break;
+                        }
+                        ++g;
+                        if (++slot == nst) {
+                            slot = 0;
+                            phase ^= 1u;
+                        }
                     }
-                    if (++slot == nst) {
-                        slot = 0;
-                        phase ^= 1u;
+                    if (n >= lag) {
+                        if (!__all_sync(0xffffffffu, mbar_wait_bounded(&full[cslot], cphase, timeout_ns))) {
+                            if (lane == 0) atomicOr(err, DEV_ERR_TIMEOUT);
+                            alive = false;
+                            break;
+                        }
+                        make_pair_copy(stages + cslot * sbytes, a_bytes, BU * bv / 2, lane);
+                        mbar_arrive(&ready[cslot]);
+                        if (++cslot == nst) {
+                            cslot = 0;
+                            cphase ^= 1u;
+                        }
                     }
                 }
             }
         } else {
             // ---- consumers ----
             for (int n = 0; n < cn && alive; ++n) {
-                if (!mbar_wait_bounded(&full[slot], phase, timeout_ns)) {
+                // the whole warp agrees on the outcome of the bounded wait
+                if (!__all_sync(0xffffffffu, mbar_wait_bounded(kH2 ? &ready[slot] : &full[slot], phase, timeout_ns))) {
                     if (lane == 0) atomicOr(err, DEV_ERR_TIMEOUT);
                     alive = false;
                     break;
                 }
                 ColView cv;
                 if (col_ok && column_view<BU>(recs[n], fdi, fdj, ez, bv, err, cv)) {
-                    const T *tile = reinterpret_cast<const T *>(stages + slot * sbytes);
-                    if constexpr (kPairs) {
+                    if constexpr (kH2) {
+                        // the pair word of column cu: A for even cu, the shifted copy B for odd
+                        const unsigned char *st = stages + slot * sbytes + ((cv.cu & 1) ? a_bytes + kPairShiftBytes : 0);
+                        const unsigned *W = reinterpret_cast<const unsigned *>(st) + (cv.cu >> 1);
+                        if (ez == TK) {
+                            accumulate_h2_pairs<TK, BU>(W, cv, acc2);
+                        } else {
+                            float tmp[TK];
+#pragma unroll
+                            for (int m = 0; m < TK / 2; ++m) upk(acc2[m], tmp[2 * m], tmp[2 * m + 1]);
+                            accumulate_h2_scalar<TK, BU>(W, cv, ez, tmp);
+#pragma unroll
+                            for (int m = 0; m < TK / 2; ++m) acc2[m] = pk(tmp[2 * m], tmp[2 * m + 1]);
+                        }
+                    } else {
+                        const T *tile = reinterpret_cast<const T *>(stages + slot * sbytes);
                         if (ez == TK) {
                             accumulate_pairs<TK, BU>(tile, cv, acc2);
                         } else {
@@ -377,11 +518,6 @@ bp_zcol_tma(const __grid_constant__ CUtensorMap tmap, const double *__restrict__
 #pragma unroll
                             for (int m = 0; m < TK / 2; ++m) acc2[m] = pk(tmp[2 * m], tmp[2 * m + 1]);
                         }
-                    } else {
-                        if (ez == TK)
-                            accumulate_scalar<T, TK, BU, true>(tile, cv, ez, acc);
-                        else
-                            accumulate_scalar<T, TK, BU, false>(tile, cv, ez, acc);
                     }
                 }
                 __syncwarp();
@@ -400,14 +536,10 @@ bp_zcol_tma(const __grid_constant__ CUtensorMap tmap, const double *__restrict__
                 atomicOr(err, DEV_ERR_TIMEOUT);
     }
     if (col_ok && alive) {
-        if constexpr (kPairs) {
-            float out[TK];
+        float out[TK];
 #pragma unroll
-            for (int m = 0; m < TK / 2; ++m) upk(acc2[m], out[2 * m], out[2 * m + 1]);
-            store_column<TK>(vol, out, b, i0 + di, j0 + dj, k0, ez, nx, ny, nz, scale, accumulate);
-        } else {
-            store_column<TK>(vol, acc, b, i0 + di, j0 + dj, k0, ez, nx, ny, nz, scale, accumulate);
-        }
+        for (int m = 0; m < TK / 2; ++m) upk(acc2[m], out[2 * m], out[2 * m + 1]);
+        store_column<TK>(vol, out, b, i0 + di, j0 + dj, k0, ez, nx, ny, nz, scale, accumulate);
     }
 }
 
@@ -492,7 +624,8 @@ bp_zsym_tma(const __grid_constant__ CUtensorMap tmap, const double *__restrict__
             }
         } else {
             for (int n = 0; n < cn && alive; ++n) {
-                if (!mbar_wait_bounded(&full[slot], phase, timeout_ns)) {
+                // the whole warp agrees on the outcome of the bounded wait
+                if (!__all_sync(0xffffffffu, mbar_wait_bounded(&full[slot], phase, timeout_ns))) {
                     if (lane == 0) atomicOr(err, DEV_ERR_TIMEOUT);
                     alive = false;
                     break;
@@ -717,8 +850,8 @@ template <typename T, int TK, int BU, int MB>
 static cudaError_t launch_tma_t(const CUtensorMap &map, bp_ctx *ctx, int view0, int nviews,
                                 int bv, int align, float *vol, int batch, float scale,
                                 int accumulate, cudaStream_t st, int kz0, int kz1) {
-    const int nst = ctx->plan.stages;
-    const int smem = kStageOffset + nst * stage_bytes<T>(BU, bv);
+    const int nst = sizeof(T) == 2 ? ctx->plan.stages16 : ctx->plan.stages;
+    const int smem = kStageOffset + nst * stage_stride<T>(BU, bv);
     auto kern = bp_zcol_tma<T, TK, BU, MB>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;

@@ -51,9 +51,8 @@ struct FpWin {
 struct __align__(16) FpPair {
     float2 v0, dv;   // v of the first voxel and per voxel (box-relative)
     float2 wt, fu;   // 1 / W^2 (0: a column without voxels), u fraction
-    int2 cw;         // window column * 33
-    int2 pad;
 };
+// beside it, per pair: the window columns times 33 (int2)
 
 // Window widths the kernel is built for (odd; the plan takes the smallest
 // that holds the widest u footprint of a patch).
@@ -68,7 +67,7 @@ int fp_window_width(int need) {
 static int fp_plane_words(int wc) { return (wc * kFpColPitch + 31) / 32 * 32; }
 
 int fp_smem_bytes(int wc) {
-    return kFpRecChunk * (int)sizeof(ViewRec) + (kFpThreads / 32) * 16 * (int)sizeof(FpPair) +
+    return kFpRecChunk * (int)sizeof(ViewRec) + (kFpThreads / 32) * 16 * (int)(sizeof(FpPair) + sizeof(int2)) +
            (kFpThreads / 32) * kFpWinRows * fp_plane_words(wc) * (int)sizeof(float);
 }
 
@@ -197,8 +196,10 @@ fp_zwin(const float *__restrict__ vol, const double *__restrict__ P, int nviews,
     ViewRec *recs = reinterpret_cast<ViewRec *>(smem);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     FpPair *pairs = reinterpret_cast<FpPair *>(smem + kFpRecChunk * sizeof(ViewRec)) + warp * 16;
+    int2 *pcw = reinterpret_cast<int2 *>(smem + kFpRecChunk * sizeof(ViewRec) + (kFpThreads / 32) * 16 * sizeof(FpPair)) +
+                warp * 16;
     float *win = reinterpret_cast<float *>(smem + kFpRecChunk * sizeof(ViewRec) +
-                                           (kFpThreads / 32) * 16 * sizeof(FpPair)) +
+                                           (kFpThreads / 32) * 16 * (sizeof(FpPair) + sizeof(int2))) +
                  warp * kWarpWords;
 
     const int ntx = (nx + kFpTX - 1) / kFpTX;
@@ -277,8 +278,7 @@ fp_zwin(const float *__restrict__ vol, const double *__restrict__ P, int nviews,
             pf[2] = cok ? cdv : dvmin;
             pf[4] = cok ? cwt : 0.0f;
             pf[6] = cok ? cfu : 0.0f;
-            reinterpret_cast<int *>(pf)[8] = cwin * kFpColPitch;
-            reinterpret_cast<int *>(pf)[10] = cwin;
+            reinterpret_cast<int *>(pcw)[lane] = cwin * kFpColPitch;
             __syncwarp();
 
             // Lane l's window starts at row floor(v0min + l * dvmin): every
@@ -299,32 +299,35 @@ fp_zwin(const float *__restrict__ vol, const double *__restrict__ P, int nviews,
 #pragma unroll
                     for (int p = 0; p < 16; ++p) {
                         const FpPair pr = pairs[p];
+                        const int2 cw2 = pcw[p];
                         const FpTaps t = fp_taps(pr, x2[p], fl2, tb);
-                        fp_add4<kPlane>(wl + t.ra * kPlane + pr.cw.x, t.gu.x, t.fu.x, t.a0.x, t.a1.x);
-                        fp_add4<kPlane>(wl + t.rb * kPlane + pr.cw.y, t.gu.y, t.fu.y, t.a0.y, t.a1.y);
+                        fp_add4<kPlane>(wl + t.ra * kPlane + cw2.x, t.gu.x, t.fu.x, t.a0.x, t.a1.x);
+                        fp_add4<kPlane>(wl + t.rb * kPlane + cw2.y, t.gu.y, t.fu.y, t.a0.y, t.a1.y);
                     }
                 } else {
                     unsigned dmax = 0;
 #pragma unroll
                     for (int p = 0; p < 16; ++p) {
                         const FpPair pr = pairs[p];
+                        const int2 cw2 = pcw[p];
                         FpTaps t = fp_taps(pr, x2[p], fl2, tb);
                         dmax = max(dmax, max((unsigned)t.ra, (unsigned)t.rb));
                         const bool ina = (unsigned)t.ra <= (unsigned)(kFpWinRows - 2);
                         const bool inb = (unsigned)t.rb <= (unsigned)(kFpWinRows - 2);
                         // beyond the window: zeros here, the pass below adds them
-                        fp_add4<kPlane>(wl + (ina ? t.ra : 0) * kPlane + pr.cw.x, t.gu.x, t.fu.x,
+                        fp_add4<kPlane>(wl + (ina ? t.ra : 0) * kPlane + cw2.x, t.gu.x, t.fu.x,
                                         ina ? t.a0.x : 0.0f, ina ? t.a1.x : 0.0f);
-                        fp_add4<kPlane>(wl + (inb ? t.rb : 0) * kPlane + pr.cw.y, t.gu.y, t.fu.y,
+                        fp_add4<kPlane>(wl + (inb ? t.rb : 0) * kPlane + cw2.y, t.gu.y, t.fu.y,
                                         inb ? t.a0.y : 0.0f, inb ? t.a1.y : 0.0f);
                     }
                     if (__any_sync(0xffffffffu, lane < ez && dmax > (unsigned)(kFpWinRows - 2))) {
 #pragma unroll
                         for (int p = 0; p < 16; ++p) {
                             const FpPair pr = pairs[p];
+                            const int2 cw2 = pcw[p];
                             const FpTaps t = fp_taps(pr, x2[p], fl2, tb);
-                            fp_direct(img, nu, nv, row0, ucol0 + pr.pad.x, t.gu.x, t.fu.x, t.a0.x, t.a1.x, t.ra, false);
-                            fp_direct(img, nu, nv, row0, ucol0 + pr.pad.y, t.gu.y, t.fu.y, t.a0.y, t.a1.y, t.rb, false);
+                            fp_direct(img, nu, nv, row0, ucol0 + cw2.x / kFpColPitch, t.gu.x, t.fu.x, t.a0.x, t.a1.x, t.ra, false);
+                            fp_direct(img, nu, nv, row0, ucol0 + cw2.y / kFpColPitch, t.gu.y, t.fu.y, t.a0.y, t.a1.y, t.rb, false);
                         }
                     }
                 }
@@ -343,9 +346,10 @@ fp_zwin(const float *__restrict__ vol, const double *__restrict__ P, int nviews,
 #pragma unroll
                 for (int p = 0; p < 16; ++p) {
                     const FpPair pr = pairs[p];
+                    const int2 cw2 = pcw[p];
                     const FpTaps t = fp_taps(pr, x2[p], fl2, tb);
-                    fp_direct(img, nu, nv, row0, ucol0 + pr.pad.x, t.gu.x, t.fu.x, t.a0.x, t.a1.x, t.ra, true);
-                    fp_direct(img, nu, nv, row0, ucol0 + pr.pad.y, t.gu.y, t.fu.y, t.a0.y, t.a1.y, t.rb, true);
+                    fp_direct(img, nu, nv, row0, ucol0 + cw2.x / kFpColPitch, t.gu.x, t.fu.x, t.a0.x, t.a1.x, t.ra, true);
+                    fp_direct(img, nu, nv, row0, ucol0 + cw2.y / kFpColPitch, t.gu.y, t.fu.y, t.a0.y, t.a1.y, t.rb, true);
                 }
             }
             __syncwarp();   // the pair records are rewritten for the next view
