@@ -208,10 +208,10 @@ bp_status bp_device_status(bp_ctx *ctx, void *stream);
  *                      least) before falling back to direct global loads. The
  *                      GPU counterpart of the paper's view batching and
  *                      prefetching depth (Section 3.1.3, Algorithm 2).
- *   bp_set_symmetry    FP32 back-projection with the mid-plane symmetry of
+ *   bp_set_symmetry    back-projection with the mid-plane symmetry of
  *                      Section 3.1.2 / Algorithm 1: a thread owns voxels k
  *                      and nz-1-k and computes v, its floor and fraction
- *                      once for both. 1 (default): used whenever
+ *                      once for both (FP32 and FP16-stored projections). 1 (default): used whenever
  *                      v(nz-1-k) = nv-1-v(k) holds for the context's matrices
  *                      (v_off = 0, volume centred on the central plane) and
  *                      the boxes fit shared memory; asking for it explicitly
@@ -232,12 +232,11 @@ bp_status bp_device_status(bp_ctx *ctx, void *stream);
  *   bp_get_plan        the launch plan: voxels per thread along z, the
  *                      staged box (FP32 width, FP16 width, rows; a width of
  *                      -1 means that element type uses direct global loads),
- *                      the pipeline depth in use, whether FP32 calls use
- *                      the mid-plane symmetry, and the depth FP16 calls use
- *                      (an FP16 stage also holds the box's shifted pair copy:
- *                      without an explicit bp_set_pipeline_depth, FP16 runs
- *                      fewer stages where two CTAs would not fit an SM).
- *                      Any pointer may be NULL.
+ *                      the pipeline depth in use and which calls use the
+ *                      mid-plane symmetry (bit 0: FP32 projections, bit 1:
+ *                      FP16-stored projections, whose boxes the kernel
+ *                      widens to FP32 in shared memory). Any pointer may be
+ *                      NULL.
  */
 bp_status bp_set_tuning(bp_ctx *ctx, int tk, int ctas_per_sm);
 bp_status bp_set_pipeline_depth(bp_ctx *ctx, int stages);
@@ -246,7 +245,7 @@ bp_status bp_set_timeout(bp_ctx *ctx, double seconds);
 bp_status bp_test_drop_view(bp_ctx *ctx, int view);
 int bp_test_live_allocations(void);
 bp_status bp_get_plan(const bp_ctx *ctx, int *tk, int *bu32, int *bu16, int *bv, int *stages,
-                      int *symmetric, int *stages16);
+                      int *symmetric);
 
 /* Message of the last failed call on ctx (never NULL; "" after success).
  * With ctx == NULL: the last failure of bp_create* in this thread. */

@@ -60,7 +60,7 @@ PROTOTYPES = {
     "bp_set_timeout": (_i, [_vp, _d]),
     "bp_test_drop_view": (_i, [_vp, _i]),
     "bp_test_live_allocations": (_i, []),
-    "bp_get_plan": (_i, [_vp, _iptr, _iptr, _iptr, _iptr, _iptr, _iptr, _iptr]),
+    "bp_get_plan": (_i, [_vp, _iptr, _iptr, _iptr, _iptr, _iptr, _iptr]),
     "bp_last_error": (ctypes.c_char_p, [_vp]),
     "bp_destroy": (None, [_vp]),
     # unet.h

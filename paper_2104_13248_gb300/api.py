@@ -136,10 +136,10 @@ def bp_get_matrices(ctx: Context) -> np.ndarray:
 
 
 def bp_get_plan(ctx: Context) -> dict:
-    v = [ctypes.c_int() for _ in range(7)]
+    v = [ctypes.c_int() for _ in range(6)]
     check(_lib.load().bp_get_plan(ctx.handle, *[ctypes.byref(x) for x in v]), ctx.handle)
     return dict(tk=v[0].value, bu32=v[1].value, bu16=v[2].value, bv=v[3].value, stages=v[4].value,
-                symmetric=bool(v[5].value), stages16=v[6].value)
+                symmetric=bool(v[5].value & 1), symmetric16=bool(v[5].value & 2))
 
 
 def bp_set_tuning(ctx: Context, tk: int = 32, ctas_per_sm: int = 2) -> None:

@@ -150,12 +150,10 @@ void max_footprint(const bp_ctx *ctx, int tx, int ty, int tk, int align, int *bu
 }
 
 // Shared memory of the staged back-projector: view records, 3 x 8 barrier
-// slots, then one box per stage (each rounded up to 128 bytes); an FP16
-// stage also holds the box's shifted pair copy (twice the box plus 128 bytes).
+// slots, then one box per stage (each rounded up to 128 bytes).
 static int tma_smem_bytes(int bu, int bv, int elem_bytes, int stages) {
     const int base = (256 * 48 + 3 * 8 * 8 + 127) / 128 * 128;
-    const int box = (bu * bv * elem_bytes + 127) / 128 * 128;
-    return base + stages * (elem_bytes == 2 ? 2 * box + 128 : box);
+    return base + stages * ((bu * bv * elem_bytes + 127) / 128 * 128);
 }
 
 // Mid-plane symmetry of the matrices (Section 3.1.2): v(i, j, nz-1-k) =
@@ -198,23 +196,24 @@ static void make_plan(bp_ctx *ctx) {
     pl.stages = ctx->stages_req;
     while (pl.stages > 2 && !fits(pl.bu, 4, pl.stages)) --pl.stages;
     if (pl.bv > 256 || !fits(pl.bu, 4, pl.stages)) pl.bu = -1;
-    // FP16: an explicit depth is kept while its stages fit; the default depth
-    // is lowered (to 2 at least) while two CTAs do not fit an SM, since the
-    // pair copies double an FP16 stage
-    pl.stages16 = ctx->stages_req;
-    while (pl.stages16 > 1 && !fits(pl.bu16, 2, pl.stages16)) --pl.stages16;
-    if (!ctx->stages_set)
-        while (pl.stages16 > 2 && tma_smem_bytes(pl.bu16, pl.bv, 2, pl.stages16) > 113 * 1024) --pl.stages16;
-    if (pl.bv > 256 || !fits(pl.bu16, 2, pl.stages16)) pl.bu16 = -1;
+    if (pl.bv > 256 || !fits(pl.bu16, 2, pl.stages)) pl.bu16 = -1;
     // mid-plane symmetry: boxes of 16-voxel half columns, two per stage
-    pl.sym_bu = pl.sym_bv = -1;
+    pl.sym_bu = pl.sym_bv = pl.sym16_bu = pl.sym16_bv = -1;
     if (ctx->sym_enable && pl.bu > 0 && mirror_symmetric(ctx)) {
         int sbu, sbv;
         max_footprint(ctx, pl.tx, pl.ty, 16, 4, &sbu, &sbv);
         sbu = plan_box_width(sbu, 4);
-        if (sbu > 0 && sbv <= 256 && tma_smem_bytes(sbu, sbv, 4, 2 * pl.stages) <= 227 * 1024) {
+        if (sbu > 0 && sbv <= 256 && sym_smem_bytes_host(sbu, sbv, pl.stages, 4) <= 227 * 1024) {
             pl.sym_bu = sbu;
             pl.sym_bv = sbv;
+        }
+        // FP16: boxes aligned to 8 halves (16 bytes, the TMA rule), widths from
+        // the FP32 list, since the widened boxes are read as FP32
+        max_footprint(ctx, pl.tx, pl.ty, 16, 8, &sbu, &sbv);
+        sbu = plan_box_width(sbu, 4);
+        if (sbu > 0 && sbv <= 256 && sym_smem_bytes_host(sbu, sbv, pl.stages, 2) <= 227 * 1024) {
+            pl.sym16_bu = sbu;
+            pl.sym16_bv = sbv;
         }
     }
     // forward projector: lane windows as wide as the u footprint of an 8 x 4
@@ -433,7 +432,7 @@ bp_status bp_backproject_views(bp_ctx *ctx, const void *proj, bp_dtype t, int vi
     bp_status s = check_bp_args(ctx, proj, t, view0, n_views, proj_batch_stride, vol, batch, scale);
     if (s != BP_OK) return s;
     // the whole volume: the lower half and its mirror where the symmetric kernel applies
-    const bool sym = ctx->zinv && t == BP_F32 && ctx->plan.sym_bu > 0;
+    const bool sym = ctx->zinv && (t == BP_F32 ? ctx->plan.sym_bu : ctx->plan.sym16_bu) > 0;
     return launch_backproject(ctx, proj, t, view0, n_views, proj_batch_stride, vol, batch, scale,
                               accumulate ? 1 : 0, (cudaStream_t)stream, 0, sym ? (ctx->nz + 1) / 2 : ctx->nz,
                               sym ? 1 : 0);
@@ -533,10 +532,10 @@ bp_status bp_set_pipeline_depth(bp_ctx *ctx, int stages) {
     if (stages < 1 || stages > 8)
         return fail(ctx, BP_ERR_INVALID_ARG, "bp_set_pipeline_depth: stages must be in [1, 8]");
     const Plan &pl = ctx->plan;
-    if (pl.bu > 0 && tma_smem_bytes(pl.bu, pl.bv, 4, stages) > 227 * 1024)
+    if ((pl.bu > 0 && tma_smem_bytes(pl.bu, pl.bv, 4, stages) > 227 * 1024) ||
+        (pl.bu16 > 0 && tma_smem_bytes(pl.bu16, pl.bv, 2, stages) > 227 * 1024))
         return fail(ctx, BP_ERR_INVALID_ARG, "bp_set_pipeline_depth: the staged boxes do not fit in shared memory");
     ctx->stages_req = stages;
-    ctx->stages_set = true;
     make_plan(ctx);
     return BP_OK;
 }
@@ -569,15 +568,14 @@ bp_status bp_test_drop_view(bp_ctx *ctx, int view) {
 }
 
 bp_status bp_get_plan(const bp_ctx *ctx, int *tk, int *bu32, int *bu16, int *bv, int *stages,
-                      int *symmetric, int *stages16) {
+                      int *symmetric) {
     if (!ctx) return fail(nullptr, BP_ERR_INVALID_ARG, "bp_get_plan: NULL context");
     if (tk) *tk = ctx->plan.tk;
     if (bu32) *bu32 = ctx->plan.bu;
     if (bu16) *bu16 = ctx->plan.bu16;
     if (bv) *bv = ctx->plan.bv;
     if (stages) *stages = ctx->plan.stages;
-    if (symmetric) *symmetric = ctx->plan.sym_bu > 0;
-    if (stages16) *stages16 = ctx->plan.stages16;
+    if (symmetric) *symmetric = (ctx->plan.sym_bu > 0 ? 1 : 0) | (ctx->plan.sym16_bu > 0 ? 2 : 0);
     return BP_OK;
 }
 

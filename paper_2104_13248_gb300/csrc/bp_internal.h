@@ -51,8 +51,8 @@ struct Plan {
     int bu, bv;              // staged detector box (columns, rows), per dtype below
     int bu16;                // box width for FP16 (multiple of 8)
     int stages;              // pipeline depth (views in flight), <= the requested depth
-    int stages16;            // the same for FP16 projections (their stages also hold a pair copy)
     int sym_bu, sym_bv;      // mid-plane symmetry kernel: staged box (16-voxel half columns), -1 if off
+    int sym16_bu, sym16_bv;  // the same for FP16-stored projections (boxes aligned to 8 halves)
     int ctas;                // CTAs per SM the TK=32 kernel's register budget targets (2 or 3)
     int fp_wbu;              // forward projector: window width in columns (8 x 4 column patch), -1 if unusable
 };
@@ -72,7 +72,6 @@ struct bp_ctx {
     unsigned *d_err = nullptr;  // device error word
     // ramp filter
     int stages_req = 4;         // requested back-projector pipeline depth (bp_set_pipeline_depth)
-    bool stages_set = false;    // the depth was set explicitly (else FP16 may run fewer stages)
     int sym_enable = 1;         // mid-plane symmetry allowed (bp_set_symmetry; used when the matrices have it)
     int fft_n = 0, fft_log2 = 0;
     float *d_H = nullptr;       // [fft_n] real spectrum (times dp, times 1/N), natural order
@@ -105,7 +104,8 @@ bp_status launch_forward(bp_ctx *ctx, const float *vol, float *proj, int batch, 
                          cudaStream_t st);
 // Dynamic shared memory of the forward projector for windows wc columns wide.
 int fp_smem_bytes(int wc);
-int fp_window_width(int need);   // smallest window width the forward projector is built for, or -1
+int fp_window_width(int need);
+int sym_smem_bytes_host(int bu, int bv, int nst, int elem_bytes);   // symmetric kernel's shared memory   // smallest window width the forward projector is built for, or -1
 bp_status launch_filter(bp_ctx *ctx, const float *proj, void *out, bp_dtype out_t,
                         long long n_views_total, cudaStream_t st);
 bp_status launch_phantom(bp_ctx *ctx, const double *d_ell, int n_ell, float *proj,

@@ -37,16 +37,6 @@ __host__ __device__ constexpr int stage_bytes(int bu, int bv) {
     return align_up(bu * bv * (int)sizeof(T), 128);
 }
 
-// FP16 stages hold the TMA box A (rows of BU halves) and, 32 bytes past its
-// 128-byte-rounded end, a copy B shifted by one half: word m of a B row is
-// (half 2m+1, half 2m+2) of the A row, so the horizontal tap pair (c, c+1) of
-// any column is one aligned 32-bit word, of A for even c and of B for odd c.
-template <typename T>
-__host__ __device__ constexpr int stage_stride(int bu, int bv) {
-    return sizeof(T) == 2 ? 2 * stage_bytes<T>(bu, bv) + 128 : stage_bytes<T>(bu, bv);
-}
-constexpr int kPairShiftBytes = 32;   // B starts 8 banks after A's rounded end
-
 constexpr int kRecBytes = kRecChunk * (int)sizeof(ViewRec);
 constexpr int kBarOffset = kRecBytes;
 constexpr int kStageOffset = align_up(kRecBytes + 3 * kMaxStages * 8, 128);   // full, empty, ready
@@ -166,77 +156,6 @@ __device__ __forceinline__ void accumulate_pairs(const float *__restrict__ tile,
         const f2 S1 = fma2(FU, sub2(Q11, Q10), Q10);
         const f2 VAL = fma2(FV, sub2(S1, S0), S0);
         acc2[m] = fma2(WT, VAL, acc2[m]);
-    }
-}
-
-// FP16 taps as horizontal pairs: W points at the stage's A words (even cu)
-// or B words (odd cu) of the column's staged box column cu / 2; a row is
-// BU / 2 words. Per voxel two 32-bit shared loads give q00, q01 and q10,
-// q11; the arithmetic after the conversion is that of accumulate_pairs.
-__device__ __forceinline__ float h_lo(unsigned w) { return __half2float(__ushort_as_half((unsigned short)(w & 0xffffu))); }
-__device__ __forceinline__ float h_hi(unsigned w) { return __half2float(__ushort_as_half((unsigned short)(w >> 16))); }
-
-template <int TK, int BU>
-__device__ __forceinline__ void accumulate_h2_pairs(const unsigned *__restrict__ W, const ColView &c, f2 *acc2) {
-    constexpr int RW = BU / 2;
-    const float2 M2 = make_float2(kMagic, kMagic), NM2 = make_float2(-kMagic, -kMagic);
-    const float2 FU = make_float2(c.fu, c.fu), WT = make_float2(c.wt, c.wt);
-    const float2 DV2 = make_float2(c.dv, c.dv), V02 = make_float2(c.v0, c.v0);
-#pragma unroll
-    for (int m = 0; m < TK / 2; ++m) {
-        const float2 V = __ffma2_rn(make_float2((float)(2 * m), (float)(2 * m + 1)), DV2, V02);
-        const float2 TV = __fadd2_rd(V, M2);
-        const float2 FL = __fadd2_rn(TV, NM2);
-        const float2 FV = __fadd2_rn(V, make_float2(-FL.x, -FL.y));
-        const int ra = __float_as_int(TV.x) - kMagicBits, rb = __float_as_int(TV.y) - kMagicBits;
-        const unsigned *pa = W + ra * RW, *pb = W + rb * RW;
-        const unsigned a0 = pa[0], a1 = pa[RW], b0 = pb[0], b1 = pb[RW];
-        const float2 Q00 = make_float2(h_lo(a0), h_lo(b0)), Q01 = make_float2(h_hi(a0), h_hi(b0));
-        const float2 Q10 = make_float2(h_lo(a1), h_lo(b1)), Q11 = make_float2(h_hi(a1), h_hi(b1));
-        const float2 S0 = __ffma2_rn(FU, __fadd2_rn(Q01, make_float2(-Q00.x, -Q00.y)), Q00);
-        const float2 S1 = __ffma2_rn(FU, __fadd2_rn(Q11, make_float2(-Q10.x, -Q10.y)), Q10);
-        float2 a;
-        upk(acc2[m], a.x, a.y);
-        a = __ffma2_rn(WT, __ffma2_rn(FV, __fadd2_rn(S1, make_float2(-S0.x, -S0.y)), S0), a);
-        acc2[m] = pk(a.x, a.y);
-    }
-}
-
-template <int TK, int BU>
-__device__ __forceinline__ void accumulate_h2_scalar(const unsigned *__restrict__ W, const ColView &c, int ez,
-                                                     float *acc) {
-    constexpr int RW = BU / 2;
-#pragma unroll
-    for (int kk = 0; kk < TK; ++kk) {
-        if (kk >= ez) continue;
-        float v = fmaf((float)kk, c.dv, c.v0);
-        float tv = __fadd_rd(v, kMagic);
-        float fv = v - (tv - kMagic);
-        const unsigned *p = W + (__float_as_int(tv) - kMagicBits) * RW;
-        const unsigned w0 = p[0], w1 = p[RW];
-        float q00 = h_lo(w0), q01 = h_hi(w0), q10 = h_lo(w1), q11 = h_hi(w1);
-        float s0 = fmaf(c.fu, q01 - q00, q00);
-        float s1 = fmaf(c.fu, q11 - q10, q10);
-        float val = fmaf(fv, s1 - s0, s0);
-        acc[kk] = fmaf(c.wt, val, acc[kk]);
-    }
-}
-
-// The producer warp's step after an FP16 box has landed: write its shifted
-// copy B (four words per lane and pass; the last word of a row takes the
-// first half of the next row, which no tap reads).
-__device__ __forceinline__ void make_pair_copy(unsigned char *stage, int a_bytes, int words, int lane) {
-    const unsigned *A = reinterpret_cast<const unsigned *>(stage);
-    unsigned *B = reinterpret_cast<unsigned *>(stage + a_bytes + kPairShiftBytes);
-    for (int t = 4 * lane; t < words; t += 128) {
-        const uint4 a = *reinterpret_cast<const uint4 *>(A + t);
-        const unsigned nx = (t + 4 < words) ? A[t + 4] : 0u;
-        uint4 o;
-        o.x = __byte_perm(a.x, a.y, 0x5432);
-        o.y = __byte_perm(a.y, a.z, 0x5432);
-        o.z = __byte_perm(a.z, a.w, 0x5432);
-        o.w = __byte_perm(a.w, nx, 0x5432);
-        *reinterpret_cast<uint4 *>(B + t) = o;
     }
 }
 
@@ -365,12 +284,9 @@ bp_zcol_tma(const __grid_constant__ CUtensorMap tmap, const double *__restrict__
     ViewRec *recs = reinterpret_cast<ViewRec *>(smem);
     unsigned long long *full = reinterpret_cast<unsigned long long *>(smem + kBarOffset);
     unsigned long long *empty = full + kMaxStages;
-    unsigned long long *ready = empty + kMaxStages;   // FP16: the pair copy of a stage is written
     unsigned char *stages = smem + kStageOffset;
-    constexpr bool kH2 = sizeof(T) == 2;
-    const int sbytes = stage_stride<T>(BU, bv);
+    const int sbytes = stage_bytes<T>(BU, bv);
     const unsigned box_bytes = (unsigned)(BU * bv * sizeof(T));
-    const int a_bytes = stage_bytes<T>(BU, bv);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int ntx = (nx + kTX - 1) / kTX;
@@ -388,25 +304,28 @@ bp_zcol_tma(const __grid_constant__ CUtensorMap tmap, const double *__restrict__
         for (int s = 0; s < nst; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], kConsumerWarps);
-            mbar_init(&ready[s], 32);
         }
         fence_barrier_init();
         prefetch_tmap(&tmap);
     }
     __syncthreads();
 
-    // accumulators: FP32 pairs (kk, kk+1)
+    // accumulators: FP32 pairs (kk, kk+1) for FP32 taps, scalars otherwise
+    constexpr bool kPairs = sizeof(T) == 4;
     f2 acc2[TK / 2];
+    float acc[kPairs ? 1 : TK];
 #pragma unroll
     for (int m = 0; m < TK / 2; ++m) acc2[m] = 0ull;
+#pragma unroll
+    for (int kk = 0; kk < (kPairs ? 1 : TK); ++kk) acc[kk] = 0.0f;
 
     __shared__ unsigned arms[kMaxStages];   // producer: armings of each full barrier
     if (tid < kMaxStages) arms[tid] = 0;
     bool alive = true;
     // pipeline position of the current view g: slot g % nst, phase (g / nst) & 1,
     // advanced per view (no division)
-    int slot = 0, cslot = 0;   // cslot, cphase: the FP16 producer's pair-copy position
-    unsigned phase = 0, g = 0, cphase = 0;
+    int slot = 0;
+    unsigned phase = 0, g = 0;
     for (int cb = 0; cb < nviews; cb += kRecChunk) {
         const int cn = min(kRecChunk, nviews - cb);
         __syncthreads();
@@ -416,68 +335,23 @@ bp_zcol_tma(const __grid_constant__ CUtensorMap tmap, const double *__restrict__
                 atomicOr(err, DEV_ERR_FOOTPRINT);
         __syncthreads();
         if (warp == kConsumerWarps) {
-            if constexpr (!kH2) {
-                // ---- producer: one elected lane issues the TMA loads ----
-                if (lane == 0 && alive) {
-                    for (int n = 0; n < cn; ++n, ++g) {
-                        if (g >= (unsigned)nst && !mbar_wait_bounded(&empty[slot], phase ^ 1u, timeout_ns)) {
-                            atomicOr(err, DEV_ERR_TIMEOUT);
-                            alive = false;
-                            break;
-                        }
-                        if (view0 + cb + n != drop_view) {   // test hook: skip this view's load
-                            mbar_arrive_expect_tx(&full[slot], box_bytes);
-                            tma_load_4d(stages + slot * sbytes, &tmap, recs[n].u_box, recs[n].v_box,
-                                        cb + n, b, &full[slot]);
-                            ++arms[slot];
-                        }
-                        if (++slot == nst) {
-                            slot = 0;
-                            phase ^= 1u;
-                        }
+            // ---- producer: one elected lane issues the TMA loads ----
+            if (lane == 0 && alive) {
+                for (int n = 0; n < cn; ++n, ++g) {
+                    if (g >= (unsigned)nst && !mbar_wait_bounded(&empty[slot], phase ^ 1u, timeout_ns)) {
+                        atomicOr(err, DEV_ERR_TIMEOUT);
+                        alive = false;
+                        break;
                     }
-                }
-            } else {
-                // ---- producer (FP16): lane 0 issues the loads; the whole warp
-                // writes each landed box's shifted pair copy, nst - 1 views behind
-                // the issue so that loads stay in flight ----
-                const int lag = nst - 1;
-                for (int n = 0; n < cn + lag && alive; ++n) {
-                    if (n < cn) {
-                        bool ok = true;
-                        if (lane == 0) {
-                            if (g >= (unsigned)nst && !mbar_wait_bounded(&empty[slot], phase ^ 1u, timeout_ns)) {
-                                atomicOr(err, DEV_ERR_TIMEOUT);
-                                ok = false;
-                            } else if (view0 + cb + n != drop_view) {   // test hook: skip this view's load
-                                mbar_arrive_expect_tx(&full[slot], box_bytes);
-                                tma_load_4d(stages + slot * sbytes, &tmap, recs[n].u_box, recs[n].v_box,
-                                            cb + n, b, &full[slot]);
-                                ++arms[slot];
-                            }
-                        }
-                        if (!__shfl_sync(0xffffffffu, ok, 0)) {
-                            alive = false;
-                            break;
-                        }
-                        ++g;
-                        if (++slot == nst) {
-                            slot = 0;
-                            phase ^= 1u;
-                        }
+                    if (view0 + cb + n != drop_view) {   // test hook: skip this view's load
+                        mbar_arrive_expect_tx(&full[slot], box_bytes);
+                        tma_load_4d(stages + slot * sbytes, &tmap, recs[n].u_box, recs[n].v_box,
+                                    cb + n, b, &full[slot]);
+                        ++arms[slot];
                     }
-                    if (n >= lag) {
-                        if (!__all_sync(0xffffffffu, mbar_wait_bounded(&full[cslot], cphase, timeout_ns))) {
-                            if (lane == 0) atomicOr(err, DEV_ERR_TIMEOUT);
-                            alive = false;
-                            break;
-                        }
-                        make_pair_copy(stages + cslot * sbytes, a_bytes, BU * bv / 2, lane);
-                        mbar_arrive(&ready[cslot]);
-                        if (++cslot == nst) {
-                            cslot = 0;
-                            cphase ^= 1u;
-                        }
+                    if (++slot == nst) {
+                        slot = 0;
+                        phase ^= 1u;
                     }
                 }
             }
@@ -485,29 +359,15 @@ bp_zcol_tma(const __grid_constant__ CUtensorMap tmap, const double *__restrict__
             // ---- consumers ----
             for (int n = 0; n < cn && alive; ++n) {
                 // the whole warp agrees on the outcome of the bounded wait
-                if (!__all_sync(0xffffffffu, mbar_wait_bounded(kH2 ? &ready[slot] : &full[slot], phase, timeout_ns))) {
+                if (!__all_sync(0xffffffffu, mbar_wait_bounded(&full[slot], phase, timeout_ns))) {
                     if (lane == 0) atomicOr(err, DEV_ERR_TIMEOUT);
                     alive = false;
                     break;
                 }
                 ColView cv;
                 if (col_ok && column_view<BU>(recs[n], fdi, fdj, ez, bv, err, cv)) {
-                    if constexpr (kH2) {
-                        // the pair word of column cu: A for even cu, the shifted copy B for odd
-                        const unsigned char *st = stages + slot * sbytes + ((cv.cu & 1) ? a_bytes + kPairShiftBytes : 0);
-                        const unsigned *W = reinterpret_cast<const unsigned *>(st) + (cv.cu >> 1);
-                        if (ez == TK) {
-                            accumulate_h2_pairs<TK, BU>(W, cv, acc2);
-                        } else {
-                            float tmp[TK];
-#pragma unroll
-                            for (int m = 0; m < TK / 2; ++m) upk(acc2[m], tmp[2 * m], tmp[2 * m + 1]);
-                            accumulate_h2_scalar<TK, BU>(W, cv, ez, tmp);
-#pragma unroll
-                            for (int m = 0; m < TK / 2; ++m) acc2[m] = pk(tmp[2 * m], tmp[2 * m + 1]);
-                        }
-                    } else {
-                        const T *tile = reinterpret_cast<const T *>(stages + slot * sbytes);
+                    const T *tile = reinterpret_cast<const T *>(stages + slot * sbytes);
+                    if constexpr (kPairs) {
                         if (ez == TK) {
                             accumulate_pairs<TK, BU>(tile, cv, acc2);
                         } else {
@@ -518,6 +378,11 @@ bp_zcol_tma(const __grid_constant__ CUtensorMap tmap, const double *__restrict__
 #pragma unroll
                             for (int m = 0; m < TK / 2; ++m) acc2[m] = pk(tmp[2 * m], tmp[2 * m + 1]);
                         }
+                    } else {
+                        if (ez == TK)
+                            accumulate_scalar<T, TK, BU, true>(tile, cv, ez, acc);
+                        else
+                            accumulate_scalar<T, TK, BU, false>(tile, cv, ez, acc);
                     }
                 }
                 __syncwarp();
@@ -536,31 +401,64 @@ bp_zcol_tma(const __grid_constant__ CUtensorMap tmap, const double *__restrict__
                 atomicOr(err, DEV_ERR_TIMEOUT);
     }
     if (col_ok && alive) {
-        float out[TK];
+        if constexpr (kPairs) {
+            float out[TK];
 #pragma unroll
-        for (int m = 0; m < TK / 2; ++m) upk(acc2[m], out[2 * m], out[2 * m + 1]);
-        store_column<TK>(vol, out, b, i0 + di, j0 + dj, k0, ez, nx, ny, nz, scale, accumulate);
+            for (int m = 0; m < TK / 2; ++m) upk(acc2[m], out[2 * m], out[2 * m + 1]);
+            store_column<TK>(vol, out, b, i0 + di, j0 + dj, k0, ez, nx, ny, nz, scale, accumulate);
+        } else {
+            store_column<TK>(vol, acc, b, i0 + di, j0 + dj, k0, ez, nx, ny, nz, scale, accumulate);
+        }
     }
 }
 
-// The staged z-column kernel with mid-plane symmetry (FP32 projections): z
-// block y covers lower slices [16y, 16y+16) of the (nz+1)/2 lower slices and
-// their mirrors; each stage holds the lower box and the mirrored box. The
-// pipeline, bounded waits and drain are those of bp_zcol_tma.
-template <int BU, int MB>
+// The producer warp's step for FP16-stored projections: widen a landed FP16
+// box (rows of BU halves) to FP32 in the same layout, eight values per lane
+// and pass. Each element is converted once here instead of at every tap.
+__device__ __forceinline__ void widen_box(const unsigned char *src, unsigned char *dst, int n, int lane) {
+    const __half *h = reinterpret_cast<const __half *>(src);
+    float *f = reinterpret_cast<float *>(dst);
+#pragma unroll 2
+    for (int t = 8 * lane; t < n; t += 256) {
+        const uint4 w = *reinterpret_cast<const uint4 *>(h + t);
+        const __half2 *p = reinterpret_cast<const __half2 *>(&w);
+        const float2 a = __half22float2(p[0]), b = __half22float2(p[1]);
+        const float2 c = __half22float2(p[2]), d = __half22float2(p[3]);
+        *reinterpret_cast<float4 *>(f + t) = make_float4(a.x, a.y, b.x, b.y);
+        *reinterpret_cast<float4 *>(f + t + 4) = make_float4(c.x, c.y, d.x, d.y);
+    }
+}
+
+// The staged z-column kernel with mid-plane symmetry: z block y covers lower
+// slices [16y, 16y+16) of the (nz+1)/2 lower slices and their mirrors; each
+// stage holds the lower box and the mirrored box. The pipeline, bounded waits
+// and drain are those of bp_zcol_tma.
+//
+// FP16-stored projections (T = __half) are staged as FP16 (half the bytes
+// through HBM, L2 and TMA) and widened by the producer warp into one of two
+// FP32 buffers, which the consumers read with the FP32 code: per voxel the
+// arithmetic is the FP32 kernel's on the exact FP32 values of the halves.
+// The producer widens a view nst - 1 views after issuing its loads, so loads
+// stay in flight; a stage is free again once it is widened, and a buffer once
+// the consumers arrive on its empty barrier (ready: widened).
+template <typename T, int BU, int MB>
 __global__ void __launch_bounds__(kThreads, MB)
 bp_zsym_tma(const __grid_constant__ CUtensorMap tmap, const double *__restrict__ P, int view0,
             int nviews, int nx, int ny, int nz, int nv, int bv, int align, float *__restrict__ vol,
             float scale, int accumulate, unsigned *err, unsigned long long timeout_ns, int drop_view,
             int nst, int kz0, int kz1) {
     extern __shared__ __align__(128) unsigned char smem[];
+    constexpr bool kWiden = sizeof(T) == 2;
     ViewRec *recs = reinterpret_cast<ViewRec *>(smem);
     unsigned long long *full = reinterpret_cast<unsigned long long *>(smem + kBarOffset);
     unsigned long long *empty = full + kMaxStages;
+    unsigned long long *ready = empty + kMaxStages;
     unsigned char *stages = smem + kStageOffset;
-    const unsigned box_bytes = (unsigned)(BU * bv * sizeof(float));
-    const int half = stage_bytes<float>(BU, bv);   // offset of the mirrored box in a stage
+    const unsigned box_bytes = (unsigned)(BU * bv * sizeof(T));
+    const int half = stage_bytes<T>(BU, bv);   // offset of the mirrored box in a stage
     const int sbytes = 2 * half;
+    const int whalf = stage_bytes<float>(BU, bv);   // FP16: FP32 buffer pair (lower, mirror)
+    unsigned char *wide = stages + nst * sbytes;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int ntx = (nx + kTX - 1) / kTX;
@@ -575,9 +473,10 @@ bp_zsym_tma(const __grid_constant__ CUtensorMap tmap, const double *__restrict__
     const float fdi = (float)di, fdj = (float)dj;
 
     if (tid == 0) {
-        for (int s = 0; s < nst; ++s) {
+        for (int s = 0; s < max(nst, 2); ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], kConsumerWarps);
+            mbar_init(&ready[s], 32);
         }
         fence_barrier_init();
         prefetch_tmap(&tmap);
@@ -591,8 +490,8 @@ bp_zsym_tma(const __grid_constant__ CUtensorMap tmap, const double *__restrict__
     __shared__ unsigned arms[kMaxStages];
     if (tid < kMaxStages) arms[tid] = 0;
     bool alive = true;
-    int slot = 0;
-    unsigned phase = 0, g = 0;
+    int slot = 0, cslot = 0, buf = 0;     // load stage; FP16: stage and buffer of the next widening
+    unsigned phase = 0, g = 0, cphase = 0, bphase = 0, nwide = 0;
     for (int cb = 0; cb < nviews; cb += kRecChunk) {
         const int cn = min(kRecChunk, nviews - cb);
         __syncthreads();
@@ -601,40 +500,89 @@ bp_zsym_tma(const __grid_constant__ CUtensorMap tmap, const double *__restrict__
                 atomicOr(err, DEV_ERR_FOOTPRINT);
         __syncthreads();
         if (warp == kConsumerWarps) {
-            if (lane == 0 && alive) {
-                for (int n = 0; n < cn; ++n, ++g) {
-                    if (g >= (unsigned)nst && !mbar_wait_bounded(&empty[slot], phase ^ 1u, timeout_ns)) {
-                        atomicOr(err, DEV_ERR_TIMEOUT);
-                        alive = false;
-                        break;
+            if constexpr (!kWiden) {
+                if (lane == 0 && alive) {
+                    for (int n = 0; n < cn; ++n, ++g) {
+                        if (g >= (unsigned)nst && !mbar_wait_bounded(&empty[slot], phase ^ 1u, timeout_ns)) {
+                            atomicOr(err, DEV_ERR_TIMEOUT);
+                            alive = false;
+                            break;
+                        }
+                        if (view0 + cb + n != drop_view) {   // test hook: skip this view's loads
+                            mbar_arrive_expect_tx(&full[slot], 2 * box_bytes);
+                            unsigned char *st = stages + slot * sbytes;
+                            tma_load_4d(st, &tmap, recs[n].u_box, recs[n].v_box, cb + n, b, &full[slot]);
+                            tma_load_4d(st + half, &tmap, recs[n].u_box, nv - recs[n].v_box - bv, cb + n, b,
+                                        &full[slot]);
+                            ++arms[slot];
+                        }
+                        if (++slot == nst) {
+                            slot = 0;
+                            phase ^= 1u;
+                        }
                     }
-                    if (view0 + cb + n != drop_view) {   // test hook: skip this view's loads
+                }
+            } else {
+                // lane 0 issues the loads of view n into stage n mod nst, whose
+                // previous view has been widened already; the warp widens view
+                // n - lag once its boxes have landed and its buffer is free
+                const int lag = nst - 1;
+                auto issue = [&](int n) {
+                    if (lane == 0 && view0 + cb + n != drop_view) {   // test hook: skip this view's loads
                         mbar_arrive_expect_tx(&full[slot], 2 * box_bytes);
                         unsigned char *st = stages + slot * sbytes;
                         tma_load_4d(st, &tmap, recs[n].u_box, recs[n].v_box, cb + n, b, &full[slot]);
-                        tma_load_4d(st + half, &tmap, recs[n].u_box, nv - recs[n].v_box - bv, cb + n, b,
-                                    &full[slot]);
+                        tma_load_4d(st + half, &tmap, recs[n].u_box, nv - recs[n].v_box - bv, cb + n, b, &full[slot]);
                         ++arms[slot];
                     }
                     if (++slot == nst) {
                         slot = 0;
                         phase ^= 1u;
                     }
+                };
+                auto widen = [&]() -> bool {
+                    if (!__all_sync(0xffffffffu, mbar_wait_bounded(&full[cslot], cphase, timeout_ns)))
+                        return false;
+                    if (nwide >= 2 && !__all_sync(0xffffffffu, mbar_wait_bounded(&empty[buf], bphase ^ 1u, timeout_ns)))
+                        return false;
+                    const unsigned char *st = stages + cslot * sbytes;
+                    unsigned char *w = wide + buf * 2 * whalf;
+                    widen_box(st, w, BU * bv, lane);
+                    widen_box(st + half, w + whalf, BU * bv, lane);
+                    __syncwarp();   // every read of the stage is done before lane 0 reloads it
+                    mbar_arrive(&ready[buf]);
+                    if (++cslot == nst) {
+                        cslot = 0;
+                        cphase ^= 1u;
+                    }
+                    buf ^= 1;
+                    if (buf == 0) bphase ^= 1u;
+                    ++nwide;
+                    return true;
+                };
+                for (int n = 0; n < cn + lag && alive; ++n) {
+                    // with one stage a view must be issued before it can be widened
+                    if (lag > 0 && n >= lag && !widen()) alive = false;
+                    if (alive && n < cn) issue(n);
+                    if (alive && lag == 0 && !widen()) alive = false;
                 }
+                if (!alive && lane == 0) atomicOr(err, DEV_ERR_TIMEOUT);
             }
         } else {
             for (int n = 0; n < cn && alive; ++n) {
                 // the whole warp agrees on the outcome of the bounded wait
-                if (!__all_sync(0xffffffffu, mbar_wait_bounded(&full[slot], phase, timeout_ns))) {
+                unsigned long long *bar = kWiden ? &ready[buf] : &full[slot];
+                if (!__all_sync(0xffffffffu, mbar_wait_bounded(bar, kWiden ? bphase : phase, timeout_ns))) {
                     if (lane == 0) atomicOr(err, DEV_ERR_TIMEOUT);
                     alive = false;
                     break;
                 }
+                const unsigned char *boxes = kWiden ? wide + buf * 2 * whalf : stages + slot * sbytes;
+                const int mir = kWiden ? whalf : half;
                 ColView cv;
                 if (col_ok && column_view<BU>(recs[n], fdi, fdj, ez, bv, err, cv)) {
-                    const float *lo = reinterpret_cast<const float *>(stages + slot * sbytes) + cv.cu;
-                    const float *hi_top = reinterpret_cast<const float *>(stages + slot * sbytes + half) +
-                                          (bv - 1) * BU + cv.cu;
+                    const float *lo = reinterpret_cast<const float *>(boxes) + cv.cu;
+                    const float *hi_top = reinterpret_cast<const float *>(boxes + mir) + (bv - 1) * BU + cv.cu;
                     if (ez == kTH) {
                         accumulate_sym_pairs<BU>(lo, hi_top, cv, acc_lo, acc_hi);
                     } else {
@@ -653,10 +601,16 @@ bp_zsym_tma(const __grid_constant__ CUtensorMap tmap, const double *__restrict__
                     }
                 }
                 __syncwarp();
-                if (lane == 0) mbar_arrive(&empty[slot]);
-                if (++slot == nst) {
-                    slot = 0;
-                    phase ^= 1u;
+                if (kWiden) {
+                    if (lane == 0) mbar_arrive(&empty[buf]);
+                    buf ^= 1;
+                    if (buf == 0) bphase ^= 1u;
+                } else {
+                    if (lane == 0) mbar_arrive(&empty[slot]);
+                    if (++slot == nst) {
+                        slot = 0;
+                        phase ^= 1u;
+                    }
                 }
             }
         }
@@ -850,8 +804,8 @@ template <typename T, int TK, int BU, int MB>
 static cudaError_t launch_tma_t(const CUtensorMap &map, bp_ctx *ctx, int view0, int nviews,
                                 int bv, int align, float *vol, int batch, float scale,
                                 int accumulate, cudaStream_t st, int kz0, int kz1) {
-    const int nst = sizeof(T) == 2 ? ctx->plan.stages16 : ctx->plan.stages;
-    const int smem = kStageOffset + nst * stage_stride<T>(BU, bv);
+    const int nst = ctx->plan.stages;
+    const int smem = kStageOffset + nst * stage_bytes<T>(BU, bv);
     auto kern = bp_zcol_tma<T, TK, BU, MB>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
@@ -884,27 +838,39 @@ static cudaError_t launch_tma_bu(const CUtensorMap &map, bp_ctx *ctx, int bu, in
 #undef BP_TMA_CASE
 }
 
-template <int BU>
+// Shared memory of the symmetric kernel: records and barriers, nst stages of
+// two boxes, and for FP16 two FP32 buffers of two boxes each.
+template <typename T>
+static int sym_smem_bytes(int bu, int bv, int nst) {
+    return kStageOffset + nst * 2 * stage_bytes<T>(bu, bv) + (sizeof(T) == 2 ? 4 * stage_bytes<float>(bu, bv) : 0);
+}
+
+int sym_smem_bytes_host(int bu, int bv, int nst, int elem_bytes) {
+    return elem_bytes == 2 ? sym_smem_bytes<__half>(bu, bv, nst) : sym_smem_bytes<float>(bu, bv, nst);
+}
+
+template <typename T, int BU>
 static cudaError_t launch_sym_t(const CUtensorMap &map, bp_ctx *ctx, int view0, int nviews, int bv,
                                 float *vol, int batch, float scale, int accumulate, cudaStream_t st, int kz0,
                                 int kz1) {
     const int nst = ctx->plan.stages;
-    const int smem = kStageOffset + nst * 2 * stage_bytes<float>(BU, bv);
-    auto kern = bp_zsym_tma<BU, 2>;
+    const int smem = sym_smem_bytes<T>(BU, bv, nst);
+    auto kern = bp_zsym_tma<T, BU, 2>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     dim3 grid(((ctx->nx + kTX - 1) / kTX) * ((ctx->ny + kTY - 1) / kTY), (kz1 - kz0 + kTH - 1) / kTH, batch);
-    kern<<<grid, kThreads, smem, st>>>(map, ctx->d_P, view0, nviews, ctx->nx, ctx->ny, ctx->nz, ctx->nv, bv, 4,
-                                       vol, scale, accumulate, ctx->d_err, ctx->timeout_ns, ctx->test_drop_view,
-                                       nst, kz0, kz1);
+    kern<<<grid, kThreads, smem, st>>>(map, ctx->d_P, view0, nviews, ctx->nx, ctx->ny, ctx->nz, ctx->nv, bv,
+                                       sizeof(T) == 2 ? 8 : 4, vol, scale, accumulate, ctx->d_err, ctx->timeout_ns,
+                                       ctx->test_drop_view, nst, kz0, kz1);
     return cudaGetLastError();
 }
 
+template <typename T>
 static cudaError_t launch_sym(const CUtensorMap &map, bp_ctx *ctx, int bu, int view0, int nviews, int bv,
                               float *vol, int batch, float scale, int accumulate, cudaStream_t st, int kz0,
                               int kz1) {
 #define BP_SYM_CASE(W) \
-    case W: return launch_sym_t<W>(map, ctx, view0, nviews, bv, vol, batch, scale, accumulate, st, kz0, kz1);
+    case W: return launch_sym_t<T, W>(map, ctx, view0, nviews, bv, vol, batch, scale, accumulate, st, kz0, kz1);
     switch (bu) {
         BP_SYM_CASE(48) BP_SYM_CASE(80) BP_SYM_CASE(112) BP_SYM_CASE(144) BP_SYM_CASE(176)
         BP_SYM_CASE(208) BP_SYM_CASE(240)
@@ -935,8 +901,8 @@ static bp_status launch_range(bp_ctx *ctx, const void *proj, bp_dtype t, int vie
         return e == cudaSuccess ? BP_OK : cuda_fail(ctx, e, "bp_voxel_gen launch");
     }
     const Plan &pl = ctx->plan;
-    const int bu = sym ? pl.sym_bu : (t == BP_F16) ? pl.bu16 : pl.bu;
-    const int bv = sym ? pl.sym_bv : pl.bv;
+    const int bu = sym ? (t == BP_F16 ? pl.sym16_bu : pl.sym_bu) : (t == BP_F16) ? pl.bu16 : pl.bu;
+    const int bv = sym ? (t == BP_F16 ? pl.sym16_bv : pl.sym_bv) : pl.bv;
     const int align = (t == BP_F16) ? 8 : 4;
     PFN_encodeTiled enc = get_encode();
     bool tma = enc != nullptr && bu > 0 && (((size_t)ctx->nu * es) % 16 == 0) &&
@@ -956,7 +922,8 @@ static bp_status launch_range(bp_ctx *ctx, const void *proj, bp_dtype t, int vie
                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (r != CUDA_SUCCESS) tma = false;
         if (tma && sym) {
-            e = launch_sym(map, ctx, bu, view0, nviews, bv, vol, batch, scale, accumulate, st, kz0, kz1);
+            e = (t == BP_F16) ? launch_sym<__half>(map, ctx, bu, view0, nviews, bv, vol, batch, scale, accumulate, st, kz0, kz1)
+                              : launch_sym<float>(map, ctx, bu, view0, nviews, bv, vol, batch, scale, accumulate, st, kz0, kz1);
             return e == cudaSuccess ? BP_OK : cuda_fail(ctx, e, "bp_zsym_tma launch");
         }
         if (tma) {
@@ -993,8 +960,8 @@ static bp_status launch_range(bp_ctx *ctx, const void *proj, bp_dtype t, int vie
 
 // Slices [z0, z0 + nzs) and, with mirror, the mirrored slices
 // [nz - z0 - nzs, nz - z0) (the caller has checked z0 + nzs <= (nz + 1) / 2):
-// one symmetric launch where the plan has the symmetric kernel and the
-// projections are FP32, else plain launches over the two ranges (the middle
+// one symmetric launch where the plan has the symmetric kernel for the
+// projections' type, else plain launches over the two ranges (the middle
 // slice of an odd nz only once).
 bp_status launch_backproject(bp_ctx *ctx, const void *proj, bp_dtype t, int view0, int nviews,
                              long long batch_stride, float *vol, int batch, float scale,
@@ -1002,7 +969,7 @@ bp_status launch_backproject(bp_ctx *ctx, const void *proj, bp_dtype t, int view
     const long long view_elems = (long long)ctx->nu * ctx->nv;
     if (batch_stride == 0) batch_stride = view_elems * nviews;
     const int z1 = z0 + nzs;
-    if (mirror && ctx->zinv && t == BP_F32 && ctx->plan.sym_bu > 0) {
+    if (mirror && ctx->zinv && (t == BP_F32 ? ctx->plan.sym_bu : ctx->plan.sym16_bu) > 0) {
         bp_status s = launch_range(ctx, proj, t, view0, nviews, batch_stride, vol, batch, scale, accumulate, st,
                                    z0, z1, true);
         if (s != BP_ERR_UNSUPPORTED) return s;

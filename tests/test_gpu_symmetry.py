@@ -26,9 +26,11 @@ def _check(g, q, views_chunk=None):
     scale = math.pi / g["np"]
     P = oracle.matrices(g)
     ref = oracle.backproject(P, q, g["nx"], g["ny"], g["nz"], scale)
+    ref16 = oracle.backproject(P, q.astype(np.float16).astype(np.float64), g["nx"], g["ny"], g["nz"], scale)
     with api.bp_create(g) as ctx:
         d = torch.from_numpy(q).cuda()
-        assert api.bp_get_plan(ctx)["symmetric"]          # the default for centred geometries
+        plan = api.bp_get_plan(ctx)
+        assert plan["symmetric"] and plan["symmetric16"]  # the default for centred geometries
         sym = api.bp_backproject(ctx, d, scale=scale).cpu().numpy()
         sym16 = api.bp_backproject(ctx, d.half(), scale=scale).cpu().numpy()
         api.bp_set_symmetry(ctx, False)
@@ -46,9 +48,13 @@ def _check(g, q, views_chunk=None):
         api.bp_device_status(ctx)
     assert rel(sym, ref) <= TOL32
     assert rel(plain, ref) <= TOL32
-    # FP16-stored projections (the plain kernel either way; the oracle takes the unquantised values)
+    # FP16-stored projections: against the unquantised values, and the FP32
+    # arithmetic on the quantised values (the symmetric kernel widens each
+    # staged FP16 box to FP32 before the taps)
     assert rel(sym16, ref) <= TOL16
     assert rel(plain16, ref) <= TOL16
+    assert rel(sym16, ref16) <= TOL32
+    assert rel(plain16, ref16) <= TOL32
     return sym, plain
 
 
