@@ -208,10 +208,10 @@ bp_status bp_device_status(bp_ctx *ctx, void *stream);
  *                      least) before falling back to direct global loads. The
  *                      GPU counterpart of the paper's view batching and
  *                      prefetching depth (Section 3.1.3, Algorithm 2).
- *   bp_set_symmetry    back-projection with the mid-plane symmetry of
+ *   bp_set_symmetry    FP32 back-projection with the mid-plane symmetry of
  *                      Section 3.1.2 / Algorithm 1: a thread owns voxels k
  *                      and nz-1-k and computes v, its floor and fraction
- *                      once for both (FP32 and FP16-stored projections). 1 (default): used whenever
+ *                      once for both. 1 (default): used whenever
  *                      v(nz-1-k) = nv-1-v(k) holds for the context's matrices
  *                      (v_off = 0, volume centred on the central plane) and
  *                      the boxes fit shared memory; asking for it explicitly
@@ -232,11 +232,8 @@ bp_status bp_device_status(bp_ctx *ctx, void *stream);
  *   bp_get_plan        the launch plan: voxels per thread along z, the
  *                      staged box (FP32 width, FP16 width, rows; a width of
  *                      -1 means that element type uses direct global loads),
- *                      the pipeline depth in use and which calls use the
- *                      mid-plane symmetry (bit 0: FP32 projections, bit 1:
- *                      FP16-stored projections, whose boxes the kernel
- *                      widens to FP32 in shared memory). Any pointer may be
- *                      NULL.
+ *                      the pipeline depth in use and whether FP32 calls use
+ *                      the mid-plane symmetry. Any pointer may be NULL.
  */
 bp_status bp_set_tuning(bp_ctx *ctx, int tk, int ctas_per_sm);
 bp_status bp_set_pipeline_depth(bp_ctx *ctx, int stages);

@@ -139,7 +139,7 @@ def bp_get_plan(ctx: Context) -> dict:
     v = [ctypes.c_int() for _ in range(6)]
     check(_lib.load().bp_get_plan(ctx.handle, *[ctypes.byref(x) for x in v]), ctx.handle)
     return dict(tk=v[0].value, bu32=v[1].value, bu16=v[2].value, bv=v[3].value, stages=v[4].value,
-                symmetric=bool(v[5].value & 1), symmetric16=bool(v[5].value & 2))
+                symmetric=bool(v[5].value))
 
 
 def bp_set_tuning(ctx: Context, tk: int = 32, ctas_per_sm: int = 2) -> None:

@@ -149,10 +149,10 @@ void max_footprint(const bp_ctx *ctx, int tx, int ty, int tk, int align, int *bu
     *bv = *std::max_element(mv.begin(), mv.end());
 }
 
-// Shared memory of the staged back-projector: view records, 3 x 8 barrier
+// Shared memory of the staged back-projector: view records, 2 x 8 barrier
 // slots, then one box per stage (each rounded up to 128 bytes).
 static int tma_smem_bytes(int bu, int bv, int elem_bytes, int stages) {
-    const int base = (256 * 48 + 3 * 8 * 8 + 127) / 128 * 128;
+    const int base = (256 * 48 + 2 * 8 * 8 + 127) / 128 * 128;
     return base + stages * ((bu * bv * elem_bytes + 127) / 128 * 128);
 }
 
@@ -198,22 +198,14 @@ static void make_plan(bp_ctx *ctx) {
     if (pl.bv > 256 || !fits(pl.bu, 4, pl.stages)) pl.bu = -1;
     if (pl.bv > 256 || !fits(pl.bu16, 2, pl.stages)) pl.bu16 = -1;
     // mid-plane symmetry: boxes of 16-voxel half columns, two per stage
-    pl.sym_bu = pl.sym_bv = pl.sym16_bu = pl.sym16_bv = -1;
+    pl.sym_bu = pl.sym_bv = -1;
     if (ctx->sym_enable && pl.bu > 0 && mirror_symmetric(ctx)) {
         int sbu, sbv;
         max_footprint(ctx, pl.tx, pl.ty, 16, 4, &sbu, &sbv);
         sbu = plan_box_width(sbu, 4);
-        if (sbu > 0 && sbv <= 256 && sym_smem_bytes_host(sbu, sbv, pl.stages, 4) <= 227 * 1024) {
+        if (sbu > 0 && sbv <= 256 && tma_smem_bytes(sbu, sbv, 4, 2 * pl.stages) <= 227 * 1024) {
             pl.sym_bu = sbu;
             pl.sym_bv = sbv;
-        }
-        // FP16: boxes aligned to 8 halves (16 bytes, the TMA rule), widths from
-        // the FP32 list, since the widened boxes are read as FP32
-        max_footprint(ctx, pl.tx, pl.ty, 16, 8, &sbu, &sbv);
-        sbu = plan_box_width(sbu, 4);
-        if (sbu > 0 && sbv <= 256 && sym_smem_bytes_host(sbu, sbv, pl.stages, 2) <= 227 * 1024) {
-            pl.sym16_bu = sbu;
-            pl.sym16_bv = sbv;
         }
     }
     // forward projector: lane windows as wide as the u footprint of an 8 x 4
@@ -432,7 +424,7 @@ bp_status bp_backproject_views(bp_ctx *ctx, const void *proj, bp_dtype t, int vi
     bp_status s = check_bp_args(ctx, proj, t, view0, n_views, proj_batch_stride, vol, batch, scale);
     if (s != BP_OK) return s;
     // the whole volume: the lower half and its mirror where the symmetric kernel applies
-    const bool sym = ctx->zinv && (t == BP_F32 ? ctx->plan.sym_bu : ctx->plan.sym16_bu) > 0;
+    const bool sym = ctx->zinv && t == BP_F32 && ctx->plan.sym_bu > 0;
     return launch_backproject(ctx, proj, t, view0, n_views, proj_batch_stride, vol, batch, scale,
                               accumulate ? 1 : 0, (cudaStream_t)stream, 0, sym ? (ctx->nz + 1) / 2 : ctx->nz,
                               sym ? 1 : 0);
@@ -575,7 +567,7 @@ bp_status bp_get_plan(const bp_ctx *ctx, int *tk, int *bu32, int *bu16, int *bv,
     if (bu16) *bu16 = ctx->plan.bu16;
     if (bv) *bv = ctx->plan.bv;
     if (stages) *stages = ctx->plan.stages;
-    if (symmetric) *symmetric = (ctx->plan.sym_bu > 0 ? 1 : 0) | (ctx->plan.sym16_bu > 0 ? 2 : 0);
+    if (symmetric) *symmetric = ctx->plan.sym_bu > 0;
     return BP_OK;
 }
 

@@ -52,7 +52,6 @@ struct Plan {
     int bu16;                // box width for FP16 (multiple of 8)
     int stages;              // pipeline depth (views in flight), <= the requested depth
     int sym_bu, sym_bv;      // mid-plane symmetry kernel: staged box (16-voxel half columns), -1 if off
-    int sym16_bu, sym16_bv;  // the same for FP16-stored projections (boxes aligned to 8 halves)
     int ctas;                // CTAs per SM the TK=32 kernel's register budget targets (2 or 3)
     int fp_wbu;              // forward projector: window width in columns (8 x 4 column patch), -1 if unusable
 };
@@ -104,8 +103,7 @@ bp_status launch_forward(bp_ctx *ctx, const float *vol, float *proj, int batch, 
                          cudaStream_t st);
 // Dynamic shared memory of the forward projector for windows wc columns wide.
 int fp_smem_bytes(int wc);
-int fp_window_width(int need);
-int sym_smem_bytes_host(int bu, int bv, int nst, int elem_bytes);   // symmetric kernel's shared memory   // smallest window width the forward projector is built for, or -1
+int fp_window_width(int need);   // smallest window width the forward projector is built for, or -1
 bp_status launch_filter(bp_ctx *ctx, const float *proj, void *out, bp_dtype out_t,
                         long long n_views_total, cudaStream_t st);
 bp_status launch_phantom(bp_ctx *ctx, const double *d_ell, int n_ell, float *proj,

@@ -39,7 +39,7 @@ __host__ __device__ constexpr int stage_bytes(int bu, int bv) {
 
 constexpr int kRecBytes = kRecChunk * (int)sizeof(ViewRec);
 constexpr int kBarOffset = kRecBytes;
-constexpr int kStageOffset = align_up(kRecBytes + 3 * kMaxStages * 8, 128);   // full, empty, ready
+constexpr int kStageOffset = align_up(kRecBytes + 2 * kMaxStages * 8, 128);
 
 // Thread -> column within the CTA tile: each warp owns an 8 x 4 patch.
 __device__ __forceinline__ void consumer_column(int warp, int lane, int *di, int *dj) {
@@ -412,53 +412,24 @@ bp_zcol_tma(const __grid_constant__ CUtensorMap tmap, const double *__restrict__
     }
 }
 
-// The producer warp's step for FP16-stored projections: widen a landed FP16
-// box (rows of BU halves) to FP32 in the same layout, eight values per lane
-// and pass. Each element is converted once here instead of at every tap.
-__device__ __forceinline__ void widen_box(const unsigned char *src, unsigned char *dst, int n, int lane) {
-    const __half *h = reinterpret_cast<const __half *>(src);
-    float *f = reinterpret_cast<float *>(dst);
-#pragma unroll 2
-    for (int t = 8 * lane; t < n; t += 256) {
-        const uint4 w = *reinterpret_cast<const uint4 *>(h + t);
-        const __half2 *p = reinterpret_cast<const __half2 *>(&w);
-        const float2 a = __half22float2(p[0]), b = __half22float2(p[1]);
-        const float2 c = __half22float2(p[2]), d = __half22float2(p[3]);
-        *reinterpret_cast<float4 *>(f + t) = make_float4(a.x, a.y, b.x, b.y);
-        *reinterpret_cast<float4 *>(f + t + 4) = make_float4(c.x, c.y, d.x, d.y);
-    }
-}
-
-// The staged z-column kernel with mid-plane symmetry: z block y covers lower
-// slices [16y, 16y+16) of the (nz+1)/2 lower slices and their mirrors; each
-// stage holds the lower box and the mirrored box. The pipeline, bounded waits
-// and drain are those of bp_zcol_tma.
-//
-// FP16-stored projections (T = __half) are staged as FP16 (half the bytes
-// through HBM, L2 and TMA) and widened by the producer warp into one of two
-// FP32 buffers, which the consumers read with the FP32 code: per voxel the
-// arithmetic is the FP32 kernel's on the exact FP32 values of the halves.
-// The producer widens a view nst - 1 views after issuing its loads, so loads
-// stay in flight; a stage is free again once it is widened, and a buffer once
-// the consumers arrive on its empty barrier (ready: widened).
-template <typename T, int BU, int MB>
+// The staged z-column kernel with mid-plane symmetry (FP32 projections): z
+// block y covers lower slices [16y, 16y+16) of the (nz+1)/2 lower slices and
+// their mirrors; each stage holds the lower box and the mirrored box. The
+// pipeline, bounded waits and drain are those of bp_zcol_tma.
+template <int BU, int MB>
 __global__ void __launch_bounds__(kThreads, MB)
 bp_zsym_tma(const __grid_constant__ CUtensorMap tmap, const double *__restrict__ P, int view0,
             int nviews, int nx, int ny, int nz, int nv, int bv, int align, float *__restrict__ vol,
             float scale, int accumulate, unsigned *err, unsigned long long timeout_ns, int drop_view,
             int nst, int kz0, int kz1) {
     extern __shared__ __align__(128) unsigned char smem[];
-    constexpr bool kWiden = sizeof(T) == 2;
     ViewRec *recs = reinterpret_cast<ViewRec *>(smem);
     unsigned long long *full = reinterpret_cast<unsigned long long *>(smem + kBarOffset);
     unsigned long long *empty = full + kMaxStages;
-    unsigned long long *ready = empty + kMaxStages;
     unsigned char *stages = smem + kStageOffset;
-    const unsigned box_bytes = (unsigned)(BU * bv * sizeof(T));
-    const int half = stage_bytes<T>(BU, bv);   // offset of the mirrored box in a stage
+    const unsigned box_bytes = (unsigned)(BU * bv * sizeof(float));
+    const int half = stage_bytes<float>(BU, bv);   // offset of the mirrored box in a stage
     const int sbytes = 2 * half;
-    const int whalf = stage_bytes<float>(BU, bv);   // FP16: FP32 buffer pair (lower, mirror)
-    unsigned char *wide = stages + nst * sbytes;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int ntx = (nx + kTX - 1) / kTX;
@@ -473,10 +444,9 @@ bp_zsym_tma(const __grid_constant__ CUtensorMap tmap, const double *__restrict__
     const float fdi = (float)di, fdj = (float)dj;
 
     if (tid == 0) {
-        for (int s = 0; s < max(nst, 2); ++s) {
+        for (int s = 0; s < nst; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], kConsumerWarps);
-            mbar_init(&ready[s], 32);
         }
         fence_barrier_init();
         prefetch_tmap(&tmap);
@@ -490,8 +460,8 @@ bp_zsym_tma(const __grid_constant__ CUtensorMap tmap, const double *__restrict__
     __shared__ unsigned arms[kMaxStages];
     if (tid < kMaxStages) arms[tid] = 0;
     bool alive = true;
-    int slot = 0, cslot = 0, buf = 0;     // load stage; FP16: stage and buffer of the next widening
-    unsigned phase = 0, g = 0, cphase = 0, bphase = 0, nwide = 0;
+    int slot = 0;
+    unsigned phase = 0, g = 0;
     for (int cb = 0; cb < nviews; cb += kRecChunk) {
         const int cn = min(kRecChunk, nviews - cb);
         __syncthreads();
@@ -500,89 +470,40 @@ bp_zsym_tma(const __grid_constant__ CUtensorMap tmap, const double *__restrict__
                 atomicOr(err, DEV_ERR_FOOTPRINT);
         __syncthreads();
         if (warp == kConsumerWarps) {
-            if constexpr (!kWiden) {
-                if (lane == 0 && alive) {
-                    for (int n = 0; n < cn; ++n, ++g) {
-                        if (g >= (unsigned)nst && !mbar_wait_bounded(&empty[slot], phase ^ 1u, timeout_ns)) {
-                            atomicOr(err, DEV_ERR_TIMEOUT);
-                            alive = false;
-                            break;
-                        }
-                        if (view0 + cb + n != drop_view) {   // test hook: skip this view's loads
-                            mbar_arrive_expect_tx(&full[slot], 2 * box_bytes);
-                            unsigned char *st = stages + slot * sbytes;
-                            tma_load_4d(st, &tmap, recs[n].u_box, recs[n].v_box, cb + n, b, &full[slot]);
-                            tma_load_4d(st + half, &tmap, recs[n].u_box, nv - recs[n].v_box - bv, cb + n, b,
-                                        &full[slot]);
-                            ++arms[slot];
-                        }
-                        if (++slot == nst) {
-                            slot = 0;
-                            phase ^= 1u;
-                        }
+            if (lane == 0 && alive) {
+                for (int n = 0; n < cn; ++n, ++g) {
+                    if (g >= (unsigned)nst && !mbar_wait_bounded(&empty[slot], phase ^ 1u, timeout_ns)) {
+                        atomicOr(err, DEV_ERR_TIMEOUT);
+                        alive = false;
+                        break;
                     }
-                }
-            } else {
-                // lane 0 issues the loads of view n into stage n mod nst, whose
-                // previous view has been widened already; the warp widens view
-                // n - lag once its boxes have landed and its buffer is free
-                const int lag = nst - 1;
-                auto issue = [&](int n) {
-                    if (lane == 0 && view0 + cb + n != drop_view) {   // test hook: skip this view's loads
+                    if (view0 + cb + n != drop_view) {   // test hook: skip this view's loads
                         mbar_arrive_expect_tx(&full[slot], 2 * box_bytes);
                         unsigned char *st = stages + slot * sbytes;
                         tma_load_4d(st, &tmap, recs[n].u_box, recs[n].v_box, cb + n, b, &full[slot]);
-                        tma_load_4d(st + half, &tmap, recs[n].u_box, nv - recs[n].v_box - bv, cb + n, b, &full[slot]);
+                        tma_load_4d(st + half, &tmap, recs[n].u_box, nv - recs[n].v_box - bv, cb + n, b,
+                                    &full[slot]);
                         ++arms[slot];
                     }
                     if (++slot == nst) {
                         slot = 0;
                         phase ^= 1u;
                     }
-                };
-                auto widen = [&]() -> bool {
-                    if (!__all_sync(0xffffffffu, mbar_wait_bounded(&full[cslot], cphase, timeout_ns)))
-                        return false;
-                    if (nwide >= 2 && !__all_sync(0xffffffffu, mbar_wait_bounded(&empty[buf], bphase ^ 1u, timeout_ns)))
-                        return false;
-                    const unsigned char *st = stages + cslot * sbytes;
-                    unsigned char *w = wide + buf * 2 * whalf;
-                    widen_box(st, w, BU * bv, lane);
-                    widen_box(st + half, w + whalf, BU * bv, lane);
-                    __syncwarp();   // every read of the stage is done before lane 0 reloads it
-                    mbar_arrive(&ready[buf]);
-                    if (++cslot == nst) {
-                        cslot = 0;
-                        cphase ^= 1u;
-                    }
-                    buf ^= 1;
-                    if (buf == 0) bphase ^= 1u;
-                    ++nwide;
-                    return true;
-                };
-                for (int n = 0; n < cn + lag && alive; ++n) {
-                    // with one stage a view must be issued before it can be widened
-                    if (lag > 0 && n >= lag && !widen()) alive = false;
-                    if (alive && n < cn) issue(n);
-                    if (alive && lag == 0 && !widen()) alive = false;
                 }
-                if (!alive && lane == 0) atomicOr(err, DEV_ERR_TIMEOUT);
             }
         } else {
             for (int n = 0; n < cn && alive; ++n) {
                 // the whole warp agrees on the outcome of the bounded wait
-                unsigned long long *bar = kWiden ? &ready[buf] : &full[slot];
-                if (!__all_sync(0xffffffffu, mbar_wait_bounded(bar, kWiden ? bphase : phase, timeout_ns))) {
+                if (!__all_sync(0xffffffffu, mbar_wait_bounded(&full[slot], phase, timeout_ns))) {
                     if (lane == 0) atomicOr(err, DEV_ERR_TIMEOUT);
                     alive = false;
                     break;
                 }
-                const unsigned char *boxes = kWiden ? wide + buf * 2 * whalf : stages + slot * sbytes;
-                const int mir = kWiden ? whalf : half;
                 ColView cv;
                 if (col_ok && column_view<BU>(recs[n], fdi, fdj, ez, bv, err, cv)) {
-                    const float *lo = reinterpret_cast<const float *>(boxes) + cv.cu;
-                    const float *hi_top = reinterpret_cast<const float *>(boxes + mir) + (bv - 1) * BU + cv.cu;
+                    const float *lo = reinterpret_cast<const float *>(stages + slot * sbytes) + cv.cu;
+                    const float *hi_top = reinterpret_cast<const float *>(stages + slot * sbytes + half) +
+                                          (bv - 1) * BU + cv.cu;
                     if (ez == kTH) {
                         accumulate_sym_pairs<BU>(lo, hi_top, cv, acc_lo, acc_hi);
                     } else {
@@ -601,16 +522,10 @@ bp_zsym_tma(const __grid_constant__ CUtensorMap tmap, const double *__restrict__
                     }
                 }
                 __syncwarp();
-                if (kWiden) {
-                    if (lane == 0) mbar_arrive(&empty[buf]);
-                    buf ^= 1;
-                    if (buf == 0) bphase ^= 1u;
-                } else {
-                    if (lane == 0) mbar_arrive(&empty[slot]);
-                    if (++slot == nst) {
-                        slot = 0;
-                        phase ^= 1u;
-                    }
+                if (lane == 0) mbar_arrive(&empty[slot]);
+                if (++slot == nst) {
+                    slot = 0;
+                    phase ^= 1u;
                 }
             }
         }
@@ -838,39 +753,27 @@ static cudaError_t launch_tma_bu(const CUtensorMap &map, bp_ctx *ctx, int bu, in
 #undef BP_TMA_CASE
 }
 
-// Shared memory of the symmetric kernel: records and barriers, nst stages of
-// two boxes, and for FP16 two FP32 buffers of two boxes each.
-template <typename T>
-static int sym_smem_bytes(int bu, int bv, int nst) {
-    return kStageOffset + nst * 2 * stage_bytes<T>(bu, bv) + (sizeof(T) == 2 ? 4 * stage_bytes<float>(bu, bv) : 0);
-}
-
-int sym_smem_bytes_host(int bu, int bv, int nst, int elem_bytes) {
-    return elem_bytes == 2 ? sym_smem_bytes<__half>(bu, bv, nst) : sym_smem_bytes<float>(bu, bv, nst);
-}
-
-template <typename T, int BU>
+template <int BU>
 static cudaError_t launch_sym_t(const CUtensorMap &map, bp_ctx *ctx, int view0, int nviews, int bv,
                                 float *vol, int batch, float scale, int accumulate, cudaStream_t st, int kz0,
                                 int kz1) {
     const int nst = ctx->plan.stages;
-    const int smem = sym_smem_bytes<T>(BU, bv, nst);
-    auto kern = bp_zsym_tma<T, BU, 2>;
+    const int smem = kStageOffset + nst * 2 * stage_bytes<float>(BU, bv);
+    auto kern = bp_zsym_tma<BU, 2>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     dim3 grid(((ctx->nx + kTX - 1) / kTX) * ((ctx->ny + kTY - 1) / kTY), (kz1 - kz0 + kTH - 1) / kTH, batch);
-    kern<<<grid, kThreads, smem, st>>>(map, ctx->d_P, view0, nviews, ctx->nx, ctx->ny, ctx->nz, ctx->nv, bv,
-                                       sizeof(T) == 2 ? 8 : 4, vol, scale, accumulate, ctx->d_err, ctx->timeout_ns,
-                                       ctx->test_drop_view, nst, kz0, kz1);
+    kern<<<grid, kThreads, smem, st>>>(map, ctx->d_P, view0, nviews, ctx->nx, ctx->ny, ctx->nz, ctx->nv, bv, 4,
+                                       vol, scale, accumulate, ctx->d_err, ctx->timeout_ns, ctx->test_drop_view,
+                                       nst, kz0, kz1);
     return cudaGetLastError();
 }
 
-template <typename T>
 static cudaError_t launch_sym(const CUtensorMap &map, bp_ctx *ctx, int bu, int view0, int nviews, int bv,
                               float *vol, int batch, float scale, int accumulate, cudaStream_t st, int kz0,
                               int kz1) {
 #define BP_SYM_CASE(W) \
-    case W: return launch_sym_t<T, W>(map, ctx, view0, nviews, bv, vol, batch, scale, accumulate, st, kz0, kz1);
+    case W: return launch_sym_t<W>(map, ctx, view0, nviews, bv, vol, batch, scale, accumulate, st, kz0, kz1);
     switch (bu) {
         BP_SYM_CASE(48) BP_SYM_CASE(80) BP_SYM_CASE(112) BP_SYM_CASE(144) BP_SYM_CASE(176)
         BP_SYM_CASE(208) BP_SYM_CASE(240)
@@ -901,8 +804,8 @@ static bp_status launch_range(bp_ctx *ctx, const void *proj, bp_dtype t, int vie
         return e == cudaSuccess ? BP_OK : cuda_fail(ctx, e, "bp_voxel_gen launch");
     }
     const Plan &pl = ctx->plan;
-    const int bu = sym ? (t == BP_F16 ? pl.sym16_bu : pl.sym_bu) : (t == BP_F16) ? pl.bu16 : pl.bu;
-    const int bv = sym ? (t == BP_F16 ? pl.sym16_bv : pl.sym_bv) : pl.bv;
+    const int bu = sym ? pl.sym_bu : (t == BP_F16) ? pl.bu16 : pl.bu;
+    const int bv = sym ? pl.sym_bv : pl.bv;
     const int align = (t == BP_F16) ? 8 : 4;
     PFN_encodeTiled enc = get_encode();
     bool tma = enc != nullptr && bu > 0 && (((size_t)ctx->nu * es) % 16 == 0) &&
@@ -922,8 +825,7 @@ static bp_status launch_range(bp_ctx *ctx, const void *proj, bp_dtype t, int vie
                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (r != CUDA_SUCCESS) tma = false;
         if (tma && sym) {
-            e = (t == BP_F16) ? launch_sym<__half>(map, ctx, bu, view0, nviews, bv, vol, batch, scale, accumulate, st, kz0, kz1)
-                              : launch_sym<float>(map, ctx, bu, view0, nviews, bv, vol, batch, scale, accumulate, st, kz0, kz1);
+            e = launch_sym(map, ctx, bu, view0, nviews, bv, vol, batch, scale, accumulate, st, kz0, kz1);
             return e == cudaSuccess ? BP_OK : cuda_fail(ctx, e, "bp_zsym_tma launch");
         }
         if (tma) {
@@ -960,8 +862,8 @@ static bp_status launch_range(bp_ctx *ctx, const void *proj, bp_dtype t, int vie
 
 // Slices [z0, z0 + nzs) and, with mirror, the mirrored slices
 // [nz - z0 - nzs, nz - z0) (the caller has checked z0 + nzs <= (nz + 1) / 2):
-// one symmetric launch where the plan has the symmetric kernel for the
-// projections' type, else plain launches over the two ranges (the middle
+// one symmetric launch where the plan has the symmetric kernel and the
+// projections are FP32, else plain launches over the two ranges (the middle
 // slice of an odd nz only once).
 bp_status launch_backproject(bp_ctx *ctx, const void *proj, bp_dtype t, int view0, int nviews,
                              long long batch_stride, float *vol, int batch, float scale,
@@ -969,7 +871,7 @@ bp_status launch_backproject(bp_ctx *ctx, const void *proj, bp_dtype t, int view
     const long long view_elems = (long long)ctx->nu * ctx->nv;
     if (batch_stride == 0) batch_stride = view_elems * nviews;
     const int z1 = z0 + nzs;
-    if (mirror && ctx->zinv && (t == BP_F32 ? ctx->plan.sym_bu : ctx->plan.sym16_bu) > 0) {
+    if (mirror && ctx->zinv && t == BP_F32 && ctx->plan.sym_bu > 0) {
         bp_status s = launch_range(ctx, proj, t, view0, nviews, batch_stride, vol, batch, scale, accumulate, st,
                                    z0, z1, true);
         if (s != BP_ERR_UNSUPPORTED) return s;
