@@ -54,6 +54,20 @@ bp_status it_mlem_update(float *x, const float *b, const float *s, long long n, 
 bp_status it_sart_update(float *x, const float *b, const float *s, long long n, float lambda,
                          int nonneg, float eps, void *stream);
 
+/* Least squares on the projector pair (the differentiable reconstruction:
+ * gradient descent on L(x) = 0.5 ||A x - p||^2, A = fp_project):
+ *   it_ls_residual  r[i] = y[i] - p[i] (FP32) and *loss = 0.5 sum r[i]^2,
+ *                   summed in FP64 (loss is a device double, overwritten;
+ *                   the blocks' partial sums are added in a varying order,
+ *                   so the loss's last bits may differ between runs, r's
+ *                   never do). y = A x, p the measured projections.
+ *   it_scale        out[i] = r[i] * (float)(*s), s a device double (the
+ *                   gradient of the loss for an upstream gradient s).
+ *   it_gd_step      x[i] = x[i] - (step * g[i]), two FP32 roundings. */
+bp_status it_ls_residual(const float *y, const float *p, float *r, long long n, double *loss, void *stream);
+bp_status it_scale(const float *r, const double *s, float *out, long long n, void *stream);
+bp_status it_gd_step(float *x, const float *g, long long n, float step, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

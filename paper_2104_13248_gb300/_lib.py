@@ -92,6 +92,9 @@ PROTOTYPES = {
     "it_residual": (_i, [_vp, _vp, _vp, _vp, _ll, _f, _vp]),
     "it_mlem_update": (_i, [_vp, _vp, _vp, _ll, _f, _vp]),
     "it_sart_update": (_i, [_vp, _vp, _vp, _ll, _f, _i, _f, _vp]),
+    "it_ls_residual": (_i, [_vp, _vp, _vp, _ll, _vp, _vp]),
+    "it_scale": (_i, [_vp, _vp, _vp, _ll, _vp]),
+    "it_gd_step": (_i, [_vp, _vp, _ll, _f, _vp]),
 }
 
 

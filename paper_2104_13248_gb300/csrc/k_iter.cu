@@ -120,6 +120,81 @@ __global__ void __launch_bounds__(kItThreads) sart_kernel(float *x, const float 
     for (long long i = tail + t0; i < n; i += stride) x[i] = sart1(x[i], b[i], s[i], lam, nonneg, eps);
 }
 
+// Least squares: r = y - p and the block's share of 0.5 sum r^2 in FP64,
+// added to *loss once per block (the order of the blocks' additions varies,
+// so the loss may differ from run to run in its last bits; r does not).
+__global__ void __launch_bounds__(kItThreads) ls_resid_kernel(const float *__restrict__ y, const float *__restrict__ p,
+                                                              float *r, long long n, double *loss, int vec) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    double acc = 0.0;
+    long long tail = 0;
+    if (vec) {
+        const float4 *y4 = reinterpret_cast<const float4 *>(y), *p4 = reinterpret_cast<const float4 *>(p);
+        float4 *r4 = reinterpret_cast<float4 *>(r);
+        for (long long i = t0; i < n / 4; i += stride) {
+            const float4 a = y4[i], b = p4[i];
+            const float4 d = make_float4(__fsub_rn(a.x, b.x), __fsub_rn(a.y, b.y), __fsub_rn(a.z, b.z),
+                                         __fsub_rn(a.w, b.w));
+            r4[i] = d;
+            acc += (double)d.x * d.x + (double)d.y * d.y + (double)d.z * d.z + (double)d.w * d.w;
+        }
+        tail = (n / 4) * 4;
+    }
+    for (long long i = tail + t0; i < n; i += stride) {
+        const float d = __fsub_rn(y[i], p[i]);
+        r[i] = d;
+        acc += (double)d * d;
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    __shared__ double part[kItThreads / 32];
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < kItThreads / 32; ++w) s += part[w];
+        atomicAdd(loss, 0.5 * s);
+    }
+}
+
+// out = r * (float)(*s): the loss gradient times a device-side scale.
+__global__ void __launch_bounds__(kItThreads) scale_kernel(const float *__restrict__ r, const double *__restrict__ s,
+                                                           float *out, long long n, int vec) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const float c = (float)*s;
+    long long tail = 0;
+    if (vec) {
+        const float4 *r4 = reinterpret_cast<const float4 *>(r);
+        float4 *o4 = reinterpret_cast<float4 *>(out);
+        for (long long i = t0; i < n / 4; i += stride) {
+            const float4 a = r4[i];
+            o4[i] = make_float4(__fmul_rn(a.x, c), __fmul_rn(a.y, c), __fmul_rn(a.z, c), __fmul_rn(a.w, c));
+        }
+        tail = (n / 4) * 4;
+    }
+    for (long long i = tail + t0; i < n; i += stride) out[i] = __fmul_rn(r[i], c);
+}
+
+// Gradient step x = x - (step * g), two roundings (no fused multiply-add).
+__global__ void __launch_bounds__(kItThreads) gd_kernel(float *x, const float *__restrict__ g, long long n, float step,
+                                                        int vec) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    long long tail = 0;
+    if (vec) {
+        float4 *x4 = reinterpret_cast<float4 *>(x);
+        const float4 *g4 = reinterpret_cast<const float4 *>(g);
+        for (long long i = t0; i < n / 4; i += stride) {
+            const float4 a = x4[i], b = g4[i];
+            x4[i] = make_float4(__fsub_rn(a.x, __fmul_rn(step, b.x)), __fsub_rn(a.y, __fmul_rn(step, b.y)),
+                                __fsub_rn(a.z, __fmul_rn(step, b.z)), __fsub_rn(a.w, __fmul_rn(step, b.w)));
+        }
+        tail = (n / 4) * 4;
+    }
+    for (long long i = tail + t0; i < n; i += stride) x[i] = __fsub_rn(x[i], __fmul_rn(step, g[i]));
+}
+
 // Enough CTAs to fill the GPU (the loops stride over the rest).
 unsigned it_blocks(long long n) {
     static int sms = 0;
@@ -191,6 +266,31 @@ bp_status it_sart_update(float *x, const float *b, const float *s, long long n, 
     sart_kernel<<<it_blocks(n), kItThreads, 0, (cudaStream_t)stream>>>(x, b, s, n, lambda, nonneg, eps,
                                                                          a16(x) && a16(b) && a16(s));
     return it_done("it_sart_update launch");
+}
+
+bp_status it_ls_residual(const float *y, const float *p, float *r, long long n, double *loss, void *stream) {
+    if (n < 0 || !loss || (n > 0 && (!y || !p || !r)))
+        return fail(nullptr, BP_ERR_INVALID_ARG, "it_ls_residual: bad arguments");
+    cudaError_t e = cudaMemsetAsync(loss, 0, sizeof(double), (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "it_ls_residual: clear");
+    if (n == 0) return BP_OK;
+    ls_resid_kernel<<<it_blocks(n), kItThreads, 0, (cudaStream_t)stream>>>(y, p, r, n, loss,
+                                                                             a16(y) && a16(p) && a16(r));
+    return it_done("it_ls_residual launch");
+}
+
+bp_status it_scale(const float *r, const double *s, float *out, long long n, void *stream) {
+    if (n < 0 || !s || (n > 0 && (!r || !out))) return fail(nullptr, BP_ERR_INVALID_ARG, "it_scale: bad arguments");
+    if (n == 0) return BP_OK;
+    scale_kernel<<<it_blocks(n), kItThreads, 0, (cudaStream_t)stream>>>(r, s, out, n, a16(r) && a16(out));
+    return it_done("it_scale launch");
+}
+
+bp_status it_gd_step(float *x, const float *g, long long n, float step, void *stream) {
+    if (n < 0 || (n > 0 && (!x || !g))) return fail(nullptr, BP_ERR_INVALID_ARG, "it_gd_step: bad arguments");
+    if (n == 0) return BP_OK;
+    gd_kernel<<<it_blocks(n), kItThreads, 0, (cudaStream_t)stream>>>(x, g, n, step, a16(x) && a16(g));
+    return it_done("it_gd_step launch");
 }
 
 }  // extern "C"

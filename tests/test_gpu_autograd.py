@@ -122,3 +122,44 @@ def test_batched_least_squares_equals_single(setup):
         xb, _ = autograd.least_squares(ctx, p2, iters=5, L=L)
         x1, _ = autograd.least_squares(ctx, p2[1], iters=5, L=L)
         assert torch.allclose(xb[1], x1, rtol=1e-5, atol=1e-6 * x1.abs().max().item())
+
+
+def test_least_squares_elementwise_exact():
+    """The least-squares residual, loss, gradient scale and update against
+    their FP32 definitions (bit for bit; the loss's FP64 sum to 1e-12), with
+    ragged lengths (vector body and scalar tail) and an unaligned start."""
+    import ctypes
+
+    from paper_2104_13248_gb300 import _lib
+    lib = _lib.load()
+    P = lambda t: ctypes.c_void_p(t.data_ptr())
+    S = lambda: ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    g = torch.Generator(device="cuda").manual_seed(2)
+    for n in (1, 7, 4096 + 3):
+        for off in (0, 1):
+            base = torch.rand(n + 1, device="cuda", generator=g)
+            y = base[off:off + n]
+            p = torch.rand(n, device="cuda", generator=g)
+            r = torch.empty(n, device="cuda")
+            loss = torch.empty((), dtype=torch.float64, device="cuda")
+            _lib.check(lib.it_ls_residual(P(y), P(p), P(r), n, P(loss), S()))
+            torch.cuda.synchronize()
+            assert torch.equal(r, y - p)
+            ref = 0.5 * float(((y - p).double() ** 2).sum())
+            assert abs(float(loss) - ref) <= 1e-12 * max(ref, 1e-300)
+            s = torch.tensor(-1.7, dtype=torch.float64, device="cuda")
+            out = torch.empty(n, device="cuda")
+            _lib.check(lib.it_scale(P(r), P(s), P(out), n, S()))
+            torch.cuda.synchronize()
+            assert torch.equal(out, r * torch.tensor(-1.7, dtype=torch.float32, device="cuda"))
+            x = torch.rand(n, device="cuda", generator=g)
+            x2 = x.clone()
+            autograd.gd_step(x2, r, 0.37)
+            torch.cuda.synchronize()
+            assert torch.equal(x2, torch.sub(x, torch.mul(torch.tensor(0.37, device="cuda"), r)))
+    # the loss Function's gradient through autograd: g (y - p)
+    y = torch.rand(1000, device="cuda", generator=g, requires_grad=True)
+    p = torch.rand(1000, device="cuda", generator=g)
+    loss = autograd.ResidualLoss.apply(y, p)
+    loss.backward(torch.tensor(2.0, dtype=torch.float64, device="cuda"))
+    assert torch.equal(y.grad, (y.detach() - p) * torch.tensor(2.0, device="cuda"))
