@@ -48,6 +48,7 @@ def test_backproject_c1(c1):
     with api.bp_create(g) as ctx:
         vol = api.bp_backproject(ctx, torch.from_numpy(c1["q"]).cuda(), scale=scale).cpu().numpy()
         api.bp_device_status(ctx)
+    print(f"back-projection c1 rel err {rel(vol, ref):.2e}")
     assert rel(vol, ref) <= TOL32
 
 
