@@ -24,12 +24,17 @@
 //   - one thread issues them (tcgen05.mma kind::f16, M 128, K 16) and commits
 //     to an mbarrier, which every thread waits for (bounded) before the next
 //     chunk overwrites shared memory.
-// Two CTAs share an SM, so one's loads overlap the other's MMAs (the brick's
-// TMA is issued before the weight copies). A warp-specialised persistent
-// version with one CTA per SM and two stages was slower: its single producer
-// warp serialised the weight copies and the brick loads of every chunk.
+// In this per-tile kernel two CTAs share an SM, so one's loads overlap the
+// other's MMAs (the brick's TMA is issued before the weight copies).
 // Epilogue: each warp reads its 32 TMEM lanes (tcgen05.ld 32x32b) per row,
 // adds the bias, applies ReLU and stores Cout channels per voxel.
+//
+// The default for layers whose weights fit is the persistent kernel further
+// down (conv3d_fwd_tcp): one CTA per SM walking the tiles, resident weights,
+// a producer warp streaming 32-byte-swizzled bricks into two stages, an MMA
+// warp and four epilogue warps draining two TMEM accumulator sets. The
+// per-tile kernel remains for layers whose weights do not fit and when
+// cnn_set_tensor_path(2) forces it.
 #include <cuda.h>
 #include <cuda_bf16.h>
 

@@ -1,6 +1,8 @@
 // The one-channel input layer and the additive skip connections of the
-// few-view correction network, on the CUDA cores. The paper has no learned
-// component; these calls serve the few-view workload.
+// few-view correction network. The paper has no learned component; these
+// calls serve the few-view workload. The input layer's GEMM runs on the
+// tensor cores with mma.sync (its K dimension is the 27 taps); the skip
+// connections and the rest are element-wise passes on the CUDA cores.
 //
 //   stem_fwd_mma    y[v][co] = act(b[co] + sum_tap w[co][tap] bf16(x[v + tap]))
 //                   for a one-channel FP32 volume: a GEMM whose K dimension
