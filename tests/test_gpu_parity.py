@@ -447,3 +447,35 @@ def test_forward_project_ragged_phantom(c1, name):
     e = rel(fx, ref)
     print(f"fp {name} phantom rel err {e:.2e}")
     assert e <= TOL32
+
+
+# detector pixels per voxel (magnification x voxel / pitch): the u width of a
+# warp's 8 x 4 column patch grows with it, so these geometries run the
+# forward projector with each window width it is built for (17 .. 49 columns)
+WINDOW_RATIOS = [1.2, 1.8, 2.2, 3.0, 4.0]
+
+
+@pytest.mark.parametrize("ratio", WINDOW_RATIOS)
+def test_forward_project_window_widths(ratio):
+    rng = np.random.default_rng(int(ratio * 10))
+    sid, sdd, sx = 600.0, 900.0, 1.0
+    du = sdd / sid * sx / ratio
+    n_det = int(np.ceil(36 * sx * sdd / sid / du)) + 8
+    g = dict(sid=sid, sdd=sdd, np=9, angles=np.sort(rng.uniform(0, 2 * np.pi, 9)), nu=n_det, nv=n_det,
+             du=du, dv=du, u_off=0.3, v_off=-0.2, nx=33, ny=30, nz=34, sx=sx, sy=sx, sz=sx, ox=0.0, oy=0.0, oz=0.0)
+    P = oracle.matrices(g)
+    x = inputs.uniform_array(31, (g["nz"], g["ny"], g["nx"]), 0, 1).astype(np.float32)
+    q = inputs.uniform_array(32, (g["np"], g["nv"], g["nu"]), -1, 1).astype(np.float32)
+    ref = oracle.forward_project(P, x, g["nu"], g["nv"], 0.5)
+    with api.bp_create(g) as ctx:
+        xd = torch.from_numpy(x).cuda()
+        fx = api.fp_project(ctx, xd, scale=0.5)
+        bq = api.bp_backproject(ctx, torch.from_numpy(q).cuda(), scale=0.5)
+        api.bp_device_status(ctx)
+        lhs = torch.dot(bq.double().flatten(), xd.double().flatten()).item()
+        rhs = torch.dot(torch.from_numpy(q).cuda().double().flatten(), fx.double().flatten()).item()
+        norm = bq.double().norm().item() * float(np.linalg.norm(x))
+    e = rel(fx.cpu().numpy(), ref)
+    print(f"fp {ratio} px/voxel ({g['nu']}^2 detector) rel err {e:.2e}")
+    assert e <= TOL32
+    assert abs(lhs - rhs) <= 1e-6 * norm
