@@ -45,8 +45,9 @@ __device__ __forceinline__ unsigned f2bf(float a, float b) {
 __device__ __forceinline__ float round_bf16(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
 
 // CTA tile 64 (x) x 8 (y) x 2 (z) outputs. The haloed input tile (66 x 10 x 4
-// values, rounded to BF16) is staged in shared memory with all loads in
-// flight at once. The products run on the tensor cores (mma.sync m16n8k16,
+// values, rounded to BF16 once and kept as BF16 bits) is staged in shared
+// memory with all loads in flight at once; the A fragments are byte
+// permutes of those bits (no conversion per use). The products run on the tensor cores (mma.sync m16n8k16,
 // BF16 in, FP32 accumulation) as a GEMM with M = 16 x-consecutive voxels,
 // N = output channels and K = the 27 taps (zero-padded to 32): a thread's
 // A-fragment entries are single shared-memory loads at the tap offsets it
@@ -76,7 +77,7 @@ __global__ void __launch_bounds__(kStThreads)
 stem_fwd_mma(const float *__restrict__ x, const bf16 *__restrict__ w, const float *__restrict__ b,
              bf16 *__restrict__ y, int ycs, int ycoff, int D, int H, int W, int relu, int tx, int ty, int tz) {
     constexpr int NT = C / 8;   // n-tiles
-    __shared__ float xs[kStHalo];   // [HZ][HY][HX]
+    __shared__ unsigned short xs[kStHalo];   // [HZ][HY][HX], BF16 bits (rounded once when staged)
     long long r = blockIdx.x;
     const int x0 = (int)(r % tx) * kStTX;
     r /= tx;
@@ -125,14 +126,14 @@ stem_fwd_mma(const float *__restrict__ x, const bf16 *__restrict__ w, const floa
 #pragma unroll
     for (int k = 0; k < kStPer; ++k) {
         const int c = threadIdx.x + k * kStThreads;
-        if (c < kStHalo) xs[c] = round_bf16(v[k]);
+        if (c < kStHalo) xs[c] = __bfloat16_as_ushort(__float2bfloat16_rn(v[k]));
     }
     __syncthreads();
     // 64 tasks of 16 voxels: row (oz, oy) = task / 4, x segment 16 * (task % 4)
     for (int task = warp; task < kStTZ * kStTY * 4; task += kStThreads / 32) {
         const int row = task >> 2, xs0 = (task & 3) * 16;
         const int oz = row / kStTY, oy = row % kStTY;
-        const float *base = xs + (oz * kStHY + oy) * kStHX + xs0 + g;   // tap (0,0,0) of voxel xs0 + g
+        const unsigned short *base = xs + (oz * kStHY + oy) * kStHX + xs0 + g;   // tap (0,0,0) of voxel xs0 + g
         float acc[NT][4];
 #pragma unroll
         for (int j = 0; j < NT; ++j) {
@@ -143,18 +144,19 @@ stem_fwd_mma(const float *__restrict__ x, const bf16 *__restrict__ w, const floa
         }
 #pragma unroll
         for (int s2 = 0; s2 < 2; ++s2) {
-            float e[2][4];   // [row g / g + 8][slot]
+            unsigned e[2][4];   // [row g / g + 8][slot], BF16 bits
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 const int o = off[s2][q];
-                e[0][q] = o >= 0 ? base[o] : 0.0f;
-                e[1][q] = o >= 0 ? base[o + 8] : 0.0f;
+                e[0][q] = o >= 0 ? base[o] : 0u;
+                e[1][q] = o >= 0 ? base[o + 8] : 0u;
             }
+            // two BF16 values per register, the lower k in the low half
             unsigned a[4];
-            a[0] = pack_bf16x2(e[0][0], e[0][1]);   // row g, k = 2 t4, 2 t4 + 1
-            a[1] = pack_bf16x2(e[1][0], e[1][1]);   // row g + 8
-            a[2] = pack_bf16x2(e[0][2], e[0][3]);   // row g, k + 8
-            a[3] = pack_bf16x2(e[1][2], e[1][3]);   // row g + 8, k + 8
+            a[0] = __byte_perm(e[0][0], e[0][1], 0x5410);   // row g, k = 2 t4, 2 t4 + 1
+            a[1] = __byte_perm(e[1][0], e[1][1], 0x5410);   // row g + 8
+            a[2] = __byte_perm(e[0][2], e[0][3], 0x5410);   // row g, k + 8
+            a[3] = __byte_perm(e[1][2], e[1][3], 0x5410);   // row g + 8, k + 8
 #pragma unroll
             for (int j = 0; j < NT; ++j) mma16816(acc[j], a, bw[s2][j][0], bw[s2][j][1]);
         }
