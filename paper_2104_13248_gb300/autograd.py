@@ -76,7 +76,8 @@ class ResidualLoss(torch.autograd.Function):
     @staticmethod
     def backward(fctx, g: torch.Tensor):
         (r,) = fctx.saved_tensors
-        g = g.to(torch.float64).contiguous()
+        # the kernel reads the upstream gradient on the device
+        g = g.to(device=r.device, dtype=torch.float64).contiguous()
         out = torch.empty_like(r)
         _lib.check(_lib.load().it_scale(_p(r), _p(g), _p(out), r.numel(), _s()))
         return out, None
