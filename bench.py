@@ -248,6 +248,15 @@ def slab_parity(ctx, g, sample) -> dict:
     return out
 
 
+def bench_config(g, workload: str, world: int) -> dict:
+    """The line's config: the workload with its sizes (both arms print the same)."""
+    proj_gb = 4.0 * g["np"] * g["nv"] * g["nu"] / 1e9
+    return {"workload": f"{workload}: {g['nu']}x{g['nv']}x{g['np']} -> "
+                        f"{g['nx']}x{g['ny']}x{g['nz']}, FP32 projections, filter + back-projection",
+            "l2": "inputs larger than L2 (projections %.2f GB), no flush" % proj_gb,
+            "parallelism": "replicas" if world > 1 else "single-gpu"}
+
+
 def run_reference(args):
     """Reference arm: the FP64 CPU oracle timed on a bounded sample (rank 0 only)."""
     rank = int(os.environ.get("RANK", "0"))
@@ -281,7 +290,7 @@ def run_reference(args):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic",
-            "config": {"workload": args.workload, "sample": sample},
+            "config": bench_config(g, args.workload, int(os.environ.get("WORLD_SIZE", "1"))),
             "cpu_baseline": {"value": val, "unit": "GUPS", "cores": oracle.num_threads(), "kind": "oracle",
                              "sample": sample, "nproc": os.cpu_count(), "cpu_model": cpu_model()},
             "e2e": {"value": val, "unit": "GUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -709,11 +718,8 @@ def run_ours(args):
         "vs_baseline": None,
         "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": f"{args.workload}: {g['nu']}x{g['nv']}x{g['np']} -> "
-                               f"{g['nx']}x{g['ny']}x{g['nz']}, FP32 projections, filter + back-projection",
-                   "l2": "inputs larger than L2 (projections %.2f GB), no flush" % (raw.numel() * 4 / 1e9),
-                   "parallelism": "replicas" if world > 1 else "single-gpu",
-                   "plan": plan},
+        "config": bench_config(g, args.workload, world),
+        "plan": plan,
         "gpu_launches": 2 * K,
         "roofline": {"bound": "alu", "resource": "shared-memory taps (4 x 4 B per update at 128 B/clk/SM)",
                      "achieved": achieved, "peak": peak_gups, "unit": "GUPS",
