@@ -479,3 +479,27 @@ def test_forward_project_window_widths(ratio):
     print(f"fp {ratio} px/voxel ({g['nu']}^2 detector) rel err {e:.2e}")
     assert e <= TOL32
     assert abs(lhs - rhs) <= 1e-6 * norm
+
+
+@pytest.mark.parametrize("name,views", [("c2_fdk256", [0, 45, 117, 300]), ("c3_paper", [31, 400])])
+def test_full_size_forward_project(name, views):
+    """The forward projector at full volume and detector size, in the launch
+    configuration the benchmark times (the same tiles and window width; only
+    the number of views is cut), on a smooth phantom-like volume (a sum of
+    Gaussian blobs) against the oracle's scatter of every voxel."""
+    p = inputs.preset(name)
+    g = dict(p["geom"])
+    ang = oracle.default_angles(g["np"])[views]
+    g.update(np=len(views), angles=ang)
+    nz, ny, nx = g["nz"], g["ny"], g["nx"]
+    z, y, x = np.meshgrid(np.linspace(-1, 1, nz), np.linspace(-1, 1, ny), np.linspace(-1, 1, nx), indexing="ij")
+    vol = (np.exp(-((x - 0.2) ** 2 + y ** 2 + (z + 0.1) ** 2) / 0.2)
+           + 0.5 * np.exp(-((x + 0.3) ** 2 + (y - 0.25) ** 2 + z ** 2) / 0.05)).astype(np.float32)
+    P = oracle.matrices(g)
+    ref = oracle.forward_project(P, vol, g["nu"], g["nv"], 1.0)
+    with api.bp_create(g) as ctx:
+        fx = api.fp_project(ctx, torch.from_numpy(vol).cuda()).cpu().numpy()
+        api.bp_device_status(ctx)
+    e = rel(fx, ref)
+    print(f"full-size forward projection {name} views {views}: rel err {e:.2e}")
+    assert e <= TOL32
