@@ -4,7 +4,7 @@
 // footprints of the CTA tiles, and every call validates its arguments
 // before launching.
 #include "bp_internal.h"
-#include "filter_quad.h"
+#include "filter_ct.h"
 
 #include <algorithm>
 #include <atomic>
@@ -221,7 +221,7 @@ static void make_plan(bp_ctx *ctx) {
 // kernel (times dp and 1/N, natural order) and the N FFT twiddles.
 static bp_status make_filter_tables(bp_ctx *ctx) {
     const bp_geometry &g = ctx->g;
-    int n = quad_fft_size(g.nu), lg = 0;
+    int n = ct_fft_size(g.nu), lg = 0;
     ctx->fft_quad = n > 0;
     if (!ctx->fft_quad) {
         n = 1;
@@ -238,28 +238,29 @@ static bp_status make_filter_tables(bp_ctx *ctx) {
                : -1.0 / (M_PI * M_PI * (double)m * (double)m * dp * dp);
     // H[k] = h[0] + 2 sum_m h[m] cos(2 pi k m / N) (even kernel -> real spectrum),
     // times dp (the convolution's quadrature weight) and 1/N (inverse FFT)
+    std::vector<double> Hd(n);
     std::vector<float> Hf(n), tw(2 * (size_t)n);
     for (int k = 0; k < n; ++k) {
         double acc = h[0];
         for (int m = 1; m < g.nu; m += 2) acc += 2.0 * h[m] * std::cos(2.0 * M_PI * (double)((long long)k * m % n) / n);
-        Hf[k] = (float)(acc * dp / n);
+        Hd[k] = acc * dp / n;
+        Hf[k] = (float)Hd[k];
     }
     if (ctx->fft_quad) {
-        // four-row kernel: spectrum and twiddle angles duplicated for its two lanes
-        std::vector<float> H2(2 * (size_t)n), tw4(4 * (size_t)n);
-        for (int k = 0; k < n; ++k) {
-            H2[2 * k] = H2[2 * k + 1] = Hf[k];
-            const float c = (float)std::cos(2.0 * M_PI * k / n), sn = (float)std::sin(2.0 * M_PI * k / n);
-            tw4[4 * k] = tw4[4 * k + 1] = c;
-            tw4[4 * k + 2] = tw4[4 * k + 3] = sn;
-        }
-        cudaError_t e = dev_alloc(ctx, &ctx->d_H2, sizeof(float) * 2 * n);
+        // four-row kernel: spectrum (times sdd, the cosine weight's numerator) at
+        // the digit-reversed positions of its fused step, and twiddles per pass
+        std::vector<double> Hs(n);
+        for (int k = 0; k < n; ++k) Hs[k] = Hd[k] * g.sdd;
+        const int ntw = ct_twiddle_count(n);
+        std::vector<float> cH(2 * (size_t)n), ctw(4 * (size_t)(ntw > 0 ? ntw : 1));
+        ct_tables(n, Hs.data(), cH.data(), ctw.data());
+        cudaError_t e = dev_alloc(ctx, &ctx->d_ctH, sizeof(float) * 2 * n);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "filter spectrum");
-        e = dev_alloc(ctx, &ctx->d_tw4, sizeof(float) * 4 * n);
+        e = dev_alloc(ctx, &ctx->d_cttw, sizeof(float) * ctw.size());
         if (e != cudaSuccess) return cuda_fail(ctx, e, "filter twiddles");
-        e = cudaMemcpy(ctx->d_H2, H2.data(), sizeof(float) * 2 * n, cudaMemcpyHostToDevice);
+        e = cudaMemcpy(ctx->d_ctH, cH.data(), sizeof(float) * 2 * n, cudaMemcpyHostToDevice);
         if (e == cudaSuccess)
-            e = cudaMemcpy(ctx->d_tw4, tw4.data(), sizeof(float) * 4 * n, cudaMemcpyHostToDevice);
+            e = cudaMemcpy(ctx->d_cttw, ctw.data(), sizeof(float) * ctw.size(), cudaMemcpyHostToDevice);
         return e == cudaSuccess ? BP_OK : cuda_fail(ctx, e, "filter tables upload");
     }
     for (int k = 0; k < n; ++k) {
@@ -582,8 +583,8 @@ void bp_destroy(bp_ctx *ctx) {
     dev_free(ctx->d_err);
     dev_free(ctx->d_H);
     dev_free(ctx->d_tw);
-    dev_free(ctx->d_H2);
-    dev_free(ctx->d_tw4);
+    dev_free(ctx->d_ctH);
+    dev_free(ctx->d_cttw);
     dev_free(ctx->d_phcoef);
     delete ctx;
 }

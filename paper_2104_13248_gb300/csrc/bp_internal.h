@@ -75,9 +75,9 @@ struct bp_ctx {
     int fft_n = 0, fft_log2 = 0;
     float *d_H = nullptr;       // [fft_n] real spectrum (times dp, times 1/N), natural order
     float2 *d_tw = nullptr;     // [fft_n] twiddles exp(-2 pi i k / N)
-    int fft_quad = 0;           // 1: four-row kernel (tables d_H2, d_tw4), 0: two-row kernel (d_H, d_tw)
-    void *d_H2 = nullptr;       // [fft_n] float2 (H, H)
-    void *d_tw4 = nullptr;      // [fft_n] float4 (cos, cos, sin, sin) of 2 pi k / N
+    int fft_quad = 0;           // 1: four-row kernel (tables d_ctH, d_cttw), 0: two-row kernel (d_H, d_tw)
+    void *d_ctH = nullptr;      // [16][fft_n / 16] float2 (H sdd, H sdd) at the fused step's positions
+    void *d_cttw = nullptr;     // [ct_twiddle_count] float4 (cos, cos, sin, sin) per pass and (k, o)
     float *d_phcoef = nullptr;  // [np][256][20] phantom coefficients (input generation)
     // launch plan
     bp::Plan plan{};

@@ -2,25 +2,27 @@
 // cosine weight, then the linear convolution of every detector row with the
 // discrete Ram-Lak kernel, done as a zero-padded FFT convolution in shared
 // memory. Rows of up to 5120 pixels go to the four-row kernel of
-// filter_quad.cuh; this file holds the dispatch and, for longer rows
-// (N = 16384), a two-row kernel with one float2 per point. Two real rows travel as the real and imaginary parts of one
+// filter_ct.cuh; this file holds the dispatch, the host tables of that
+// kernel and, for longer rows (N = 16384), a two-row kernel with one float2
+// per point. Two real rows travel as the real and imaginary parts of one
 // complex FFT: the kernel's spectrum is real and even, so the product keeps
 // the two rows apart.
 //
-// The FFT is a Stockham autosort transform with radix-16 passes (a last pass
-// of radix 2/4/8 when log2 N is not a multiple of 4): every thread holds R
-// points of one butterfly group in registers, applies the inter-pass
-// twiddles from a table, runs an R-point DFT in registers and writes the
-// results to their sorted positions, so each pass reads and writes shared
-// memory once and the output comes out in natural order. The first forward
-// pass reads the projections from global memory (with the cosine weight);
-// the last forward pass multiplies by the spectrum of the kernel (which
-// carries dp and the 1/N of the inverse); the last inverse pass writes the
-// first nu samples of each row to global memory.
+// The two-row kernel's FFT is a Stockham autosort transform with radix-16
+// passes (a last pass of radix 2/4/8 when log2 N is not a multiple of 4):
+// every thread holds R points of one butterfly group in registers, applies
+// the inter-pass twiddles from a table, runs an R-point DFT in registers and
+// writes the results to their sorted positions, so each pass reads and
+// writes shared memory once and the output comes out in natural order. The
+// first forward pass reads the projections from global memory (with the
+// cosine weight); the last forward pass multiplies by the spectrum of the
+// kernel (which carries dp and the 1/N of the inverse); the last inverse
+// pass writes the first nu samples of each row to global memory.
+#include <cmath>
 #include <cstdint>
 
 #include "bp_internal.h"
-#include "filter_quad.h"
+#include "filter_ct.cuh"
 
 namespace bp {
 
@@ -337,7 +339,38 @@ static cudaError_t launch_lg(int lg, const FilterArgs &a, unsigned nblk, int sme
 #undef BP_FILTER_CASE
 }
 
-int quad_fft_size(int nu) {
+int ct_twiddle_count(int N) { return fct::plan_tw_offset(N, fct::plan_count(N) - 1); }
+
+// Spectrum at the fused step's slots, Ht[k2][g] = H[f(16 g + k2)], with f the
+// frequency of a digit-reversed position (digit k_p = (pos mod S_p) / T_p,
+// weight R_0 ... R_(p-1)); twiddles of pass p at (k - 1) T_p + o, angle
+// 2 pi o k / S_p.
+void ct_tables(int N, const double *H, float *Ht, float *tw) {
+    const int C = fct::plan_count(N), G = N / 16;
+    for (int pos = 0; pos < N; ++pos) {
+        long long f = 0, w = 1;
+        for (int p = 0; p < C; ++p) {
+            const int S = fct::plan_span(N, p), T = fct::plan_stride(N, p);
+            f += (long long)((pos % S) / T) * w;
+            w *= fct::plan_radix(N, p);
+        }
+        const int g = pos / 16, k2 = pos % 16;
+        Ht[2 * ((size_t)k2 * G + g)] = Ht[2 * ((size_t)k2 * G + g) + 1] = (float)H[f];
+    }
+    for (int p = 0; p + 1 < C; ++p) {
+        const int S = fct::plan_span(N, p), T = fct::plan_stride(N, p), R = fct::plan_radix(N, p);
+        const int off = fct::plan_tw_offset(N, p);
+        for (int k = 1; k < R; ++k)
+            for (int o = 0; o < T; ++o) {
+                const double ang = 2.0 * M_PI * (double)((long long)o * k % S) / S;
+                float *e = tw + 4 * ((size_t)off + (size_t)(k - 1) * T + o);
+                e[0] = e[1] = (float)std::cos(ang);
+                e[2] = e[3] = (float)std::sin(ang);
+            }
+    }
+}
+
+int ct_fft_size(int nu) {
     static const int sizes[] = {32, 64, 128, 256, 512, 1024, 1280, 2048, 2560, 4096, 5120, 8192, 10240};
     for (int n : sizes)
         if (n >= 2 * nu - 1) return n;
@@ -349,39 +382,38 @@ bp_status launch_filter(bp_ctx *ctx, const float *proj, void *out, bp_dtype out_
     const bp_geometry &g = ctx->g;
     const int N = ctx->fft_n;
     if (ctx->fft_quad) {
-        QArgs q;
-        q.in = proj;
-        q.out = out;
-        q.nrows = n_views_total * ctx->nv;
-        q.nu = ctx->nu;
-        q.nv = ctx->nv;
-        q.out_f16 = out_t == BP_F16;
-        q.in_vec = (ctx->nu % 4 == 0) && (reinterpret_cast<uintptr_t>(proj) % 16 == 0);
-        q.H2 = reinterpret_cast<const float2 *>(ctx->d_H2);
-        q.tw4 = reinterpret_cast<const ulonglong2 *>(ctx->d_tw4);
-        q.sdd = (float)g.sdd;
-        q.du = (float)g.du;
-        q.dv = (float)g.dv;
-        q.cu = (float)(0.5 * (g.nu - 1) + g.u_off_px);
-        q.cv = (float)(0.5 * (g.nv - 1) + g.v_off_px);
+        CtArgs c;
+        c.in = proj;
+        c.out = out;
+        c.nrows = n_views_total * ctx->nv;
+        c.nu = ctx->nu;
+        c.nv = ctx->nv;
+        c.out_f16 = out_t == BP_F16;
+        c.Ht = reinterpret_cast<const float2 *>(ctx->d_ctH);
+        c.tw = reinterpret_cast<const ulonglong2 *>(ctx->d_cttw);
+        c.sdd2 = (float)(g.sdd * g.sdd);
+        c.du = (float)g.du;
+        c.dv = (float)g.dv;
+        c.cu = (float)(0.5 * (g.nu - 1) + g.u_off_px);
+        c.cv = (float)(0.5 * (g.nv - 1) + g.v_off_px);
         cudaError_t e;
         switch (N) {
-            case 32: e = launch_quad<32>(q, st); break;
-            case 64: e = launch_quad<64>(q, st); break;
-            case 128: e = launch_quad<128>(q, st); break;
-            case 256: e = launch_quad<256>(q, st); break;
-            case 512: e = launch_quad<512>(q, st); break;
-            case 1024: e = launch_quad<1024>(q, st); break;
-            case 1280: e = launch_quad<1280>(q, st); break;
-            case 2048: e = launch_quad<2048>(q, st); break;
-            case 2560: e = launch_quad<2560>(q, st); break;
-            case 4096: e = launch_quad<4096>(q, st); break;
-            case 5120: e = launch_quad<5120>(q, st); break;
-            case 8192: e = launch_quad<8192>(q, st); break;
-            case 10240: e = launch_quad<10240>(q, st); break;
+            case 32: e = launch_ct<32>(c, st); break;
+            case 64: e = launch_ct<64>(c, st); break;
+            case 128: e = launch_ct<128>(c, st); break;
+            case 256: e = launch_ct<256>(c, st); break;
+            case 512: e = launch_ct<512>(c, st); break;
+            case 1024: e = launch_ct<1024>(c, st); break;
+            case 1280: e = launch_ct<1280>(c, st); break;
+            case 2048: e = launch_ct<2048>(c, st); break;
+            case 2560: e = launch_ct<2560>(c, st); break;
+            case 4096: e = launch_ct<4096>(c, st); break;
+            case 5120: e = launch_ct<5120>(c, st); break;
+            case 8192: e = launch_ct<8192>(c, st); break;
+            case 10240: e = launch_ct<10240>(c, st); break;
             default: return fail(ctx, BP_ERR_UNSUPPORTED, "bp_filter: no transform of this size");
         }
-        return e == cudaSuccess ? BP_OK : cuda_fail(ctx, e, "ramp_filter_quad launch");
+        return e == cudaSuccess ? BP_OK : cuda_fail(ctx, e, "ramp_filter_ct launch");
     }
     if (ctx->fft_log2 != 14)
         return fail(ctx, BP_ERR_UNSUPPORTED, "bp_filter: detector rows longer than 8192 pixels");
