@@ -158,6 +158,25 @@ __device__ __forceinline__ unsigned long long global_ns() {
     return t;
 }
 
+// try_wait with a suspend-time hint: a thread whose phase is not complete
+// sleeps until it completes or hint_ns passes, instead of polling (a polling
+// producer warp takes issue slots from the consumer warps beside it).
+#ifndef BP_WAIT_HINT_NS
+#define BP_WAIT_HINT_NS 20000
+#endif
+__device__ __forceinline__ bool mbar_try_wait_sleep(unsigned long long *bar, unsigned parity,
+                                                    unsigned hint_ns) {
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity), "r"(hint_ns)
+        : "memory");
+    return ok != 0;
+}
+
 // Wait for the phase with the given parity; gives up after timeout_ns and
 // returns false (the caller records DEV_ERR_TIMEOUT and leaves its loop).
 __device__ __forceinline__ bool mbar_wait_bounded(unsigned long long *bar, unsigned parity,
@@ -165,8 +184,7 @@ __device__ __forceinline__ bool mbar_wait_bounded(unsigned long long *bar, unsig
     if (mbar_try_wait(bar, parity)) return true;
     unsigned long long t0 = global_ns();
     while (true) {
-        for (int it = 0; it < 64; ++it)
-            if (mbar_try_wait(bar, parity)) return true;
+        if (mbar_try_wait_sleep(bar, parity, BP_WAIT_HINT_NS)) return true;
         if (global_ns() - t0 > timeout_ns) return false;
     }
 }
