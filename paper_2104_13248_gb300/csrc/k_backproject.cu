@@ -65,17 +65,33 @@ __device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) {
     asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
     return r;
 }
-__device__ __forceinline__ f2 sub2(f2 a, f2 b) {
-    f2 r;
-    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-    return r;
-}
 __device__ __forceinline__ f2 add2_rd(f2 a, f2 b) {
     f2 r;
     asm("add.rm.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
     return r;
 }
 
+// Shared-memory load at a 32-bit shared address plus a compile-time byte
+// offset. The tap addresses are formed in 32-bit arithmetic (one IMAD per
+// tap row): pointer arithmetic on the staged box went through 64-bit
+// generic addresses, several integer instructions per tap row.
+template <int OFF>
+__device__ __forceinline__ float lds32(unsigned a) {
+    float v;
+    asm volatile("ld.shared.f32 %0, [%1+%2];" : "=f"(v) : "r"(a), "n"(OFF));
+    return v;
+}
+
+__device__ __forceinline__ f2 mul2(f2 a, f2 b) {
+    f2 r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f2 add2(f2 a, f2 b) {
+    f2 r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
 // Per (column, view) quantities of the z-column update: the 1/W^2 weight,
 // the staged-box column cu and u fraction fu, v at the tile's first slice
 // and its step per slice. Returns false (and flags the device error word)
@@ -132,30 +148,37 @@ __device__ __forceinline__ void accumulate_scalar(const T *__restrict__ tile, co
     }
 }
 
-// The same arithmetic on voxel pairs (kk, kk+1) with f32x2 instructions:
-// identical per-lane results, about 11 instructions per voxel instead of 17.
+// The same sampling on voxel pairs (kk, kk+1) with f32x2 instructions, the
+// weights written without subtraction: (1 - fu) wt and fu wt on the two
+// columns, then acc + (1 - fv) s0 + fv s1 (equal to the scalar form up to
+// rounding).
+// tile_s: shared address of the staged box. The row of voxel v is the bit
+// pattern of v + 1.5 * 2^23 (rounded down) minus that of 1.5 * 2^23; the
+// constant is folded into the base (unsigned arithmetic, exact mod 2^32).
 template <int TK, int BU>
-__device__ __forceinline__ void accumulate_pairs(const float *__restrict__ tile, const ColView &c,
-                                                 f2 *acc2) {
-    const float *base = tile + c.cu;
-    const f2 M2 = pk(kMagic, kMagic), FU = pk(c.fu, c.fu), WT = pk(c.wt, c.wt);
+__device__ __forceinline__ void accumulate_pairs(unsigned tile_s, const ColView &c, f2 *acc2) {
+    constexpr unsigned kRow = BU * 4u;
+    const unsigned base = tile_s + 4u * (unsigned)c.cu - (unsigned)kMagicBits * kRow;
+    // subtraction-free weights (see accumulate_sym_pairs): (1 - fu) wt and fu wt
+    // on the two columns, acc + (1 - fv) s0 + fv s1 as two FMAs
+    const float gu = 1.0f - c.fu;
+    const f2 M2 = pk(kMagic, kMagic), GUW = pk(c.wt * gu, c.wt * gu), FUW = pk(c.wt * c.fu, c.wt * c.fu);
+    const f2 NM2 = pk(-kMagic, -kMagic), N1 = pk(-1.0f, -1.0f), ONE = pk(1.0f, 1.0f);
 #pragma unroll
     for (int m = 0; m < TK / 2; ++m) {
         const float va = fmaf((float)(2 * m), c.dv, c.v0);
         const float vb = fmaf((float)(2 * m + 1), c.dv, c.v0);
         const f2 V = pk(va, vb);
         const f2 TV = add2_rd(V, M2);
-        const f2 FV = sub2(V, sub2(TV, M2));
+        const f2 FV = fma2(add2(TV, NM2), N1, V);   // v - floor(v), exact
         float ta, tb;
         upk(TV, ta, tb);
-        const float *pa = base + (__float_as_int(ta) - kMagicBits) * BU;
-        const float *pb = base + (__float_as_int(tb) - kMagicBits) * BU;
-        const f2 Q00 = pk(pa[0], pb[0]), Q01 = pk(pa[1], pb[1]);
-        const f2 Q10 = pk(pa[BU], pb[BU]), Q11 = pk(pa[BU + 1], pb[BU + 1]);
-        const f2 S0 = fma2(FU, sub2(Q01, Q00), Q00);
-        const f2 S1 = fma2(FU, sub2(Q11, Q10), Q10);
-        const f2 VAL = fma2(FV, sub2(S1, S0), S0);
-        acc2[m] = fma2(WT, VAL, acc2[m]);
+        const unsigned pa = base + __float_as_uint(ta) * kRow, pb = base + __float_as_uint(tb) * kRow;
+        const f2 Q00 = pk(lds32<0>(pa), lds32<0>(pb)), Q01 = pk(lds32<4>(pa), lds32<4>(pb));
+        const f2 Q10 = pk(lds32<kRow>(pa), lds32<kRow>(pb)), Q11 = pk(lds32<kRow + 4>(pa), lds32<kRow + 4>(pb));
+        const f2 GV = fma2(FV, N1, ONE);
+        const f2 S0 = fma2(FUW, Q01, mul2(GUW, Q00)), S1 = fma2(FUW, Q11, mul2(GUW, Q10));
+        acc2[m] = fma2(FV, S1, fma2(GV, S0, acc2[m]));
     }
 }
 
@@ -187,45 +210,47 @@ __device__ __forceinline__ void store_column(float *__restrict__ vol, const floa
 // ---------------------------------------------------------------------------
 constexpr int kTH = 16;   // lower voxels per thread
 
-// Written with the float2 pair intrinsics (__ffma2_rn, __fadd2_rn / _rd;
-// subtraction as addition of the negated pair, exact) for the taps and
-// lerps, while the accumulators stay 64-bit: measured on c3, 1774 GUPS
-// against 1750 with inline f32x2 assembly throughout and 1754 with float2
-// accumulators as well.
+// f32x2 pair arithmetic on voxels (k, k+1) and their mirrors, 64-bit
+// accumulators, no subtraction in the weights (1825 GUPS on c3 against 1774
+// for the lerps q0 + f (q1 - q0), whose packed subtractions cost integer
+// sign flips).
 template <int BU>
-__device__ __forceinline__ void accumulate_sym_pairs(const float *__restrict__ lo,
-                                                     const float *__restrict__ hi_top, const ColView &c,
+__device__ __forceinline__ void accumulate_sym_pairs(unsigned lo_s, unsigned hi_s, const ColView &c,
                                                      f2 *acc_lo, f2 *acc_hi) {
-    // lo = lower box + c.cu; hi_top = mirrored box + (BV-1)*BU + c.cu
-    const float2 M2 = make_float2(kMagic, kMagic), NM2 = make_float2(-kMagic, -kMagic);
-    const float2 FU = make_float2(c.fu, c.fu), WT = make_float2(c.wt, c.wt);
-    const float2 DV2 = make_float2(c.dv, c.dv), V02 = make_float2(c.v0, c.v0);
+    // lo_s = shared address of the lower box + 4 c.cu; hi_s = of the mirrored
+    // box + (BV-1) rows + 4 c.cu. The magic constant of the row index is
+    // folded into both bases (unsigned arithmetic, exact mod 2^32).
+    constexpr unsigned kRow = BU * 4u;
+    const unsigned lo_m = lo_s - (unsigned)kMagicBits * kRow, hi_m = hi_s + (unsigned)kMagicBits * kRow;
+    // Weights without subtractions (a packed subtraction costs two integer
+    // sign flips): each u-lerp is (1 - fu) wt q0 + fu wt q1 with the view
+    // weight wt folded into both, and the v-lerp is two FMAs into the
+    // accumulator, acc + (1 - fv) s0 + fv s1.
+    const float gu = 1.0f - c.fu;
+    const f2 GUW = pk(c.wt * gu, c.wt * gu), FUW = pk(c.wt * c.fu, c.wt * c.fu);
+    const f2 M2 = pk(kMagic, kMagic), NM2 = pk(-kMagic, -kMagic), N1 = pk(-1.0f, -1.0f), ONE = pk(1.0f, 1.0f);
+    const f2 DV2 = pk(c.dv, c.dv), V02 = pk(c.v0, c.v0);
 #pragma unroll
     for (int m = 0; m < kTH / 2; ++m) {
-        const float2 V = __ffma2_rn(make_float2((float)(2 * m), (float)(2 * m + 1)), DV2, V02);
-        const float2 TV = __fadd2_rd(V, M2);
-        const float2 FL = __fadd2_rn(TV, NM2);
-        const float2 FV = __fadd2_rn(V, make_float2(-FL.x, -FL.y));
-        const int ra = __float_as_int(TV.x) - kMagicBits, rb = __float_as_int(TV.y) - kMagicBits;
-        const float *pa = lo + ra * BU, *pb = lo + rb * BU;
-        const float2 Q00 = make_float2(pa[0], pb[0]), Q01 = make_float2(pa[1], pb[1]);
-        const float2 Q10 = make_float2(pa[BU], pb[BU]), Q11 = make_float2(pa[BU + 1], pb[BU + 1]);
-        const float2 S0 = __ffma2_rn(FU, __fadd2_rn(Q01, make_float2(-Q00.x, -Q00.y)), Q00);
-        const float2 S1 = __ffma2_rn(FU, __fadd2_rn(Q11, make_float2(-Q10.x, -Q10.y)), Q10);
-        float2 al;
-        upk(acc_lo[m], al.x, al.y);
-        al = __ffma2_rn(WT, __ffma2_rn(FV, __fadd2_rn(S1, make_float2(-S0.x, -S0.y)), S0), al);
-        acc_lo[m] = pk(al.x, al.y);
+        const f2 V = fma2(pk((float)(2 * m), (float)(2 * m + 1)), DV2, V02);
+        const f2 TV = add2_rd(V, M2);
+        const f2 FV = fma2(add2(TV, NM2), N1, V);   // v - floor(v), exact
+        const f2 GV = fma2(FV, N1, ONE);
+        float tvx, tvy;
+        upk(TV, tvx, tvy);
+        const unsigned ta = __float_as_uint(tvx), tb = __float_as_uint(tvy);
+        const unsigned pa = lo_m + ta * kRow, pb = lo_m + tb * kRow;
+        const f2 Q00 = pk(lds32<0>(pa), lds32<0>(pb)), Q01 = pk(lds32<4>(pa), lds32<4>(pb));
+        const f2 Q10 = pk(lds32<kRow>(pa), lds32<kRow>(pb)), Q11 = pk(lds32<kRow + 4>(pa), lds32<kRow + 4>(pb));
+        const f2 S0 = fma2(FUW, Q01, mul2(GUW, Q00)), S1 = fma2(FUW, Q11, mul2(GUW, Q10));
+        acc_lo[m] = fma2(FV, S1, fma2(GV, S0, acc_lo[m]));
         // mirror: row BV-1-r (weight 1-f) and the row above it, BV-2-r (weight f)
-        const float *qa = hi_top - ra * BU, *qb = hi_top - rb * BU;
-        const float2 R00 = make_float2(qa[0], qb[0]), R01 = make_float2(qa[1], qb[1]);
-        const float2 R10 = make_float2(qa[-BU], qb[-BU]), R11 = make_float2(qa[1 - BU], qb[1 - BU]);
-        const float2 T0 = __ffma2_rn(FU, __fadd2_rn(R01, make_float2(-R00.x, -R00.y)), R00);
-        const float2 T1 = __ffma2_rn(FU, __fadd2_rn(R11, make_float2(-R10.x, -R10.y)), R10);
-        float2 ah;
-        upk(acc_hi[m], ah.x, ah.y);
-        ah = __ffma2_rn(WT, __ffma2_rn(FV, __fadd2_rn(T1, make_float2(-T0.x, -T0.y)), T0), ah);
-        acc_hi[m] = pk(ah.x, ah.y);
+        const unsigned qa = hi_m - ta * kRow, qb = hi_m - tb * kRow;
+        const f2 R00 = pk(lds32<0>(qa), lds32<0>(qb)), R01 = pk(lds32<4>(qa), lds32<4>(qb));
+        const f2 R10 = pk(lds32<-(int)kRow>(qa), lds32<-(int)kRow>(qb));
+        const f2 R11 = pk(lds32<4 - (int)kRow>(qa), lds32<4 - (int)kRow>(qb));
+        const f2 T0 = fma2(FUW, R01, mul2(GUW, R00)), T1 = fma2(FUW, R11, mul2(GUW, R10));
+        acc_hi[m] = fma2(FV, T1, fma2(GV, T0, acc_hi[m]));
     }
 }
 
@@ -369,7 +394,7 @@ bp_zcol_tma(const __grid_constant__ CUtensorMap tmap, const double *__restrict__
                     const T *tile = reinterpret_cast<const T *>(stages + slot * sbytes);
                     if constexpr (kPairs) {
                         if (ez == TK) {
-                            accumulate_pairs<TK, BU>(tile, cv, acc2);
+                            accumulate_pairs<TK, BU>(smem_addr(tile), cv, acc2);
                         } else {
                             float tmp[TK];
 #pragma unroll
@@ -505,7 +530,7 @@ bp_zsym_tma(const __grid_constant__ CUtensorMap tmap, const double *__restrict__
                     const float *hi_top = reinterpret_cast<const float *>(stages + slot * sbytes + half) +
                                           (bv - 1) * BU + cv.cu;
                     if (ez == kTH) {
-                        accumulate_sym_pairs<BU>(lo, hi_top, cv, acc_lo, acc_hi);
+                        accumulate_sym_pairs<BU>(smem_addr(lo), smem_addr(hi_top), cv, acc_lo, acc_hi);
                     } else {
                         float tl[kTH], th[kTH];
 #pragma unroll
