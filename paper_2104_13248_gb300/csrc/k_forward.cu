@@ -50,7 +50,7 @@ struct FpWin {
 // patch, written by the threads owning the columns and read by every lane.
 struct __align__(16) FpPair {
     float2 v0, dv;   // v of the first voxel and per voxel (box-relative)
-    float2 wt, fu;   // 1 / W^2 (0: a column without voxels), u fraction
+    float2 wgu, wfu; // column weights (1 - fu) / W^2 and fu / W^2 (0: a column without voxels)
 };
 // beside it, per pair: the window columns times 33 (int2)
 
@@ -141,23 +141,26 @@ __device__ __forceinline__ void fp_flush(const float *win, float *img, int nu, i
 // v, its floor and fraction for both columns as f32x2 pairs (each lane of a
 // pair computed exactly as the scalar back-projector does), then the value
 // times scale / W^2 split between rows floor(v) and floor(v) + 1.
+// The weights are the back-projector's: (1 - fu) / W^2 and fu / W^2 on the
+// two columns (from the record), 1 - fv and fv on the two rows. No packed
+// subtraction (each costs integer sign flips): fv = fma(floor(v), -1, v),
+// and the row shares as a1 = fv x, a0 = fma(a1, -1, x).
 struct FpTaps {
-    float2 fu, gu, a0, a1;   // u fraction, 1 - fu, (1 - fv) val, fv val
+    float2 fu, gu, a0, a1;   // wfu, wgu (column weights), (1 - fv) x, fv x
     int ra, rb;              // window rows floor(v) - lane base (columns 2p, 2p+1)
 };
 
 __device__ __forceinline__ FpTaps fp_taps(const FpPair &pr, float2 x, float2 fl2, int tb) {
     const float2 M2 = make_float2(kMagic, kMagic), NM2 = make_float2(-kMagic, -kMagic);
+    const float2 N1 = make_float2(-1.0f, -1.0f);
     const float2 V = __ffma2_rn(fl2, pr.dv, pr.v0);
     const float2 TV = __fadd2_rd(V, M2);
-    const float2 FL = __fadd2_rn(TV, NM2);
-    const float2 FV = __fadd2_rn(V, make_float2(-FL.x, -FL.y));
-    const float2 VAL = __fmul2_rn(pr.wt, x);
+    const float2 FV = __ffma2_rn(__fadd2_rn(TV, NM2), N1, V);   // v - floor(v), exact
     FpTaps t;
-    t.a1 = __fmul2_rn(FV, VAL);
-    t.a0 = __fadd2_rn(VAL, make_float2(-t.a1.x, -t.a1.y));
-    t.fu = pr.fu;
-    t.gu = __fadd2_rn(make_float2(1.0f, 1.0f), make_float2(-pr.fu.x, -pr.fu.y));
+    t.a1 = __fmul2_rn(FV, x);
+    t.a0 = __ffma2_rn(t.a1, N1, x);
+    t.fu = pr.wfu;
+    t.gu = pr.wgu;
     t.ra = __float_as_int(TV.x) - tb;
     t.rb = __float_as_int(TV.y) - tb;
     return t;
@@ -276,8 +279,8 @@ fp_zwin(const float *__restrict__ vol, const double *__restrict__ P, int nviews,
             const int cwin = cok ? cu - uo : 0;
             pf[0] = cok ? cv0 : v0min;
             pf[2] = cok ? cdv : dvmin;
-            pf[4] = cok ? cwt : 0.0f;
-            pf[6] = cok ? cfu : 0.0f;
+            pf[4] = cok ? cwt * (1.0f - cfu) : 0.0f;
+            pf[6] = cok ? cwt * cfu : 0.0f;
             reinterpret_cast<int *>(pcw)[lane] = cwin * kFpColPitch;
             __syncwarp();
 
