@@ -551,7 +551,7 @@ def learned_block() -> dict:
     from paper_2104_13248_gb300 import learned
     t0 = time.perf_counter()
     try:
-        r = learned.run(steps=4000, lr=5e-4, log_every=0)
+        r = learned.run(steps=16000, lr=5e-4, log_every=0)
     except Exception as e:   # the line keeps the back-projection numbers either way
         return {"error": f"{type(e).__name__}: {e}"}
     keys = ("rmse_few_view", "rmse_few_view_plus_net", "rmse_ratio", "ms_full_view_fdk", "ms_few_view_fdk",

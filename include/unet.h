@@ -192,6 +192,22 @@ bp_status cnn_head1_backward(const void *x, int x_cstride, const float *w, const
                              int dx_cstride, float *dw, float *db, long long nvox, int cin,
                              void *stream);
 
+/* Inference of the network's last step when no convolution follows the
+ * last skip (no counterpart in the paper, whose method has no network):
+ * cnn_upsample2_add_forward into a temporary and cnn_head1_forward on it,
+ * in one pass and bit for bit their result, the full-resolution sum never
+ * written:
+ *   a[v][ci] = bf16(up(x)[v][ci] + skip[v][ci]),
+ *   out[v] = res[v] + b[0] + sum_ci w[ci] a[v][ci].
+ * x BF16 [n][d][h][wd][c] (dense, coarse), skip BF16 [n][2d][2h][2wd]
+ * [s_cstride] (channels s_coff ..), w FP32 [c], b FP32 [1] (may be NULL),
+ * res and out FP32 [n][2d][2h][2wd] (res may be NULL). c a multiple of 8 up
+ * to 32; s_cstride and s_coff multiples of 8; x and skip 16-byte aligned.
+ * BP_ERR_INVALID_ARG on bad arguments. */
+bp_status cnn_upsample2_add_head1_forward(const void *x, const void *skip, int s_cstride, int s_coff,
+                                          const float *w, const float *b, const float *res, float *out, int n,
+                                          int d, int h, int wd, int c, void *stream);
+
 /* Mean-square error: g = 2 (p - t) / n (FP32), and sum (p - t)^2 added
  * into loss[0] (FP32, caller zeroes it). */
 bp_status cnn_mse(const float *p, const float *t, float *g, float *loss, long long n, void *stream);

@@ -82,6 +82,7 @@ PROTOTYPES = {
     "cnn_head1_forward": (_i, [_vp, _i, _vp, _vp, _vp, _vp, _ll, _i, _vp]),
     "cnn_head1_backward": (_i, [_vp, _i, _vp, _vp, _vp, _i, _vp, _vp, _ll, _i, _vp]),
     "cnn_upsample2_add_forward": (_i, [_vp, _vp, _i, _i, _vp, _i, _i, _i, _i, _i, _i, _i, _vp]),
+    "cnn_upsample2_add_head1_forward": (_i, [_vp, _vp, _i, _i, _vp, _vp, _vp, _vp, _i, _i, _i, _i, _i, _vp]),
     "cnn_mse": (_i, [_vp, _vp, _vp, _vp, _ll, _vp]),
     "cnn_adam": (_i, [_vp, _vp, _vp, _vp, _vp, _ll, _f, _f, _f, _f, _i, _vp]),
     "cnn_set_tensor_path": (_i, [_i]),

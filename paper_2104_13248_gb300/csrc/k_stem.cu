@@ -342,6 +342,48 @@ __global__ void head1_bwd(const bf16 *__restrict__ x, int cs, const float *__res
     if (threadIdx.x == 0 && db) atomicAdd(db, part[C]);
 }
 
+// Nearest upsampling of x plus the skip, rounded to BF16 per channel pair as
+// upsample2_add_v8 rounds it, then the 1x1 head of head1_fwd on that value
+// (same products, same channel order): bit for bit the two kernels, without
+// the full-resolution sum ever reaching memory. One thread per fine voxel.
+__global__ void upsample2_add_head1_fwd(const bf16 *__restrict__ x, const bf16 *__restrict__ skip, int scs,
+                                        int scoff, const float *__restrict__ w, const float *__restrict__ bptr,
+                                        const float *__restrict__ res, float *__restrict__ out, int N, int D,
+                                        int H, int W, int c8) {
+    __shared__ float ws[kStemMaxC];
+    for (int t = threadIdx.x; t < c8 * 8; t += blockDim.x) ws[t] = w[t];
+    __syncthreads();
+    const float b0 = bptr ? *bptr : 0.0f;
+    const int W2 = 2 * W, H2 = 2 * H, D2 = 2 * D;
+    const long long nvox = (long long)N * D2 * H2 * W2;
+    const int C = c8 * 8;
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < nvox;
+         v += (long long)gridDim.x * blockDim.x) {
+        long long r = v;
+        const int xf = (int)(r % W2);
+        r /= W2;
+        const int yf = (int)(r % H2);
+        r /= H2;
+        const int zf = (int)(r % D2);
+        const long long nb = r / D2;
+        const long long cv = ((nb * D + (zf >> 1)) * H + (yf >> 1)) * W + (xf >> 1);
+        float acc = 0.0f;
+        for (int g = 0; g < c8; ++g) {
+            const uint4 q = *reinterpret_cast<const uint4 *>(x + cv * C + g * 8);
+            const uint4 sk = *reinterpret_cast<const uint4 *>(skip + v * scs + scoff + g * 8);
+            const unsigned qa[4] = {q.x, q.y, q.z, q.w}, sa[4] = {sk.x, sk.y, sk.z, sk.w};
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const float2 a = bf2f(qa[k]), b = bf2f(sa[k]);
+                const float2 f = bf2f(f2bf(a.x + b.x, a.y + b.y));
+                acc = fmaf(ws[g * 8 + 2 * k], f.x, acc);
+                acc = fmaf(ws[g * 8 + 2 * k + 1], f.y, acc);
+            }
+        }
+        out[v] = acc + b0 + (res ? res[v] : 0.0f);
+    }
+}
+
 unsigned blocks_for(long long n) {
     long long b = (n + 255) / 256;
     return (unsigned)(b < 1 ? 1 : (b > 65535LL * 16 ? 65535LL * 16 : b));
@@ -430,6 +472,18 @@ bp_status cnn_upsample2_add_forward(const void *x, const void *skip, int s_cstri
     upsample2_add_v8<<<blocks_for(tot8), 256, 0, (cudaStream_t)stream>>>(
         (const uint4 *)x, (const bf16 *)skip, s_cstride, s_coff, (bf16 *)y, y_cstride, y_coff, n, d, h, wd, c / 8);
     return launched("upsample2_add_v8");
+}
+
+bp_status cnn_upsample2_add_head1_forward(const void *x, const void *skip, int s_cstride, int s_coff,
+                                          const float *w, const float *b, const float *res, float *out, int n,
+                                          int d, int h, int wd, int c, void *stream) {
+    if (!x || !skip || !w || !out || n < 1 || d < 1 || h < 1 || wd < 1 || c < 8 || c % 8 || c > kStemMaxC ||
+        s_cstride % 8 || s_coff % 8 || s_coff < 0 || s_coff + c > s_cstride || !al16(x) || !al16(skip))
+        return fail(nullptr, BP_ERR_INVALID_ARG, "cnn_upsample2_add_head1_forward: bad arguments");
+    const long long nvox = 8LL * n * d * h * wd;
+    upsample2_add_head1_fwd<<<blocks_for(nvox), 256, 0, (cudaStream_t)stream>>>(
+        (const bf16 *)x, (const bf16 *)skip, s_cstride, s_coff, w, b, res, out, n, d, h, wd, c / 8);
+    return launched("upsample2_add_head1_fwd");
 }
 
 }  // extern "C"

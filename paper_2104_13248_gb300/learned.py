@@ -146,8 +146,8 @@ def time_paths(maker: PairMaker, net: UNet, seed: int, reps: int = 5):
     return t_full, t_few, t_net
 
 
-def run(preset: str = "c5_learned", steps: int = 4000, crops_per_volume: int = 4, heldout: int | None = None,
-        lr: float = 5e-4, log_every: int = 250) -> dict:
+def run(preset: str = "c5_learned", steps: int = 16000, crops_per_volume: int = 4, heldout: int | None = None,
+        lr: float = 5e-4, log_every: int = 250, e1b: bool = False, d1: bool = False) -> dict:
     """The few-view workload end to end; returns a JSON-able summary."""
     p = inputs.preset(preset)
     g = p["geom"]
@@ -157,7 +157,7 @@ def run(preset: str = "c5_learned", steps: int = 4000, crops_per_volume: int = 4
     t0 = time.time()
     xs, ts = make_training_set(maker, range(p["seed"], p["seed"] + n_vol), p["crop"], crops_per_volume, rng)
     t_data = time.time() - t0
-    net = UNet(seed=p["seed"])
+    net = UNet(seed=p["seed"], e1b=e1b, d1=d1)
     t0 = time.time()
     losses = train(net, xs, ts, steps, lr=lr, log_every=log_every)
     torch.cuda.synchronize()
@@ -168,7 +168,7 @@ def run(preset: str = "c5_learned", steps: int = 4000, crops_per_volume: int = 4
     seeds = range(p["heldout_seed"], p["heldout_seed"] + n_eval)
     r_few, r_net = evaluate(net, maker, seeds, mask)
     t_full, t_few, t_net = time_paths(maker, net, p["heldout_seed"])
-    flops = conv_flops((1, g["nz"], g["ny"], g["nx"]))
+    flops = conv_flops((1, g["nz"], g["ny"], g["nx"]), e1b=e1b, d1=d1)
     out = {"preset": preset, "train_pairs": p["train_pairs"], "crop": p["crop"], "steps": steps,
            "heldout": n_eval, "rmse_few_view": r_few, "rmse_few_view_plus_net": r_net,
            "rmse_ratio": r_net / r_few, "loss_first": float(np.mean(losses[:50])),
@@ -182,6 +182,6 @@ def run(preset: str = "c5_learned", steps: int = 4000, crops_per_volume: int = 4
 
 if __name__ == "__main__":
     import sys
-    steps = int(sys.argv[1]) if len(sys.argv) > 1 else 4000
+    steps = int(sys.argv[1]) if len(sys.argv) > 1 else 16000
     lr = float(sys.argv[2]) if len(sys.argv) > 2 else 5e-4
     print(json.dumps(run(steps=steps, lr=lr)))

@@ -250,23 +250,30 @@ def _torch_reference(net, x, flat):
         return F.interpolate(t, scale_factor=2)
 
     t = x[None, None]
-    e1 = conv("e1b", conv("e1a", t.to(torch.bfloat16).float()))   # the input layer reads BF16-rounded values
+    e1 = conv("e1a", t.to(torch.bfloat16).float())   # the input layer reads BF16-rounded values
+    if net.has_e1b:
+        e1 = conv("e1b", e1)
     e2 = conv("e2b", conv("e2a", F.max_pool3d(e1, 2)))
     e3 = conv("e3b", conv("e3a", F.max_pool3d(e2, 2)))
     d2 = conv("d2", up(conv("u3", e3)) + e2)
-    d1 = conv("d1", up(conv("u2", d2)) + e1)
+    d1 = up(conv("u2", d2)) + e1
+    if net.has_d1:
+        d1 = conv("d1", d1)
     h0 = net.head_off
     hw = flat[h0:h0 + 16].reshape(1, 16, 1, 1, 1)
     return (F.conv3d(d1, hw, flat[h0 + 16:h0 + 17]) + t)[0, 0]
 
 
-def test_unet_forward_backward_against_plain_pytorch():
+@pytest.mark.parametrize("full_res", [False, True], ids=["default", "with_e1b_d1"])
+def test_unet_forward_backward_against_plain_pytorch(full_res):
     """Forward output and every layer's weight gradient vs autograd on a plain
     FP32 PyTorch copy of the network (weights rounded to BF16 like the
-    kernels read them). The kernels keep activations and their gradients in
-    BF16, so the comparison allows BF16-level differences: outputs within
-    2e-2 of the maximum, gradients with cosine similarity above 0.99."""
-    net = UNet(seed=3)
+    kernels read them), for the default network and for the one with the
+    two extra full-resolution convolutions. The kernels keep activations and
+    their gradients in BF16, so the comparison allows BF16-level
+    differences: outputs within 2e-2 of the maximum, gradients with cosine
+    similarity above 0.99."""
+    net = UNet(seed=3, e1b=full_res, d1=full_res)
     with torch.no_grad():
         net.params[net.head_off:net.head_off + 16] = torch.randn(16, device="cuda") * 0.3
     x = torch.from_numpy(inputs.uniform_array(8, (16, 16, 24), 0, 1).astype(np.float32))
@@ -301,7 +308,7 @@ def test_fused_head_matches_two_calls():
     the two calls. The outputs agree bit for bit; with the tensor path forced
     to mma.sync the fused call reports BP_ERR_UNSUPPORTED and inference falls
     back to the two calls."""
-    net = UNet(seed=4)
+    net = UNet(seed=4, e1b=True, d1=True)
     with torch.no_grad():
         net.params[net.head_off:net.head_off + 16] = torch.randn(16, device="cuda") * 0.3
     x = torch.from_numpy(inputs.uniform_array(21, (1, 8, 12, 128), 0, 1).astype(np.float32)).cuda()
@@ -322,8 +329,42 @@ def test_fused_head_matches_two_calls():
     _lib.check(lib.cnn_device_status(S()))
 
 
-def test_training_reduces_loss_and_checkpoint_resume(tmp_path):
-    net = UNet(seed=1)
+@pytest.mark.parametrize("full_res", [False, True], ids=["default", "with_e1b_d1"])
+def test_fused_upsample_head_matches_two_calls():
+    """Inference of the default network (no convolution after the last skip)
+    fuses the upsampling, the skip sum and the 1x1 head in one kernel
+    (cnn_upsample2_add_head1_forward); training runs the upsampling and the
+    head as two calls. The outputs agree bit for bit, also on a ragged
+    width and with a channel offset into a wider skip tensor."""
+    net = UNet(seed=5)
+    with torch.no_grad():
+        net.params[net.head_off:net.head_off + 17] = torch.randn(17, device="cuda") * 0.3
+    x = torch.from_numpy(inputs.uniform_array(22, (1, 8, 12, 20), 0, 1).astype(np.float32)).cuda()
+    a = net.forward(x, train=False).clone()
+    b = net.forward(x, train=True).clone()
+    assert torch.equal(a, b)
+    lib = _lib.load()
+    g = torch.Generator(device="cuda").manual_seed(6)
+    xc = torch.randn((2, 3, 5, 7, 16), generator=g, device="cuda").to(torch.bfloat16)
+    sk = torch.randn((2, 6, 10, 14, 32), generator=g, device="cuda").to(torch.bfloat16)
+    res = torch.randn((2, 6, 10, 14), generator=g, device="cuda")
+    w = torch.randn(16, generator=g, device="cuda")
+    bias = torch.randn(1, generator=g, device="cuda")
+    a1 = torch.empty((2, 6, 10, 14, 16), dtype=torch.bfloat16, device="cuda")
+    two = torch.empty((2, 6, 10, 14), device="cuda")
+    one = torch.empty_like(two)
+    _lib.check(lib.cnn_upsample2_add_forward(P(xc), P(sk), 32, 16, P(a1), 16, 0, 2, 3, 5, 7, 16, S()))
+    _lib.check(lib.cnn_head1_forward(P(a1), 16, P(w), P(bias), P(res), P(two), a1.numel() // 16, 16, S()))
+    _lib.check(lib.cnn_upsample2_add_head1_forward(P(xc), P(sk), 32, 16, P(w), P(bias), P(res), P(one),
+                                                   2, 3, 5, 7, 16, S()))
+    assert torch.equal(one, two)
+    assert lib.cnn_upsample2_add_head1_forward(P(xc), P(sk), 32, 20, P(w), P(bias), P(res), P(one),
+                                               2, 3, 5, 7, 16, S()) == _lib.BP_ERR_INVALID_ARG
+    _lib.check(lib.cnn_device_status(S()))
+
+
+def test_training_reduces_loss_and_checkpoint_resume(tmp_path, full_res):
+    net = UNet(seed=1, e1b=full_res, d1=full_res)
     x = torch.from_numpy(inputs.uniform_array(1, (2, 16, 16, 16), 0, 1).astype(np.float32)).cuda()
     t = (x * 0.5 + 0.1).contiguous()
     losses = [net.train_step(x, t, lr=3e-3) for _ in range(60)]
@@ -332,7 +373,7 @@ def test_training_reduces_loss_and_checkpoint_resume(tmp_path):
     path = tmp_path / "ck.pt"
     torch.save(net.state_dict(), path)
     cont = [net.train_step(x, t, lr=3e-3) for _ in range(3)]
-    net2 = UNet(seed=99)
+    net2 = UNet(seed=99, e1b=full_res, d1=full_res)
     net2.load_state_dict(torch.load(path))
     cont2 = [net2.train_step(x, t, lr=3e-3) for _ in range(3)]
     np.testing.assert_allclose(cont, cont2, rtol=2e-3)
@@ -348,7 +389,9 @@ def test_learned_few_view_gain_small():
     rng = np.random.default_rng(0)
     xs, ts = learned.make_training_set(maker, range(2000, 2016), 32, 4, rng)
     net = UNet(seed=0)
-    learned.train(net, xs, ts, steps=400, lr=5e-4, batch=2)
+    # the default network (no extra full-resolution convolutions) trains
+    # with four times the steps of the full one, as in the full-size workload
+    learned.train(net, xs, ts, steps=1600, lr=5e-4, batch=2)
     mask = learned.fov_mask(g)
     r_few, r_net = learned.evaluate(net, maker, range(9000, 9004), mask)
     print(f"few-view RMSE {r_few:.4f}, with network {r_net:.4f}")
