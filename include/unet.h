@@ -202,8 +202,8 @@ bp_status cnn_head1_backward(const void *x, int x_cstride, const float *w, const
  * x BF16 [n][d][h][wd][c] (dense, coarse), skip BF16 [n][2d][2h][2wd]
  * [s_cstride] (channels s_coff ..), w FP32 [c], b FP32 [1] (may be NULL),
  * res and out FP32 [n][2d][2h][2wd] (res may be NULL). c a multiple of 8 up
- * to 32; s_cstride and s_coff multiples of 8; x and skip 16-byte aligned.
- * BP_ERR_INVALID_ARG on bad arguments. */
+ * to 32; s_cstride and s_coff multiples of 8; x and skip 16-byte aligned,
+ * res and out 8-byte aligned. BP_ERR_INVALID_ARG on bad arguments. */
 bp_status cnn_upsample2_add_head1_forward(const void *x, const void *skip, int s_cstride, int s_coff,
                                           const float *w, const float *b, const float *res, float *out, int n,
                                           int d, int h, int wd, int c, void *stream);

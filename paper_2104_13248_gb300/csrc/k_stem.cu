@@ -345,7 +345,9 @@ __global__ void head1_bwd(const bf16 *__restrict__ x, int cs, const float *__res
 // Nearest upsampling of x plus the skip, rounded to BF16 per channel pair as
 // upsample2_add_v8 rounds it, then the 1x1 head of head1_fwd on that value
 // (same products, same channel order): bit for bit the two kernels, without
-// the full-resolution sum ever reaching memory. One thread per fine voxel.
+// the full-resolution sum ever reaching memory. One thread per coarse voxel
+// and fine (z, y) child row: the coarse channels are loaded once for the two
+// fine voxels along x, whose outputs and residuals are one float2.
 __global__ void upsample2_add_head1_fwd(const bf16 *__restrict__ x, const bf16 *__restrict__ skip, int scs,
                                         int scoff, const float *__restrict__ w, const float *__restrict__ bptr,
                                         const float *__restrict__ res, float *__restrict__ out, int N, int D,
@@ -354,33 +356,44 @@ __global__ void upsample2_add_head1_fwd(const bf16 *__restrict__ x, const bf16 *
     for (int t = threadIdx.x; t < c8 * 8; t += blockDim.x) ws[t] = w[t];
     __syncthreads();
     const float b0 = bptr ? *bptr : 0.0f;
-    const int W2 = 2 * W, H2 = 2 * H, D2 = 2 * D;
-    const long long nvox = (long long)N * D2 * H2 * W2;
     const int C = c8 * 8;
-    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < nvox;
-         v += (long long)gridDim.x * blockDim.x) {
-        long long r = v;
-        const int xf = (int)(r % W2);
-        r /= W2;
-        const int yf = (int)(r % H2);
-        r /= H2;
-        const int zf = (int)(r % D2);
-        const long long nb = r / D2;
-        const long long cv = ((nb * D + (zf >> 1)) * H + (yf >> 1)) * W + (xf >> 1);
-        float acc = 0.0f;
+    // t = ((((nb * D + z) * 2 + cz) * H + y) * 2 + cy) * W + xc: consecutive threads walk x
+    const long long total = (long long)N * D * H * W * 4;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        long long r = t;
+        const int xc = (int)(r % W);
+        r /= W;
+        const int cy = (int)(r & 1);
+        r >>= 1;
+        const int yc = (int)(r % H);
+        r /= H;
+        const int cz = (int)(r & 1);
+        r >>= 1;
+        const int zc = (int)(r % D);
+        const long long nb = r / D;
+        const long long cv = ((nb * D + zc) * H + yc) * W + xc;
+        const long long v0 = ((nb * 2 * D + 2 * zc + cz) * (2 * H) + 2 * yc + cy) * (2LL * W) + 2 * xc;
+        float acc0 = 0.0f, acc1 = 0.0f;
         for (int g = 0; g < c8; ++g) {
             const uint4 q = *reinterpret_cast<const uint4 *>(x + cv * C + g * 8);
-            const uint4 sk = *reinterpret_cast<const uint4 *>(skip + v * scs + scoff + g * 8);
-            const unsigned qa[4] = {q.x, q.y, q.z, q.w}, sa[4] = {sk.x, sk.y, sk.z, sk.w};
+            const uint4 s0 = *reinterpret_cast<const uint4 *>(skip + v0 * scs + scoff + g * 8);
+            const uint4 s1 = *reinterpret_cast<const uint4 *>(skip + (v0 + 1) * scs + scoff + g * 8);
+            const unsigned qa[4] = {q.x, q.y, q.z, q.w};
+            const unsigned sa[4] = {s0.x, s0.y, s0.z, s0.w}, sb[4] = {s1.x, s1.y, s1.z, s1.w};
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
-                const float2 a = bf2f(qa[k]), b = bf2f(sa[k]);
-                const float2 f = bf2f(f2bf(a.x + b.x, a.y + b.y));
-                acc = fmaf(ws[g * 8 + 2 * k], f.x, acc);
-                acc = fmaf(ws[g * 8 + 2 * k + 1], f.y, acc);
+                const float2 a = bf2f(qa[k]), u = bf2f(sa[k]), o = bf2f(sb[k]);
+                const float2 f0 = bf2f(f2bf(a.x + u.x, a.y + u.y)), f1 = bf2f(f2bf(a.x + o.x, a.y + o.y));
+                acc0 = fmaf(ws[g * 8 + 2 * k], f0.x, acc0);
+                acc0 = fmaf(ws[g * 8 + 2 * k + 1], f0.y, acc0);
+                acc1 = fmaf(ws[g * 8 + 2 * k], f1.x, acc1);
+                acc1 = fmaf(ws[g * 8 + 2 * k + 1], f1.y, acc1);
             }
         }
-        out[v] = acc + b0 + (res ? res[v] : 0.0f);
+        float2 rr = make_float2(0.0f, 0.0f);
+        if (res) rr = *reinterpret_cast<const float2 *>(res + v0);
+        *reinterpret_cast<float2 *>(out + v0) = make_float2(acc0 + b0 + rr.x, acc1 + b0 + rr.y);
     }
 }
 
@@ -480,8 +493,10 @@ bp_status cnn_upsample2_add_head1_forward(const void *x, const void *skip, int s
     if (!x || !skip || !w || !out || n < 1 || d < 1 || h < 1 || wd < 1 || c < 8 || c % 8 || c > kStemMaxC ||
         s_cstride % 8 || s_coff % 8 || s_coff < 0 || s_coff + c > s_cstride || !al16(x) || !al16(skip))
         return fail(nullptr, BP_ERR_INVALID_ARG, "cnn_upsample2_add_head1_forward: bad arguments");
-    const long long nvox = 8LL * n * d * h * wd;
-    upsample2_add_head1_fwd<<<blocks_for(nvox), 256, 0, (cudaStream_t)stream>>>(
+    if (((uintptr_t)out & 7u) || ((uintptr_t)res & 7u))
+        return fail(nullptr, BP_ERR_INVALID_ARG, "cnn_upsample2_add_head1_forward: res and out must be 8-byte aligned");
+    const long long nthreads = 4LL * n * d * h * wd;
+    upsample2_add_head1_fwd<<<blocks_for(nthreads), 256, 0, (cudaStream_t)stream>>>(
         (const bf16 *)x, (const bf16 *)skip, s_cstride, s_coff, w, b, res, out, n, d, h, wd, c / 8);
     return launched("upsample2_add_head1_fwd");
 }

@@ -329,7 +329,6 @@ def test_fused_head_matches_two_calls():
     _lib.check(lib.cnn_device_status(S()))
 
 
-@pytest.mark.parametrize("full_res", [False, True], ids=["default", "with_e1b_d1"])
 def test_fused_upsample_head_matches_two_calls():
     """Inference of the default network (no convolution after the last skip)
     fuses the upsampling, the skip sum and the 1x1 head in one kernel
@@ -363,6 +362,7 @@ def test_fused_upsample_head_matches_two_calls():
     _lib.check(lib.cnn_device_status(S()))
 
 
+@pytest.mark.parametrize("full_res", [False, True], ids=["default", "with_e1b_d1"])
 def test_training_reduces_loss_and_checkpoint_resume(tmp_path, full_res):
     net = UNet(seed=1, e1b=full_res, d1=full_res)
     x = torch.from_numpy(inputs.uniform_array(1, (2, 16, 16, 16), 0, 1).astype(np.float32)).cuda()
