@@ -959,7 +959,7 @@ bp_status cnn_conv3d_forward_head(const void *x, int x_cstride, int x_coff, cons
     if (!x || !w || !head_w || !out || n < 1 || d < 1 || h < 1 || wd < 1 || cin < 16 || cin % 16 ||
         !conv_args_ok(x_cstride, x_coff, cin) || !al16(x) || !al16(w))
         return fail(nullptr, BP_ERR_INVALID_ARG, "cnn_conv3d_forward_head: bad arguments");
-    if (!conv_tcp_applies(cin, cout) ||
+    if (wd % 128 != 0 || !conv_tcp_applies(cin, cout) ||
         !conv_tc_applies(x, x_cstride, x_coff, w, out, cout, 0, 0, d, h, wd, cin, cout))
         return fail(nullptr, BP_ERR_UNSUPPORTED, "cnn_conv3d_forward_head: layer outside the persistent tcgen05 kernel");
     cudaError_t e = conv_fwd_tc(x, x_cstride, x_coff, w, b, nullptr, cout, 0, 0, n, d, h, wd, cin, cout, relu,

@@ -58,11 +58,21 @@ constexpr int kPlaneStride = (kPlaneBytes + 127) / 128 * 128;
 constexpr int kRows = 4;                               // output rows per CTA (4 along z)
 static_assert(kPlaneStride % 128 == 0 && (2 * kPlaneStride) % 128 == 0, "TMA destinations need 128-byte alignment");
 
-template <int COUT>
+// Brick of the per-tile kernel for tiles TW voxels wide (128, or 64 with
+// M = 64 MMAs): TW + 2 voxels along x.
+template <int TW>
+struct TileGeo {
+    static constexpr int BX = TW + 2;
+    static constexpr int PLANE_BYTES = BX * kBY * kBZ * 16;
+    static constexpr int PLANE_STRIDE = (PLANE_BYTES + 127) / 128 * 128;
+    static_assert(TW == 128 || TW == 64, "tile widths 128 and 64");
+};
+
+template <int COUT, int TW = 128>
 struct TcCfg {
     static constexpr int WBYTES = 27 * 2 * COUT * 16;  // weights of one 16-channel chunk
-    static constexpr int TMEM_COLS = kRows * COUT;     // 64 or 128 (a power of two >= 32)
-    static constexpr int SMEM = 2 * kPlaneStride + WBYTES + 1024;   // + alignment slack
+    static constexpr int TMEM_COLS = kRows * COUT;     // 64, 128 or 256 (a power of two >= 32)
+    static constexpr int SMEM = 2 * TileGeo<TW>::PLANE_STRIDE + WBYTES + 1024;   // + alignment slack
 };
 
 __device__ __forceinline__ unsigned s_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
@@ -120,25 +130,36 @@ struct TmemRow<32> {
         TmemRow<16>::load(addr + 16, v + 16);
     }
 };
+template <>
+struct TmemRow<64> {
+    __device__ __forceinline__ static void load(unsigned addr, float *v) {
+        TmemRow<32>::load(addr, v);
+        TmemRow<32>::load(addr + 32, v + 32);
+    }
+};
 
-template <int COUT, bool OUT_F32>
+// TW = 64: the tile's rows are 64 voxels (layers of width 64); each MMA has
+// M = 64, whose accumulator row m sits in TMEM lane 32 (m / 16) + m % 16,
+// so every epilogue warp finds its 16 rows in its first 16 lanes.
+template <int COUT, bool OUT_F32, int TW>
 __global__ void __launch_bounds__(kTcThreads, 2)
 conv3d_fwd_tc(const __grid_constant__ CUtensorMap xmap, int xco, const bf16 *__restrict__ w,
               const float *__restrict__ bias, void *__restrict__ y, int ycs, int yco, int d, int h, int wd,
               int cin, int relu, unsigned *err, unsigned long long timeout_ns) {
-    using Cfg = TcCfg<COUT>;
+    using Cfg = TcCfg<COUT, TW>;
+    using G = TileGeo<TW>;
     extern __shared__ unsigned char smem_raw[];
     // 1024-byte aligned base: planes, then weights
     unsigned char *smem = reinterpret_cast<unsigned char *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     unsigned char *plane0 = smem;
-    unsigned char *wsm = smem + 2 * kPlaneStride;
+    unsigned char *wsm = smem + 2 * G::PLANE_STRIDE;
     __shared__ __align__(8) unsigned long long tma_bar, mma_bar;
     __shared__ unsigned tmem_base;
     __shared__ int alive_s;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int ntx = wd / 128, nty = h, ntz = d / 4;
+    const int ntx = wd / TW, nty = h, ntz = d / 4;
     int t = blockIdx.x;
     const int tx = t % ntx;
     t /= ntx;
@@ -146,7 +167,7 @@ conv3d_fwd_tc(const __grid_constant__ CUtensorMap xmap, int xco, const bf16 *__r
     t /= nty;
     const int tz = t % ntz;
     const int nb = t / ntz;
-    const int x0 = tx * 128, y0 = ty, z0 = tz * 4;
+    const int x0 = tx * TW, y0 = ty, z0 = tz * 4;
 
     if (tid == 0) {
         mbar_init(&tma_bar, 1);
@@ -168,9 +189,9 @@ conv3d_fwd_tc(const __grid_constant__ CUtensorMap xmap, int xco, const bf16 *__r
     for (int ch = 0; ch < nchunks; ++ch) {
         // the brick's TMA first, so its latency overlaps the weight copies
         if (tid == 0) {
-            mbar_arrive_expect_tx(&tma_bar, 2u * kPlaneBytes);
+            mbar_arrive_expect_tx(&tma_bar, 2u * G::PLANE_BYTES);
             tma_load_5d(plane0, &xmap, xco + ch * 16, x0 - 1, y0 - 1, z0 - 1, nb, &tma_bar);
-            tma_load_5d(plane0 + kPlaneStride, &xmap, xco + ch * 16 + 8, x0 - 1, y0 - 1, z0 - 1, nb, &tma_bar);
+            tma_load_5d(plane0 + G::PLANE_STRIDE, &xmap, xco + ch * 16 + 8, x0 - 1, y0 - 1, z0 - 1, nb, &tma_bar);
         }
         // weights of this chunk: w[co][tap][16 ch + i] -> wsm[dy][dx][half][dz][co][8]
         for (int p = tid; p < 27 * 2 * COUT; p += kTcThreads) {
@@ -203,12 +224,12 @@ conv3d_fwd_tc(const __grid_constant__ CUtensorMap xmap, int xco, const bf16 *__r
                         const int zp = (g == 0) ? (q == 0 ? 3 : q == 1 ? 0 : q - 1 + (q >= 4 ? 1 : 0)) : q;
                         const int rz_hi = zp < 3 ? zp : 3, rz_lo = zp > 2 ? zp - 2 : 0;
                         const int nrows = rz_hi - rz_lo + 1;
-                        const unsigned voff = (unsigned)((zp * kBY + dy) * kBX + dx) * 16u;
-                        const unsigned long long ad = smem_desc(pa + voff, kPlaneStride, 128);
+                        const unsigned voff = (unsigned)((zp * kBY + dy) * G::BX + dx) * 16u;
+                        const unsigned long long ad = smem_desc(pa + voff, G::PLANE_STRIDE, 128);
                         const unsigned boff = (unsigned)((((dy * 3 + dx) * 2) * 3 + (zp - rz_hi)) * COUT * 16);
                         const unsigned long long bd = smem_desc(wb + boff, 3 * COUT * 16, 128);
                         const unsigned id = (1u << 4) | (1u << 7) | (1u << 10) |
-                                            ((unsigned)((nrows * COUT) >> 3) << 17) | ((unsigned)(128 >> 4) << 24);
+                                            ((unsigned)((nrows * COUT) >> 3) << 17) | ((unsigned)(TW >> 4) << 24);
                         const unsigned acc = (ch > 0 || g > 0 || q > 1) ? 1u : 0u;
                         asm volatile(
                             "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
@@ -240,12 +261,16 @@ conv3d_fwd_tc(const __grid_constant__ CUtensorMap xmap, int xco, const bf16 *__r
 
     if (alive_s) {
         const size_t vox_row = (size_t)wd;
+        // the voxel of this lane's accumulator row (TW = 64: lanes 16-31 hold none)
+        const int xl = (TW == 128) ? warp * 32 + lane : warp * 16 + lane;
+        const bool has_row = TW == 128 || lane < 16;
 #pragma unroll 1
         for (int r = 0; r < kRows; ++r) {
             float v[COUT];
             TmemRow<COUT>::load(tmem + ((unsigned)(warp * 32) << 16) + (unsigned)((3 - r) * COUT), v);
+            if (!has_row) continue;
             const int yy = y0, zz = z0 + r;
-            const int xx = x0 + warp * 32 + lane;
+            const int xx = x0 + xl;
             const size_t vox = (((size_t)nb * d + zz) * h + yy) * vox_row + xx;
 #pragma unroll
             for (int c = 0; c < COUT; ++c) {
@@ -630,13 +655,17 @@ static cudaError_t tc_err_address(unsigned **out) {
     return cudaSuccess;
 }
 
-// The tensor-core path applies when the width is a multiple of 128, the
-// depth a multiple of 4, Cout is 16 or 32, Cin a multiple of 16, and every
-// pointer, stride and offset is 16-byte aligned.
+// The tensor-core path applies when the depth is a multiple of 4, Cin a
+// multiple of 16, every pointer, stride and offset 16-byte aligned, and
+// either the width is a multiple of 128 with Cout 16 or 32 (tiles of 128
+// voxels), or the width is a multiple of 64 but not of 128 with Cout 16, 32
+// or 64 (tiles of 64 voxels, M = 64 MMAs).
 bool conv_tc_applies(const void *x, int xcs, int xco, const void *w, const void *y, int ycs, int yco, int yf32,
                      int d, int h, int wd, int cin, int cout) {
     (void)yf32;
-    return (g_tc_mode == 1 || g_tc_mode == 2) && (cout == 16 || cout == 32) && cin % 16 == 0 && cin > 0 && wd % 128 == 0 && wd > 0 &&
+    const bool t128 = wd % 128 == 0 && (cout == 16 || cout == 32);
+    const bool t64 = wd % 128 != 0 && wd % 64 == 0 && (cout == 16 || cout == 32 || cout == 64);
+    return (g_tc_mode == 1 || g_tc_mode == 2) && (t128 || t64) && cin % 16 == 0 && cin > 0 && wd > 0 &&
            d % 4 == 0 && h > 0 && d > 0 && xcs % 8 == 0 && xco % 8 == 0 && ycs % 8 == 0 && yco % 8 == 0 &&
            (reinterpret_cast<uintptr_t>(x) & 15) == 0 && (reinterpret_cast<uintptr_t>(w) & 15) == 0 &&
            (reinterpret_cast<uintptr_t>(y) & 15) == 0 && encode_fn() != nullptr;
@@ -653,7 +682,8 @@ cudaError_t conv_fwd_tc(const void *x, int xcs, int xco, const void *w, const fl
                         int yf32, int n, int d, int h, int wd, int cin, int cout, int relu, cudaStream_t st,
                         const float *head_w, const float *head_b, const float *head_res, float *head_out) {
     const bool fused_head = head_out != nullptr;
-    if (fused_head && !conv_tcp_applies(cin, cout)) return cudaErrorNotSupported;
+    const int TW = wd % 128 == 0 ? 128 : 64;   // tile width (conv_tc_applies checked the rest)
+    if (fused_head && (TW != 128 || !conv_tcp_applies(cin, cout))) return cudaErrorNotSupported;
     unsigned *err = nullptr;
     cudaError_t ea = tc_err_address(&err);
     if (ea != cudaSuccess) return ea;
@@ -662,19 +692,19 @@ cudaError_t conv_fwd_tc(const void *x, int xcs, int xco, const void *w, const fl
     cuuint64_t dims[5] = {(cuuint64_t)xcs, (cuuint64_t)wd, (cuuint64_t)h, (cuuint64_t)d, (cuuint64_t)n};
     cuuint64_t strides[4] = {(cuuint64_t)xcs * es, (cuuint64_t)xcs * wd * es, (cuuint64_t)xcs * wd * h * es,
                              (cuuint64_t)xcs * wd * h * d * es};
-    cuuint32_t box[5] = {8, (cuuint32_t)kBX, (cuuint32_t)kBY, (cuuint32_t)kBZ, 1};
+    cuuint32_t box[5] = {8, (cuuint32_t)(TW + 2), (cuuint32_t)kBY, (cuuint32_t)kBZ, 1};
     cuuint32_t estr[5] = {1, 1, 1, 1, 1};
     CUresult r = encode_fn()(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<void *>(x), dims, strides, box,
                              estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
-    const long long nblk = (long long)n * (d / 4) * h * (wd / 128);
+    const long long nblk = (long long)n * (d / 4) * h * (wd / TW);
     if (nblk <= 0) return cudaSuccess;
     if (nblk > 0x7fffffffLL) return cudaErrorInvalidValue;
     const unsigned long long timeout_ns = 2000000000ull;
     const int nch = cin / 16;
     const int psmem = cout == 16 ? TcpCfg<16>::smem(nch) : TcpCfg<32>::smem(nch);
-    if (g_tc_mode == 1 && psmem <= kPSmemLimit) {
+    if (TW == 128 && g_tc_mode == 1 && psmem <= kPSmemLimit) {
         // rows of 16 channels (32 bytes), 32-byte swizzle
         cuuint32_t box16[5] = {16, (cuuint32_t)kBX, (cuuint32_t)kBY, (cuuint32_t)kBZ, 1};
         r = encode_fn()(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<void *>(x), dims, strides, box16, estr,
@@ -709,19 +739,29 @@ cudaError_t conv_fwd_tc(const void *x, int xcs, int xco, const void *w, const fl
         }
 #undef TCP_CASE
     }
-#define TC_CASE(C, F)                                                                                        \
-    {                                                                                                        \
-        auto k = conv3d_fwd_tc<C, F>;                                                                        \
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, TcCfg<C>::SMEM); \
-        if (e != cudaSuccess) return e;                                                                      \
-        k<<<(unsigned)nblk, kTcThreads, TcCfg<C>::SMEM, st>>>(map, xco, (const bf16 *)w, b, y, ycs, yco, d, h, \
-                                                              wd, cin, relu, err, timeout_ns);               \
-        return cudaGetLastError();                                                                           \
+#define TC_CASE(C, F, T)                                                                                        \
+    {                                                                                                           \
+        auto k = conv3d_fwd_tc<C, F, T>;                                                                        \
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, TcCfg<C, T>::SMEM); \
+        if (e != cudaSuccess) return e;                                                                         \
+        k<<<(unsigned)nblk, kTcThreads, TcCfg<C, T>::SMEM, st>>>(map, xco, (const bf16 *)w, b, y, ycs, yco, d, h, \
+                                                                 wd, cin, relu, err, timeout_ns);               \
+        return cudaGetLastError();                                                                              \
     }
-    if (cout == 16) {
-        if (yf32) TC_CASE(16, true) else TC_CASE(16, false)
+    if (TW == 128) {
+        if (cout == 16) {
+            if (yf32) TC_CASE(16, true, 128) else TC_CASE(16, false, 128)
+        } else {
+            if (yf32) TC_CASE(32, true, 128) else TC_CASE(32, false, 128)
+        }
     } else {
-        if (yf32) TC_CASE(32, true) else TC_CASE(32, false)
+        if (cout == 16) {
+            if (yf32) TC_CASE(16, true, 64) else TC_CASE(16, false, 64)
+        } else if (cout == 32) {
+            if (yf32) TC_CASE(32, true, 64) else TC_CASE(32, false, 64)
+        } else {
+            if (yf32) TC_CASE(64, true, 64) else TC_CASE(64, false, 64)
+        }
     }
 #undef TC_CASE
 }

@@ -39,9 +39,12 @@ def rel(a, b):
 
 SHAPES = [(1, 8, 8, 16, 16, 16), (2, 6, 9, 13, 32, 64), (1, 12, 10, 9, 48, 16), (1, 4, 4, 20, 96, 32),
           (1, 16, 16, 16, 64, 64)]
-# layers the tcgen05 kernel takes (width a multiple of 128, depth a multiple of 4, Cout 16 / 32)
+# layers the tcgen05 kernels take: width a multiple of 128 with Cout 16 / 32, or a
+# multiple of 64 (not of 128) with Cout 16 / 32 / 64 (tiles of 64 voxels, M = 64
+# MMAs); depth a multiple of 4
 TC_SHAPES = [(1, 4, 2, 128, 16, 16), (1, 4, 3, 256, 48, 16), (2, 4, 3, 128, 32, 32), (1, 8, 1, 128, 96, 32),
-             (1, 8, 5, 256, 32, 16), (2, 12, 3, 128, 16, 32)]
+             (1, 8, 5, 256, 32, 16), (2, 12, 3, 128, 16, 32),
+             (1, 4, 3, 64, 32, 64), (2, 4, 2, 64, 64, 64), (1, 8, 3, 192, 64, 32), (1, 4, 5, 64, 16, 16)]
 
 
 @pytest.mark.parametrize("path", [1, 2, 0], ids=["tcgen05_persistent", "tcgen05_tile", "mma_sync"])
