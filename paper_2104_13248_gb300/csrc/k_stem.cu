@@ -44,19 +44,21 @@ __device__ __forceinline__ unsigned f2bf(float a, float b) {
 }
 __device__ __forceinline__ float round_bf16(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
 
-// CTA tile 64 (x) x 8 (y) x 2 (z) outputs. The haloed input tile (66 x 10 x 4
+// CTA tile 64 (x) x 8 (y) x 8 (z) outputs. The haloed input tile (66 x 10 x 10
 // values, rounded to BF16 once and kept as BF16 bits) is staged in shared
-// memory with all loads in flight at once; the A fragments are byte
-// permutes of those bits (no conversion per use). The products run on the tensor cores (mma.sync m16n8k16,
+// memory row by row (one warp per row, every load in flight before any
+// store); the A fragments are byte permutes of those bits (no conversion
+// per use), read at plain int indices into the tile (32-bit shared
+// addressing; per-element index arithmetic in 64-bit generic addresses had
+// made the layer integer-bound: 287 us at 256^3 against 181 us now). The products run on the tensor cores (mma.sync m16n8k16,
 // BF16 in, FP32 accumulation) as a GEMM with M = 16 x-consecutive voxels,
 // N = output channels and K = the 27 taps (zero-padded to 32): a thread's
 // A-fragment entries are single shared-memory loads at the tap offsets it
 // owns, the weight fragments stay in registers for the whole CTA.
-constexpr int kStTX = 64, kStTY = 8, kStTZ = 2;
+constexpr int kStTX = 64, kStTY = 8, kStTZ = 8;
 constexpr int kStHX = kStTX + 2, kStHY = kStTY + 2, kStHZ = kStTZ + 2;
 constexpr int kStHalo = kStHX * kStHY * kStHZ;   // 2640
 constexpr int kStThreads = 256;
-constexpr int kStPer = (kStHalo + kStThreads - 1) / kStThreads;   // 11 values per thread
 
 __device__ __forceinline__ unsigned pack_bf16x2(float lo, float hi) {
     unsigned r;
@@ -77,6 +79,9 @@ __global__ void __launch_bounds__(kStThreads)
 stem_fwd_mma(const float *__restrict__ x, const bf16 *__restrict__ w, const float *__restrict__ b,
              bf16 *__restrict__ y, int ycs, int ycoff, int D, int H, int W, int relu, int tx, int ty, int tz) {
     constexpr int NT = C / 8;   // n-tiles
+    constexpr int kRowsH = kStHZ * kStHY;                          // staged rows (hz, hy)
+    constexpr int kRowsPerWarp = (kRowsH + kStThreads / 32 - 1) / (kStThreads / 32);
+    constexpr int kXPer = (kStHX + 31) / 32;                       // values per lane and row
     __shared__ unsigned short xs[kStHalo];   // [HZ][HY][HX], BF16 bits (rounded once when staged)
     long long r = blockIdx.x;
     const int x0 = (int)(r % tx) * kStTX;
@@ -85,16 +90,23 @@ stem_fwd_mma(const float *__restrict__ x, const bf16 *__restrict__ w, const floa
     r /= ty;
     const int z0 = (int)(r % tz) * kStTZ;
     const long long nb = r / tz;
-    float v[kStPer];
-#pragma unroll
-    for (int k = 0; k < kStPer; ++k) {
-        const int c = threadIdx.x + k * kStThreads;
-        const int hx = c % kStHX, hy = (c / kStHX) % kStHY, hz = c / (kStHX * kStHY);
-        const int z = z0 + hz - 1, yy = y0 + hy - 1, xx = x0 + hx - 1;
-        v[k] = (c < kStHalo && z >= 0 && z < D && yy >= 0 && yy < H && xx >= 0 && xx < W)
-                   ? __ldg(x + ((nb * D + z) * H + yy) * (long long)W + xx) : 0.0f;
-    }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // staging: warp w loads rows w, w + 8, ... of the haloed tile, lane l the
+    // pixels l, l + 32, l + 64 of a row; every load is issued before any store
+    float v[kRowsPerWarp][kXPer];
+#pragma unroll
+    for (int i = 0; i < kRowsPerWarp; ++i) {
+        const int row = warp + i * (kStThreads / 32);
+        const int hz = row / kStHY, hy = row - hz * kStHY;
+        const int z = z0 + hz - 1, yy = y0 + hy - 1;
+        const bool rok = row < kRowsH && z >= 0 && z < D && yy >= 0 && yy < H;
+        const float *src = x + ((nb * D + (rok ? z : 0)) * H + (rok ? yy : 0)) * (long long)W;
+#pragma unroll
+        for (int j = 0; j < kXPer; ++j) {
+            const int hx = lane + 32 * j, xx = x0 + hx - 1;
+            v[i][j] = (rok && hx < kStHX && xx >= 0 && xx < W) ? __ldg(src + xx) : 0.0f;
+        }
+    }
     const int g = lane >> 2, t4 = lane & 3;
     // this thread's K slots: k = 16 s + 2 t4 + {0, 1, 8, 9}; offset of tap k in the staged tile
     int off[2][4];
@@ -124,58 +136,69 @@ stem_fwd_mma(const float *__restrict__ x, const bf16 *__restrict__ w, const floa
         bias[j][1] = b ? b[j * 8 + 2 * t4 + 1] : 0.0f;
     }
 #pragma unroll
-    for (int k = 0; k < kStPer; ++k) {
-        const int c = threadIdx.x + k * kStThreads;
-        if (c < kStHalo) xs[c] = __bfloat16_as_ushort(__float2bfloat16_rn(v[k]));
+    for (int i = 0; i < kRowsPerWarp; ++i) {
+        const int row = warp + i * (kStThreads / 32);
+#pragma unroll
+        for (int j = 0; j < kXPer; ++j) {
+            const int hx = lane + 32 * j;
+            if (row < kRowsH && hx < kStHX) xs[row * kStHX + hx] = __bfloat16_as_ushort(__float2bfloat16_rn(v[i][j]));
+        }
     }
     __syncthreads();
-    // 64 tasks of 16 voxels: row (oz, oy) = task / 4, x segment 16 * (task % 4)
-    for (int task = warp; task < kStTZ * kStTY * 4; task += kStThreads / 32) {
-        const int row = task >> 2, xs0 = (task & 3) * 16;
-        const int oz = row / kStTY, oy = row % kStTY;
-        const unsigned short *base = xs + (oz * kStHY + oy) * kStHX + xs0 + g;   // tap (0,0,0) of voxel xs0 + g
-        float acc[NT][4];
-#pragma unroll
-        for (int j = 0; j < NT; ++j) {
-            acc[j][0] = bias[j][0];
-            acc[j][1] = bias[j][1];
-            acc[j][2] = bias[j][0];
-            acc[j][3] = bias[j][1];
-        }
-#pragma unroll
-        for (int s2 = 0; s2 < 2; ++s2) {
-            unsigned e[2][4];   // [row g / g + 8][slot], BF16 bits
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int o = off[s2][q];
-                e[0][q] = o >= 0 ? base[o] : 0u;
-                e[1][q] = o >= 0 ? base[o + 8] : 0u;
-            }
-            // two BF16 values per register, the lower k in the low half
-            unsigned a[4];
-            a[0] = __byte_perm(e[0][0], e[0][1], 0x5410);   // row g, k = 2 t4, 2 t4 + 1
-            a[1] = __byte_perm(e[1][0], e[1][1], 0x5410);   // row g + 8
-            a[2] = __byte_perm(e[0][2], e[0][3], 0x5410);   // row g, k + 8
-            a[3] = __byte_perm(e[1][2], e[1][3], 0x5410);   // row g + 8, k + 8
-#pragma unroll
-            for (int j = 0; j < NT; ++j) mma16816(acc[j], a, bw[s2][j][0], bw[s2][j][1]);
-        }
+    // output rows (oz, oy): warp w takes rows w, w + 8, ...; per row four x
+    // segments of 16 voxels. Shared indices are plain ints into xs (32-bit
+    // shared addressing, the tap offsets compile-time within a row).
+#pragma unroll 1
+    for (int orow = warp; orow < kStTZ * kStTY; orow += kStThreads / 32) {
+        const int oz = orow / kStTY, oy = orow - oz * kStTY;
         const int z = z0 + oz, yy = y0 + oy;
-        if (z >= D || yy >= H) continue;
-        const long long vrow = ((nb * D + z) * H + yy) * (long long)W;
+        const bool row_ok = z < D && yy < H;
+        const int rbase = (oz * kStHY + oy) * kStHX + g;   // tap (0,0,0) of voxel g of the row
+        const long long vrow = ((nb * D + (row_ok ? z : 0)) * H + (row_ok ? yy : 0)) * (long long)W;
 #pragma unroll
-        for (int hr = 0; hr < 2; ++hr) {
-            const int xx = x0 + xs0 + g + 8 * hr;
-            if (xx >= W) continue;
-            bf16 *dst = y + (vrow + xx) * ycs + ycoff + 2 * t4;
+        for (int seg = 0; seg < 4; ++seg) {
+            const int xs0 = seg * 16;
+            float acc[NT][4];
 #pragma unroll
             for (int j = 0; j < NT; ++j) {
-                float a0 = acc[j][2 * hr], a1 = acc[j][2 * hr + 1];
-                if (relu) {
-                    a0 = fmaxf(a0, 0.0f);
-                    a1 = fmaxf(a1, 0.0f);
+                acc[j][0] = bias[j][0];
+                acc[j][1] = bias[j][1];
+                acc[j][2] = bias[j][0];
+                acc[j][3] = bias[j][1];
+            }
+#pragma unroll
+            for (int s2 = 0; s2 < 2; ++s2) {
+                unsigned e[2][4];   // [row g / g + 8][slot], BF16 bits
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int o = off[s2][q];
+                    e[0][q] = o >= 0 ? xs[rbase + xs0 + o] : 0u;
+                    e[1][q] = o >= 0 ? xs[rbase + xs0 + o + 8] : 0u;
                 }
-                *reinterpret_cast<unsigned *>(dst + j * 8) = f2bf(a0, a1);
+                // two BF16 values per register, the lower k in the low half
+                unsigned a[4];
+                a[0] = __byte_perm(e[0][0], e[0][1], 0x5410);   // row g, k = 2 t4, 2 t4 + 1
+                a[1] = __byte_perm(e[1][0], e[1][1], 0x5410);   // row g + 8
+                a[2] = __byte_perm(e[0][2], e[0][3], 0x5410);   // row g, k + 8
+                a[3] = __byte_perm(e[1][2], e[1][3], 0x5410);   // row g + 8, k + 8
+#pragma unroll
+                for (int j = 0; j < NT; ++j) mma16816(acc[j], a, bw[s2][j][0], bw[s2][j][1]);
+            }
+            if (!row_ok) continue;
+#pragma unroll
+            for (int hr = 0; hr < 2; ++hr) {
+                const int xx = x0 + xs0 + g + 8 * hr;
+                if (xx >= W) continue;
+                bf16 *dst = y + (vrow + xx) * ycs + ycoff + 2 * t4;
+#pragma unroll
+                for (int j = 0; j < NT; ++j) {
+                    float a0 = acc[j][2 * hr], a1 = acc[j][2 * hr + 1];
+                    if (relu) {
+                        a0 = fmaxf(a0, 0.0f);
+                        a1 = fmaxf(a1, 0.0f);
+                    }
+                    *reinterpret_cast<unsigned *>(dst + j * 8) = f2bf(a0, a1);
+                }
             }
         }
     }
