@@ -142,8 +142,9 @@ bp_status cnn_relu_backward(void *g, int g_cstride, int g_coff, const void *y, i
 bp_status cnn_pack_input(const float *x, void *y, int cstride, long long nvox, void *stream);
 
 /* Input layer for a one-channel FP32 volume x [N][D][H][W] (the network's
- * first convolution, on the CUDA cores: a tensor-core layer would spend 15/16
- * of its products on zero channels):
+ * first convolution, a GEMM whose K dimension is the 27 taps, on the tensor
+ * cores with mma.sync; a GEMM over channels would spend 15/16 of its
+ * products on zero channels):
  *   y[v][y_coff + co] = act(b[co] + sum_tap w[co][tap] * bf16(x[v + tap]))
  * x is rounded to BF16 (the network's activation type) before the products,
  * which accumulate in FP32 from the bias in tap order; act = ReLU when
@@ -162,6 +163,16 @@ bp_status cnn_stem_forward(const float *x, const void *w, const float *b, void *
  * layout as cnn_stem_forward (any wd). */
 bp_status cnn_stem_wgrad(const float *x, const void *dy, int dy_cstride, int dy_coff, float *dw,
                          float *db, int n, int d, int h, int wd, int cout, void *stream);
+
+/* The input layer and the 2 x 2 x 2 max pooling that follows it in one pass
+ * (no counterpart in the paper, whose method has no network): y as
+ * cnn_stem_forward writes it, and pooled[v'][co] = max over the eight voxels
+ * of y[.][co] under v' (bit for bit cnn_maxpool2_forward on y), without
+ * reading y back. pooled is BF16 [n][d/2][h/2][wd/2][cout] (dense, 16-byte
+ * aligned); d and h even, other limits as cnn_stem_forward.
+ * BP_ERR_INVALID_ARG on bad arguments. */
+bp_status cnn_stem_pool_forward(const float *x, const void *w, const float *b, void *y, int y_cstride, int y_coff,
+                                void *pooled, int n, int d, int h, int wd, int cout, int relu, void *stream);
 
 /* Additive skip connection: nearest 2x upsampling of x (BF16
  * [N][D][H][W][c], dense) plus a skip tensor at the fine resolution:

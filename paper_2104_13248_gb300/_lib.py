@@ -77,6 +77,7 @@ PROTOTYPES = {
     "cnn_relu_backward": (_i, [_vp, _i, _i, _vp, _i, _i, _ll, _i, _vp]),
     "cnn_pack_input": (_i, [_vp, _vp, _i, _ll, _vp]),
     "cnn_stem_forward": (_i, [_vp, _vp, _vp, _vp, _i, _i, _i, _i, _i, _i, _i, _i, _vp]),
+    "cnn_stem_pool_forward": (_i, [_vp, _vp, _vp, _vp, _i, _i, _vp, _i, _i, _i, _i, _i, _i, _vp]),
     "cnn_stem_wgrad": (_i, [_vp, _vp, _i, _i, _vp, _vp, _i, _i, _i, _i, _i, _vp]),
     "cnn_conv3d_forward_head": (_i, [_vp, _i, _i, _vp, _vp, _vp, _vp, _vp, _vp, _i, _i, _i, _i, _i, _i, _i, _vp]),
     "cnn_head1_forward": (_i, [_vp, _i, _vp, _vp, _vp, _vp, _ll, _i, _vp]),

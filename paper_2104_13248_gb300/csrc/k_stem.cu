@@ -74,10 +74,16 @@ __device__ __forceinline__ void mma16816(float *c, const unsigned *a, unsigned b
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
-template <int C>
+// POOL: the 2 x 2 x 2 max pooling of the (BF16) output is written as well, to
+// pooled [N][D/2][H/2][W/2][C]: the tile holds whole pooling windows, a warp
+// takes 2 x 2 blocks of output rows and keeps the running maximum of each
+// voxel pair's rounded outputs, and the x pairs meet by a lane shuffle. The
+// maxima are those of the stored values: bit for bit cnn_maxpool2_forward.
+template <int C, bool POOL>
 __global__ void __launch_bounds__(kStThreads)
 stem_fwd_mma(const float *__restrict__ x, const bf16 *__restrict__ w, const float *__restrict__ b,
-             bf16 *__restrict__ y, int ycs, int ycoff, int D, int H, int W, int relu, int tx, int ty, int tz) {
+             bf16 *__restrict__ y, int ycs, int ycoff, bf16 *__restrict__ pooled, int D, int H, int W, int relu,
+             int tx, int ty, int tz) {
     constexpr int NT = C / 8;   // n-tiles
     constexpr int kRowsH = kStHZ * kStHY;                          // staged rows (hz, hy)
     constexpr int kRowsPerWarp = (kRowsH + kStThreads / 32 - 1) / (kStThreads / 32);
@@ -145,59 +151,116 @@ stem_fwd_mma(const float *__restrict__ x, const bf16 *__restrict__ w, const floa
         }
     }
     __syncthreads();
-    // output rows (oz, oy): warp w takes rows w, w + 8, ...; per row four x
-    // segments of 16 voxels. Shared indices are plain ints into xs (32-bit
-    // shared addressing, the tap offsets compile-time within a row).
-#pragma unroll 1
-    for (int orow = warp; orow < kStTZ * kStTY; orow += kStThreads / 32) {
-        const int oz = orow / kStTY, oy = orow - oz * kStTY;
-        const int z = z0 + oz, yy = y0 + oy;
-        const bool row_ok = z < D && yy < H;
-        const int rbase = (oz * kStHY + oy) * kStHX + g;   // tap (0,0,0) of voxel g of the row
-        const long long vrow = ((nb * D + (row_ok ? z : 0)) * H + (row_ok ? yy : 0)) * (long long)W;
+    // output rows (oz, oy): without pooling warp w takes rows w, w + 8, ...;
+    // with pooling, the 2 x 2 row blocks w, w + 8, ... Per row four x segments
+    // of 16 voxels. Shared indices are plain ints into xs (32-bit shared
+    // addressing, the tap offsets compile-time within a row).
+    auto row_mma = [&](int oz, int oy, int xs0, float (*acc)[4]) {
+        const int rbase = (oz * kStHY + oy) * kStHX + g + xs0;   // tap (0,0,0) of voxel xs0 + g of the row
 #pragma unroll
-        for (int seg = 0; seg < 4; ++seg) {
-            const int xs0 = seg * 16;
-            float acc[NT][4];
+        for (int j = 0; j < NT; ++j) {
+            acc[j][0] = bias[j][0];
+            acc[j][1] = bias[j][1];
+            acc[j][2] = bias[j][0];
+            acc[j][3] = bias[j][1];
+        }
+#pragma unroll
+        for (int s2 = 0; s2 < 2; ++s2) {
+            unsigned e[2][4];   // [row g / g + 8][slot], BF16 bits
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int o = off[s2][q];
+                e[0][q] = o >= 0 ? xs[rbase + o] : 0u;
+                e[1][q] = o >= 0 ? xs[rbase + o + 8] : 0u;
+            }
+            // two BF16 values per register, the lower k in the low half
+            unsigned a[4];
+            a[0] = __byte_perm(e[0][0], e[0][1], 0x5410);   // row g, k = 2 t4, 2 t4 + 1
+            a[1] = __byte_perm(e[1][0], e[1][1], 0x5410);   // row g + 8
+            a[2] = __byte_perm(e[0][2], e[0][3], 0x5410);   // row g, k + 8
+            a[3] = __byte_perm(e[1][2], e[1][3], 0x5410);   // row g + 8, k + 8
+#pragma unroll
+            for (int j = 0; j < NT; ++j) mma16816(acc[j], a, bw[s2][j][0], bw[s2][j][1]);
+        }
+    };
+    // act(acc) rounded to BF16 (pairs of channels) and stored at row vrow
+    auto store_row = [&](float (*acc)[4], long long vrow, int xs0, unsigned (*q)[2]) {
+#pragma unroll
+        for (int hr = 0; hr < 2; ++hr) {
 #pragma unroll
             for (int j = 0; j < NT; ++j) {
-                acc[j][0] = bias[j][0];
-                acc[j][1] = bias[j][1];
-                acc[j][2] = bias[j][0];
-                acc[j][3] = bias[j][1];
-            }
-#pragma unroll
-            for (int s2 = 0; s2 < 2; ++s2) {
-                unsigned e[2][4];   // [row g / g + 8][slot], BF16 bits
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const int o = off[s2][q];
-                    e[0][q] = o >= 0 ? xs[rbase + xs0 + o] : 0u;
-                    e[1][q] = o >= 0 ? xs[rbase + xs0 + o + 8] : 0u;
+                float a0 = acc[j][2 * hr], a1 = acc[j][2 * hr + 1];
+                if (relu) {
+                    a0 = fmaxf(a0, 0.0f);
+                    a1 = fmaxf(a1, 0.0f);
                 }
-                // two BF16 values per register, the lower k in the low half
-                unsigned a[4];
-                a[0] = __byte_perm(e[0][0], e[0][1], 0x5410);   // row g, k = 2 t4, 2 t4 + 1
-                a[1] = __byte_perm(e[1][0], e[1][1], 0x5410);   // row g + 8
-                a[2] = __byte_perm(e[0][2], e[0][3], 0x5410);   // row g, k + 8
-                a[3] = __byte_perm(e[1][2], e[1][3], 0x5410);   // row g + 8, k + 8
-#pragma unroll
-                for (int j = 0; j < NT; ++j) mma16816(acc[j], a, bw[s2][j][0], bw[s2][j][1]);
+                q[j][hr] = f2bf(a0, a1);
             }
-            if (!row_ok) continue;
+            const int xx = x0 + xs0 + g + 8 * hr;
+            if (xx >= W) continue;
+            bf16 *dst = y + (vrow + xx) * ycs + ycoff + 2 * t4;
 #pragma unroll
-            for (int hr = 0; hr < 2; ++hr) {
-                const int xx = x0 + xs0 + g + 8 * hr;
-                if (xx >= W) continue;
-                bf16 *dst = y + (vrow + xx) * ycs + ycoff + 2 * t4;
+            for (int j = 0; j < NT; ++j) *reinterpret_cast<unsigned *>(dst + j * 8) = q[j][hr];
+        }
+    };
+    if constexpr (!POOL) {
+#pragma unroll 1
+        for (int orow = warp; orow < kStTZ * kStTY; orow += kStThreads / 32) {
+            const int oz = orow / kStTY, oy = orow - oz * kStTY;
+            const int z = z0 + oz, yy = y0 + oy;
+            if (z >= D || yy >= H) continue;
+            const long long vrow = ((nb * D + z) * H + yy) * (long long)W;
 #pragma unroll
-                for (int j = 0; j < NT; ++j) {
-                    float a0 = acc[j][2 * hr], a1 = acc[j][2 * hr + 1];
-                    if (relu) {
-                        a0 = fmaxf(a0, 0.0f);
-                        a1 = fmaxf(a1, 0.0f);
+            for (int seg = 0; seg < 4; ++seg) {
+                float acc[NT][4];
+                unsigned q[NT][2];
+                row_mma(oz, oy, seg * 16, acc);
+                store_row(acc, vrow, seg * 16, q);
+            }
+        }
+    } else {
+        const int Dh = D >> 1, Hh = H >> 1, Wh = W >> 1;
+#pragma unroll 1
+        for (int blk = warp; blk < (kStTZ / 2) * (kStTY / 2); blk += kStThreads / 32) {
+            const int bz = blk / (kStTY / 2), by = blk - bz * (kStTY / 2);
+            const int z = z0 + 2 * bz, yy = y0 + 2 * by;
+            if (z >= D || yy >= H) continue;   // D, H even: the whole block is in or out
+            const long long prow = ((nb * Dh + (z >> 1)) * Hh + (yy >> 1)) * (long long)Wh;
+#pragma unroll 1
+            for (int seg = 0; seg < 4; ++seg) {
+                float pm[NT][4];
+#pragma unroll
+                for (int rr = 0; rr < 4; ++rr) {
+                    const int oz = 2 * bz + (rr >> 1), oy = 2 * by + (rr & 1);
+                    const long long vrow = ((nb * D + z0 + oz) * H + y0 + oy) * (long long)W;
+                    float acc[NT][4];
+                    unsigned q[NT][2];
+                    row_mma(oz, oy, seg * 16, acc);
+                    store_row(acc, vrow, seg * 16, q);
+#pragma unroll
+                    for (int j = 0; j < NT; ++j)
+#pragma unroll
+                        for (int hr = 0; hr < 2; ++hr) {
+                            const float2 f = bf2f(q[j][hr]);
+                            pm[j][2 * hr] = rr ? fmaxf(pm[j][2 * hr], f.x) : f.x;
+                            pm[j][2 * hr + 1] = rr ? fmaxf(pm[j][2 * hr + 1], f.y) : f.y;
+                        }
+                }
+                // voxel x and x ^ 1 are lanes l and l ^ 4 (g = l / 4)
+#pragma unroll
+                for (int j = 0; j < NT; ++j)
+#pragma unroll
+                    for (int e2 = 0; e2 < 4; ++e2) pm[j][e2] = fmaxf(pm[j][e2], __shfl_xor_sync(0xffffffffu, pm[j][e2], 4));
+                if ((g & 1) == 0) {
+#pragma unroll
+                    for (int hr = 0; hr < 2; ++hr) {
+                        const int xx = x0 + seg * 16 + g + 8 * hr;
+                        if (xx >= W) continue;
+                        bf16 *dst = pooled + (prow + (xx >> 1)) * C + 2 * t4;
+#pragma unroll
+                        for (int j = 0; j < NT; ++j)
+                            *reinterpret_cast<unsigned *>(dst + j * 8) = f2bf(pm[j][2 * hr], pm[j][2 * hr + 1]);
                     }
-                    *reinterpret_cast<unsigned *>(dst + j * 8) = f2bf(a0, a1);
                 }
             }
         }
@@ -437,6 +500,32 @@ bp_status launched(const char *what) {
 
 using namespace bp;
 
+static bp_status launch_stem(const float *x, const void *w, const float *b, void *y, int y_cstride, int y_coff,
+                             void *pooled, int n, int d, int h, int wd, int cout, int relu, void *stream) {
+    const int tx = (wd + kStTX - 1) / kStTX, ty = (h + kStTY - 1) / kStTY, tz = (d + kStTZ - 1) / kStTZ;
+    const long long nt = (long long)n * tx * ty * tz;
+    if (nt > 0x7fffffffLL) return fail(nullptr, BP_ERR_INVALID_ARG, "stem: volume too large");
+    cudaStream_t st = (cudaStream_t)stream;
+    bf16 *p = (bf16 *)pooled;
+#define STEM_CASE(C)                                                                                              \
+    case C:                                                                                                       \
+        if (p)                                                                                                    \
+            stem_fwd_mma<C, true><<<(unsigned)nt, kStThreads, 0, st>>>(x, (const bf16 *)w, b, (bf16 *)y,           \
+                                                                       y_cstride, y_coff, p, d, h, wd, relu, tx, ty, tz); \
+        else                                                                                                      \
+            stem_fwd_mma<C, false><<<(unsigned)nt, kStThreads, 0, st>>>(x, (const bf16 *)w, b, (bf16 *)y,          \
+                                                                        y_cstride, y_coff, p, d, h, wd, relu, tx, ty, tz); \
+        break;
+    switch (cout) {
+        STEM_CASE(8)
+        STEM_CASE(16)
+        STEM_CASE(24)
+        default: STEM_CASE(32)
+    }
+#undef STEM_CASE
+    return launched("stem_fwd_mma");
+}
+
 extern "C" {
 
 bp_status cnn_stem_forward(const float *x, const void *w, const float *b, void *y, int y_cstride, int y_coff,
@@ -444,17 +533,16 @@ bp_status cnn_stem_forward(const float *x, const void *w, const float *b, void *
     if (!x || !w || !y || n < 1 || d < 1 || h < 1 || wd < 4 || wd % 4 || cout < 8 || cout % 8 ||
         cout > kStemMaxC || y_cstride % 8 || y_coff % 8 || y_coff < 0 || y_coff + cout > y_cstride || !al16(y))
         return fail(nullptr, BP_ERR_INVALID_ARG, "cnn_stem_forward: bad arguments");
-    const int tx = (wd + kStTX - 1) / kStTX, ty = (h + kStTY - 1) / kStTY, tz = (d + kStTZ - 1) / kStTZ;
-    const long long nt = (long long)n * tx * ty * tz;
-    if (nt > 0x7fffffffLL) return fail(nullptr, BP_ERR_INVALID_ARG, "cnn_stem_forward: volume too large");
-    cudaStream_t st = (cudaStream_t)stream;
-    switch (cout) {
-        case 8: stem_fwd_mma<8><<<(unsigned)nt, kStThreads, 0, st>>>(x, (const bf16 *)w, b, (bf16 *)y, y_cstride, y_coff, d, h, wd, relu, tx, ty, tz); break;
-        case 16: stem_fwd_mma<16><<<(unsigned)nt, kStThreads, 0, st>>>(x, (const bf16 *)w, b, (bf16 *)y, y_cstride, y_coff, d, h, wd, relu, tx, ty, tz); break;
-        case 24: stem_fwd_mma<24><<<(unsigned)nt, kStThreads, 0, st>>>(x, (const bf16 *)w, b, (bf16 *)y, y_cstride, y_coff, d, h, wd, relu, tx, ty, tz); break;
-        default: stem_fwd_mma<32><<<(unsigned)nt, kStThreads, 0, st>>>(x, (const bf16 *)w, b, (bf16 *)y, y_cstride, y_coff, d, h, wd, relu, tx, ty, tz); break;
-    }
-    return launched("stem_fwd_mma");
+    return launch_stem(x, w, b, y, y_cstride, y_coff, nullptr, n, d, h, wd, cout, relu, stream);
+}
+
+bp_status cnn_stem_pool_forward(const float *x, const void *w, const float *b, void *y, int y_cstride, int y_coff,
+                                void *pooled, int n, int d, int h, int wd, int cout, int relu, void *stream) {
+    if (!x || !w || !y || !pooled || n < 1 || d < 2 || h < 2 || wd < 4 || wd % 4 || d % 2 || h % 2 || cout < 8 ||
+        cout % 8 || cout > kStemMaxC || y_cstride % 8 || y_coff % 8 || y_coff < 0 || y_coff + cout > y_cstride ||
+        !al16(y) || !al16(pooled))
+        return fail(nullptr, BP_ERR_INVALID_ARG, "cnn_stem_pool_forward: bad arguments");
+    return launch_stem(x, w, b, y, y_cstride, y_coff, pooled, n, d, h, wd, cout, relu, stream);
 }
 
 bp_status cnn_stem_wgrad(const float *x, const void *dy, int dy_cstride, int dy_coff, float *dw, float *db, int n,

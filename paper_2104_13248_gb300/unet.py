@@ -203,9 +203,11 @@ class UNet:
         if self.has_e1b:
             self._conv("e1a", x, 1, 0, B["e1a"], 16, 0, l1)
             self._conv("e1b", B["e1a"], 16, 0, B["s1"], 16, 0, l1)
+            check(lib.cnn_maxpool2_forward(_p(B["s1"]), 16, 0, _p(B["p1"]), *l1, 16, st))
         else:
-            self._conv("e1a", x, 1, 0, B["s1"], 16, 0, l1)
-        check(lib.cnn_maxpool2_forward(_p(B["s1"]), 16, 0, _p(B["p1"]), *l1, 16, st))
+            # the input layer writes s1 and its pooling p1 in one pass
+            check(lib.cnn_stem_pool_forward(_p(x), _p(self.w16("e1a")), _p(self.bias("e1a")), _p(B["s1"]), 16, 0,
+                                            _p(B["p1"]), n, d, h, w, 16, 1, st))
         self._conv("e2a", B["p1"], 16, 0, B["e2a"], 32, 0, l2)
         self._conv("e2b", B["e2a"], 32, 0, B["s2"], 32, 0, l2)
         check(lib.cnn_maxpool2_forward(_p(B["s2"]), 32, 0, _p(B["p2"]), *l2, 32, st))

@@ -332,6 +332,33 @@ def test_fused_head_matches_two_calls():
     _lib.check(lib.cnn_device_status(S()))
 
 
+@pytest.mark.parametrize("dims", [(1, 8, 8, 64), (2, 6, 10, 20), (1, 18, 14, 132)], ids=["tile", "ragged", "wide"])
+def test_stem_pool_matches_stem_then_pool(dims):
+    """The input layer with its 2 x 2 x 2 max pooling in one pass
+    (cnn_stem_pool_forward) writes bit for bit what cnn_stem_forward and
+    cnn_maxpool2_forward write, on whole and ragged tiles and into a channel
+    slice of a wider output."""
+    n, d, h, w = dims
+    lib = _lib.load()
+    g = torch.Generator(device="cuda").manual_seed(sum(dims))
+    x = torch.rand((n, d, h, w), generator=g, device="cuda") * 2 - 0.5
+    wt = (0.3 * torch.randn((16, 27), generator=g, device="cuda")).to(torch.bfloat16)
+    b = torch.randn(16, generator=g, device="cuda") * 0.1
+    y1 = torch.zeros((n, d, h, w, 24), dtype=torch.bfloat16, device="cuda")
+    y2 = torch.zeros_like(y1)
+    p1 = torch.empty((n, d // 2, h // 2, w // 2, 16), dtype=torch.bfloat16, device="cuda")
+    p2 = torch.empty_like(p1)
+    _lib.check(lib.cnn_stem_forward(P(x), P(wt), P(b), P(y1), 24, 8, n, d, h, w, 16, 1, S()))
+    ys = y1[..., 8:].contiguous()
+    _lib.check(lib.cnn_maxpool2_forward(P(ys), 16, 0, P(p1), n, d, h, w, 16, S()))
+    _lib.check(lib.cnn_stem_pool_forward(P(x), P(wt), P(b), P(y2), 24, 8, P(p2), n, d, h, w, 16, 1, S()))
+    _lib.check(lib.cnn_device_status(S()))
+    assert torch.equal(y1, y2)
+    assert torch.equal(p1, p2)
+    assert lib.cnn_stem_pool_forward(P(x), P(wt), P(b), P(y2), 24, 8, P(p2), n, d + 1, h, w, 16, 1,
+                                     S()) == _lib.BP_ERR_INVALID_ARG
+
+
 def test_fused_upsample_head_matches_two_calls():
     """Inference of the default network (no convolution after the last skip)
     fuses the upsampling, the skip sum and the 1x1 head in one kernel
