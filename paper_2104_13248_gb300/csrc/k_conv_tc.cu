@@ -332,16 +332,24 @@ conv3d_fwd_tc(const __grid_constant__ CUtensorMap xmap, int xco, const bf16 *__r
 // 16-byte-row planes, each of which fetched whole 32-byte sectors.
 constexpr int kPStages = 2;
 constexpr int kPThreads = 192;
-constexpr int kSwBrickBytes = kBX * kBY * kBZ * 32;                  // 74,880
-constexpr int kPStageBytes = (kSwBrickBytes + 1023) / 1024 * 1024;   // 75,776: swizzle atoms stay aligned
-static_assert(kPStageBytes % 1024 == 0, "stage bases must keep the swizzle pattern's alignment");
+// Swizzled brick of a tile TW voxels wide (TW + 2 voxels along x) and its
+// stage: 74,880 / 75,776 bytes at TW = 128, 38,016 / 38,912 at TW = 64.
+template <int TW>
+struct PGeo {
+    static constexpr int BX = TW + 2;
+    static constexpr int BRICK = BX * kBY * kBZ * 32;
+    static constexpr int STAGE = (BRICK + 1023) / 1024 * 1024;   // swizzle atoms stay aligned
+    static_assert(STAGE % 1024 == 0, "stage bases must keep the swizzle pattern's alignment");
+};
 constexpr int kPSmemLimit = 232448;   // opt-in shared memory per block (227 KB)
 
-template <int COUT>
+template <int COUT, int TW = 128>
 struct TcpCfg {
     static constexpr int WCHUNK = TcCfg<COUT>::WBYTES;
     static constexpr int TMEM_COLS = 2 * kRows * COUT;   // two accumulator sets: 128 or 256 columns
-    __host__ __device__ static constexpr int smem(int nch) { return kPStages * kPStageBytes + nch * WCHUNK + 1024; }
+    __host__ __device__ static constexpr int smem(int nch) {
+        return kPStages * PGeo<TW>::STAGE + nch * WCHUNK + 1024;
+    }
 };
 
 // Epilogues of the persistent kernel: BF16 or FP32 activations, or the fused
@@ -353,23 +361,27 @@ struct HeadArgs {
     float *out;
 };
 
-template <int COUT, int EPI>
+// TW = 64 (layers of width 64): M = 64 MMAs, whose accumulator row m sits in
+// TMEM lane 32 (m / 16) + m % 16; epilogue warp w drains rows 16 w .. 16 w + 15
+// from its first 16 lanes.
+template <int COUT, int EPI, int TW = 128>
 __global__ void __launch_bounds__(kPThreads, 1)
 conv3d_fwd_tcp(const __grid_constant__ CUtensorMap xmap, int xco, const bf16 *__restrict__ w,
                const float *__restrict__ bias, void *__restrict__ y, int ycs, int yco, int d, int h, int wd,
                int cin, int relu, int ntiles, HeadArgs head, unsigned *err, unsigned long long timeout_ns) {
-    using Cfg = TcpCfg<COUT>;
+    using Cfg = TcpCfg<COUT, TW>;
+    using G = PGeo<TW>;
     extern __shared__ unsigned char smem_raw[];
     unsigned char *smem = reinterpret_cast<unsigned char *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     unsigned char *stage0 = smem;
-    unsigned char *wsm = smem + kPStages * kPStageBytes;
+    unsigned char *wsm = smem + kPStages * G::STAGE;
     __shared__ __align__(8) unsigned long long full[kPStages], empty[kPStages], tfull[2], tempty[2], done_bar;
     __shared__ unsigned tmem_base;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int nch = cin / 16;
-    const int ntx = wd / 128, nty = h, ntz = d / 4;
+    const int ntx = wd / TW, nty = h, ntz = d / 4;
 
     if (tid == 0) {
         for (int s = 0; s < kPStages; ++s) {
@@ -424,8 +436,8 @@ conv3d_fwd_tcp(const __grid_constant__ CUtensorMap xmap, int xco, const bf16 *__
                     ok = false;
                     break;
                 }
-                mbar_arrive_expect_tx(&full[s], (unsigned)kSwBrickBytes);
-                tma_load_5d(stage0 + s * kPStageBytes, &xmap, xco + ch * 16, tx * 128 - 1, ty - 1, tz * 4 - 1, nb,
+                mbar_arrive_expect_tx(&full[s], (unsigned)G::BRICK);
+                tma_load_5d(stage0 + s * G::STAGE, &xmap, xco + ch * 16, tx * TW - 1, ty - 1, tz * 4 - 1, nb,
                             &full[s]);
                 issued[s] = (int)ph;
                 if (++s == kPStages) {
@@ -473,7 +485,7 @@ conv3d_fwd_tcp(const __grid_constant__ CUtensorMap xmap, int xco, const bf16 *__
                 }
                 __syncwarp();
                 asm volatile("tcgen05.fence::after_thread_sync;");
-                const unsigned a0 = s_u32(stage0 + s * kPStageBytes) >> 4;
+                const unsigned a0 = s_u32(stage0 + s * G::STAGE) >> 4;
                 const unsigned b0 = s_u32(wsm + ch * Cfg::WCHUNK) >> 4;
                 const unsigned first_acc = ch > 0 ? 1u : 0u;
 #pragma unroll
@@ -484,10 +496,10 @@ conv3d_fwd_tcp(const __grid_constant__ CUtensorMap xmap, int xco, const bf16 *__
                         const int zp = (g == 0) ? (q == 0 ? 3 : q == 1 ? 0 : q - 1 + (q >= 4 ? 1 : 0)) : q;
                         const int rz_hi = zp < 3 ? zp : 3, rz_lo = zp > 2 ? zp - 2 : 0;
                         const int nrows = rz_hi - rz_lo + 1;
-                        const unsigned a16 = (unsigned)(2 * ((zp * kBY + dy) * kBX + dx));
+                        const unsigned a16 = (unsigned)(2 * ((zp * kBY + dy) * G::BX + dx));
                         const unsigned b16 = (unsigned)(((((dy * 3 + dx) * 2) * 3 + (zp - rz_hi)) * COUT * 16) >> 4);
                         const unsigned id = (1u << 4) | (1u << 7) | (1u << 10) |
-                                            ((unsigned)((nrows * COUT) >> 3) << 17) | ((unsigned)(128 >> 4) << 24);
+                                            ((unsigned)((nrows * COUT) >> 3) << 17) | ((unsigned)(TW >> 4) << 24);
                         const unsigned acc = (g == 0 && q <= 1) ? first_acc : 1u;
                         const unsigned long long ad = lbo_sbo_a | (unsigned long long)((a0 + a16) & 0x3FFF);
                         const unsigned long long bd = lbo_sbo_b | (unsigned long long)((b0 + b16) & 0x3FFF);
@@ -554,12 +566,13 @@ conv3d_fwd_tcp(const __grid_constant__ CUtensorMap xmap, int xco, const bf16 *__
             t /= nty;
             const int tz = t % ntz;
             const int nb = t / ntz;
-            const int xx = tx * 128 + warp * 32 + lane;
+            const int xx = tx * TW + (TW == 128 ? warp * 32 + lane : warp * 16 + lane);
 #pragma unroll 1
             for (int r = 0; r < kRows; ++r) {
                 float v[COUT];
                 TmemRow<COUT>::load(tmem + ((unsigned)(warp * 32) << 16) + (unsigned)(a * kRows * COUT + (3 - r) * COUT),
                                     v);
+                if (TW == 64 && lane >= 16) continue;   // M = 64: rows in the first 16 lanes only
                 const size_t vox = (((size_t)nb * d + tz * 4 + r) * h + ty) * (size_t)wd + xx;
 #pragma unroll
                 for (int c = 0; c < COUT; ++c) {
@@ -703,10 +716,15 @@ cudaError_t conv_fwd_tc(const void *x, int xcs, int xco, const void *w, const fl
     if (nblk > 0x7fffffffLL) return cudaErrorInvalidValue;
     const unsigned long long timeout_ns = 2000000000ull;
     const int nch = cin / 16;
-    const int psmem = cout == 16 ? TcpCfg<16>::smem(nch) : TcpCfg<32>::smem(nch);
-    if (TW == 128 && g_tc_mode == 1 && psmem <= kPSmemLimit) {
+    // the persistent kernel keeps every chunk's weights resident; Cout 64
+    // (width-64 layers) runs as two launches of 32 output channels, each
+    // writing its channel slice (the bricks stay in L2 between them)
+    const int cpl = cout == 64 ? 32 : cout;   // output channels per launch
+    const int psmem = TW == 128 ? (cpl == 16 ? TcpCfg<16, 128>::smem(nch) : TcpCfg<32, 128>::smem(nch))
+                                : (cpl == 16 ? TcpCfg<16, 64>::smem(nch) : TcpCfg<32, 64>::smem(nch));
+    if (g_tc_mode == 1 && psmem <= kPSmemLimit && (TW == 64 || cout != 64)) {
         // rows of 16 channels (32 bytes), 32-byte swizzle
-        cuuint32_t box16[5] = {16, (cuuint32_t)kBX, (cuuint32_t)kBY, (cuuint32_t)kBZ, 1};
+        cuuint32_t box16[5] = {16, (cuuint32_t)(TW + 2), (cuuint32_t)kBY, (cuuint32_t)kBZ, 1};
         r = encode_fn()(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<void *>(x), dims, strides, box16, estr,
                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -723,19 +741,32 @@ cudaError_t conv_fwd_tc(const void *x, int xcs, int xco, const void *w, const fl
         }
         const unsigned grid = (unsigned)(nblk < g_num_sms[dev] ? nblk : g_num_sms[dev]);
         const HeadArgs ha{head_w, head_b, head_res, head_out};
-#define TCP_CASE(C, E)                                                                                      \
-    {                                                                                                       \
-        auto k = conv3d_fwd_tcp<C, E>;                                                                      \
-        e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, psmem);                    \
-        if (e != cudaSuccess) return e;                                                                     \
-        k<<<grid, kPThreads, psmem, st>>>(map, xco, (const bf16 *)w, b, y, ycs, yco, d, h, wd, cin, relu,   \
-                                          (int)nblk, ha, err, timeout_ns);                                 \
-        return cudaGetLastError();                                                                          \
+#define TCP_CASE(C, E, T)                                                                                       \
+    {                                                                                                           \
+        auto k = conv3d_fwd_tcp<C, E, T>;                                                                       \
+        e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, psmem);                        \
+        if (e != cudaSuccess) return e;                                                                         \
+        for (int c0 = 0; c0 < cout; c0 += C) {                                                                  \
+            k<<<grid, kPThreads, psmem, st>>>(map, xco, (const bf16 *)w + (size_t)c0 * 27 * cin, b ? b + c0 : b, \
+                                              y, ycs, yco + c0, d, h, wd, cin, relu, (int)nblk, ha, err,        \
+                                              timeout_ns);                                                      \
+            e = cudaGetLastError();                                                                             \
+            if (e != cudaSuccess) return e;                                                                     \
+        }                                                                                                       \
+        return cudaSuccess;                                                                                     \
     }
-        if (cout == 16) {
-            if (fused_head) TCP_CASE(16, kEpiHead) else if (yf32) TCP_CASE(16, kEpiF32) else TCP_CASE(16, kEpiBf16)
+        if (TW == 128) {
+            if (cpl == 16) {
+                if (fused_head) TCP_CASE(16, kEpiHead, 128) else if (yf32) TCP_CASE(16, kEpiF32, 128) else TCP_CASE(16, kEpiBf16, 128)
+            } else {
+                if (fused_head) TCP_CASE(32, kEpiHead, 128) else if (yf32) TCP_CASE(32, kEpiF32, 128) else TCP_CASE(32, kEpiBf16, 128)
+            }
         } else {
-            if (fused_head) TCP_CASE(32, kEpiHead) else if (yf32) TCP_CASE(32, kEpiF32) else TCP_CASE(32, kEpiBf16)
+            if (cpl == 16) {
+                if (yf32) TCP_CASE(16, kEpiF32, 64) else TCP_CASE(16, kEpiBf16, 64)
+            } else {
+                if (yf32) TCP_CASE(32, kEpiF32, 64) else TCP_CASE(32, kEpiBf16, 64)
+            }
         }
 #undef TCP_CASE
     }
