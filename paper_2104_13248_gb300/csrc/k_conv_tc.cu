@@ -623,6 +623,299 @@ conv3d_fwd_tcp(const __grid_constant__ CUtensorMap xmap, int xco, const bf16 *__
     }
 }
 
+// ---------------------------------------------------------------------------
+// The one-channel input layer (3x3x3, 1 -> 16 channels) on tcgen05, for widths
+// that are multiples of 8. With one input channel the usual implicit GEMM
+// (K = channels of a tap) would spend 15/16 of its products on zero channels;
+// here the taps along x go into K instead. A tile is 8 outputs along x,
+// 128 along y and 2 along z. Every staged input row holds the 16 values
+// x0 - 4 .. x0 + 11 (K), and the weights of each (kz, ky) become a banded
+// matrix B[16 xo + c][j] = w[c][kz][ky][j - xo - 3] (zero off the band), so
+//   D[y][16 xo + c] += A_(z, kz, ky)[y][j] B_(kz, ky)[16 xo + c][j]
+// with M = 128 rows along y, N = 128 (8 voxels x 16 channels), K = 16: nine
+// MMAs per output slice, 2304 products per voxel for the 432 of the tap sum.
+// A TMEM lane is one y row, so an epilogue thread holds all 16 channels of
+// its voxels: whole-voxel 16-byte stores, and the 2 x 2 x 2 pooling needs one
+// lane shuffle (the y pair); the x pair and the z pair are its own columns.
+// Persistent: two CTAs per SM, each builds the banded weights once and walks
+// the tiles; the next tile's input is loaded into registers while the MMAs of
+// the current one run.
+constexpr int kSxT = 8, kSyT = 128, kSzT = 2;
+constexpr int kSRows = kSyT + 2;                          // staged rows per plane (y halo)
+constexpr int kSPlanes = kSzT + 2;                        // staged planes (z halo)
+constexpr int kSHalf = kSPlanes * kSRows * 16;            // bytes of one 8-value K half: 8320
+constexpr int kSABytes = 2 * kSHalf;                      // staged input (A): 16640
+constexpr int kSBBytes = 9 * 2 * 128 * 16;                // banded weights (B): 36864
+constexpr int kSThreads = 256;
+constexpr int kSCBytes = (kSThreads / 32) * 32 * 128;   // epilogue staging: 32 rows x 128 bytes a warp
+constexpr int kSChunks = kSPlanes * kSRows * 4;           // float4 chunks of a staged tile: 2080
+constexpr int kSPer = (kSChunks + kSThreads - 1) / kSThreads;   // 9 per thread
+// 86 KB a CTA: two CTAs share an SM (each holds 256 TMEM columns), never three
+constexpr int kSSmem = 86 * 1024;
+static_assert(kSABytes + kSBBytes + kSCBytes + 128 <= kSSmem, "stem buffers exceed the shared-memory request");
+static_assert(3 * (kSSmem + 2048) > 228 * 1024, "a third CTA per SM would wait for tensor memory");
+static_assert(kSHalf % 16 == 0, "operand halves start 16-byte aligned");
+
+__device__ __forceinline__ void tmem_ld32(unsigned addr, float *v) {
+    unsigned r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(addr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// (lo, hi) rounded to BF16 and packed (lo in the low half); with RELU a
+// negative result becomes +0 (max(x, 0) commutes with the rounding).
+template <bool RELU>
+__device__ __forceinline__ unsigned cvt_bf16x2(float lo, float hi) {
+    unsigned r;
+    if constexpr (RELU)
+        asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+    else
+        asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+    return r;
+}
+
+__device__ __forceinline__ unsigned max_bf16x2(unsigned a, unsigned b) {
+    unsigned r;
+    asm("max.bf16x2 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b));
+    return r;
+}
+
+__device__ __forceinline__ unsigned bf16x2_bits(float lo, float hi) {
+    __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<unsigned *>(&h);
+}
+
+template <bool POOL, bool RELU>
+__global__ void __launch_bounds__(kSThreads, 2)
+stem_fwd_tc(const float *__restrict__ x, const bf16 *__restrict__ w, const float *__restrict__ b,
+            bf16 *__restrict__ y, int ycs, int yco, bf16 *__restrict__ pooled, int D, int H, int W,
+            int ntiles, unsigned *err, unsigned long long timeout_ns) {
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char *smem = reinterpret_cast<unsigned char *>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~(uintptr_t)127);
+    unsigned char *As = smem;              // [half][plane][row][8 BF16]: staged input
+    unsigned char *Bs = smem + kSABytes;   // [kz ky][half][16 xo + c][8 BF16]: banded weights
+    unsigned char *Cs = Bs + kSBBytes;     // per warp [row][8 x 16 bytes], 16-byte slots XOR-swizzled by row
+    __shared__ __align__(8) unsigned long long mma_bar;
+    __shared__ unsigned tmem_base;
+    __shared__ float wsm[16 * 27];
+    __shared__ float bsm[16];   // bias, carried by the MMA: K slots 0 and 1 of every staged row hold 1.0
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int ntx = W / kSxT, nty = (H + kSyT - 1) / kSyT, ntz = (D + kSzT - 1) / kSzT;
+
+    for (int i = tid; i < 16 * 27; i += kSThreads) wsm[i] = __bfloat162float(w[i]);
+    if (tid < 16) bsm[tid] = b ? b[tid] : 0.0f;
+    if (tid == 0) {
+        mbar_init(&mma_bar, 1);
+        fence_barrier_init();
+    }
+    __syncthreads();
+    // banded weights: 16-byte row (g = 3 kz + ky, half, n = 16 xo + c) holds j = 8 half .. 8 half + 7.
+    // The band uses j = 3 .. 12; in (kz, ky) = (0, 0), j = 0 and 1 carry the
+    // bias as hi = bf16(b) and lo = bf16(b - hi) (within 2^-16 of b), against
+    // the 1.0 staged in those K slots.
+    for (int q = tid; q < 9 * 2 * 128; q += kSThreads) {
+        const int nn = q & 127, half = (q >> 7) & 1, g = q >> 8;
+        const int xo = nn >> 4, c = nn & 15;
+        const float bhi = __bfloat162float(__float2bfloat16_rn(bsm[c]));
+        const float blo = __bfloat162float(__float2bfloat16_rn(bsm[c] - bhi));
+        unsigned v[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int j0 = 8 * half + 2 * e, k0 = j0 - xo - 3, k1 = k0 + 1;
+            float f0 = (k0 >= 0 && k0 < 3) ? wsm[c * 27 + g * 3 + k0] : 0.0f;
+            float f1 = (k1 >= 0 && k1 < 3) ? wsm[c * 27 + g * 3 + k1] : 0.0f;
+            if (g == 0 && j0 == 0) {
+                f0 = bhi;
+                f1 = blo;
+            }
+            v[e] = bf16x2_bits(f0, f1);
+        }
+        *reinterpret_cast<uint4 *>(Bs + q * 16) = make_uint4(v[0], v[1], v[2], v[3]);
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(s_u32(&tmem_base)),
+                     "r"(256));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // generic writes -> tensor core reads
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const unsigned tmem = tmem_base;
+
+    // Input chunk i of this thread: float4 q = tid + 256 i of the staged tile,
+    // row q / 4 (plane p, row r), values 4 (q mod 4) .. + 3 of the K window.
+    float4 pre[kSPer];
+    auto load_tile = [&](int tile) {
+        int t = tile;
+        const int tx = t % ntx;
+        t /= ntx;
+        const int ty = t % nty;
+        t /= nty;
+        const int tz = t % ntz;
+        const long long nb = t / ntz;
+#pragma unroll
+        for (int i = 0; i < kSPer; ++i) {
+            const int q = tid + kSThreads * i;
+            const int row = q >> 2, part = q & 3;
+            const int p = row / kSRows, r = row - p * kSRows;
+            const int z = tz * kSzT - 1 + p, yy = ty * kSyT - 1 + r, xx = tx * kSxT - 4 + 4 * part;
+            const bool ok = q < kSChunks && z >= 0 && z < D && yy >= 0 && yy < H && xx >= 0 && xx < W;
+            pre[i] = ok ? __ldg(reinterpret_cast<const float4 *>(x + ((nb * D + z) * H + yy) * (long long)W + xx))
+                        : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+    };
+    auto store_tile = [&]() {
+#pragma unroll
+        for (int i = 0; i < kSPer; ++i) {
+            const int q = tid + kSThreads * i;
+            if (q < kSChunks) {
+                const int row = q >> 2, part = q & 3;
+                const unsigned a = s_u32(As + (part >> 1) * kSHalf + row * 16 + (part & 1) * 8);
+                // K slots 0 and 1 (values x0 - 4, x0 - 3, outside every output's taps) hold 1.0
+                const unsigned lo = part == 0 ? 0x3F803F80u : bf16x2_bits(pre[i].x, pre[i].y);
+                asm volatile("st.shared.v2.b32 [%0], {%1, %2};" ::"r"(a), "r"(lo), "r"(bf16x2_bits(pre[i].z, pre[i].w))
+                             : "memory");
+            }
+        }
+    };
+
+    const int quarter = warp & 3, xh = warp >> 2;   // TMEM lanes 32 quarter .., voxels xo = 4 xh .. 4 xh + 3
+    unsigned phase = 0;
+    bool timed_out = false;
+    if (blockIdx.x < ntiles) load_tile(blockIdx.x);
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        store_tile();
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        if (tid == 0) {
+            // A: no swizzle, K halves kSHalf apart (LBO), 8-row groups 128 bytes apart (SBO)
+            const unsigned a_base = s_u32(As), b_base = s_u32(Bs);
+            const unsigned idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(128 >> 3) << 17) |
+                                   ((unsigned)(128 >> 4) << 24);
+#pragma unroll
+            for (int zz = 0; zz < kSzT; ++zz)
+#pragma unroll
+                for (int g = 0; g < 9; ++g) {
+                    const int kz = g / 3, ky = g % 3;
+                    const unsigned long long ad = smem_desc(a_base + ((zz + kz) * kSRows + ky) * 16, kSHalf, 128);
+                    const unsigned long long bd = smem_desc(b_base + g * 4096, 2048, 128);
+                    asm volatile(
+                        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem + (unsigned)(zz * 128)),
+                        "l"(ad), "l"(bd), "r"(idesc), "r"(g > 0 ? 1u : 0u));
+                }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                s_u32(&mma_bar)));
+        }
+        const int tile_now = tile;
+        if (tile + (int)gridDim.x < ntiles) load_tile(tile + gridDim.x);   // lands while the MMAs run
+        const bool ok = mbar_wait_bounded(&mma_bar, phase, timeout_ns);
+        phase ^= 1u;
+        if (__syncthreads_or(!ok)) {
+            timed_out = true;
+            break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        // ---- epilogue: lane = row y0 + 32 quarter + lane, columns 16 xo + c of slices z0, z0 + 1
+        int t = tile_now;
+        const int tx = t % ntx;
+        t /= ntx;
+        const int ty = t % nty;
+        t /= nty;
+        const int tz = t % ntz;
+        const long long nb = t / ntz;
+        const int yy = ty * kSyT + 32 * quarter + lane;
+        const bool yok = yy < H;
+        // A thread's row is 4 voxels = 128 contiguous bytes of y; the rows of a
+        // warp lie W voxels apart. Each warp stages its 32 rows in shared memory
+        // and stores them transposed: 8 lanes per row, 4 whole rows (128-byte
+        // lines) per instruction, where direct stores would touch 32 lines each.
+        unsigned char *cw = Cs + warp * 4096;
+        const int x0w = tx * kSxT + 4 * xh;   // first voxel of the warp's rows
+        unsigned mx[2][8];                    // running maxima of the pooling windows, BF16 pairs
+#pragma unroll 1
+        for (int zz = 0; zz < kSzT; ++zz) {
+            const int z = tz * kSzT + zz;
+#pragma unroll
+            for (int pp = 0; pp < 2; ++pp) {   // voxels 4 xh + 2 pp, + 1
+                float v[32];
+                tmem_ld32(tmem + ((unsigned)(32 * quarter) << 16) + (unsigned)(zz * 128 + (4 * xh + 2 * pp) * 16), v);
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    unsigned q[8];
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) {
+                        q[k] = cvt_bf16x2<RELU>(v[16 * e + 2 * k], v[16 * e + 2 * k + 1]);
+                        if constexpr (POOL) mx[pp][k] = (zz == 0 && e == 0) ? q[k] : max_bf16x2(mx[pp][k], q[k]);
+                    }
+                    const int xo = 2 * pp + e;
+                    const int s0 = (2 * xo) ^ (lane & 7), s1 = (2 * xo + 1) ^ (lane & 7);
+                    *reinterpret_cast<uint4 *>(cw + lane * 128 + s0 * 16) = make_uint4(q[0], q[1], q[2], q[3]);
+                    *reinterpret_cast<uint4 *>(cw + lane * 128 + s1 * 16) = make_uint4(q[4], q[5], q[6], q[7]);
+                }
+            }
+            __syncwarp();
+            // 8 lanes per row, 4 rows (128-byte lines) per store instruction
+            const int k = lane & 7;
+            bf16 *yrow = y + (((nb * D + z) * H + ty * kSyT + 32 * quarter) * (long long)W + x0w + (k >> 1)) * ycs +
+                         yco + (k & 1) * 8;
+#pragma unroll
+            for (int it = 0; it < 8; ++it) {
+                const int r = 4 * it + (lane >> 3);   // row of the warp
+                const uint4 val = *reinterpret_cast<const uint4 *>(cw + r * 128 + ((k ^ (r & 7)) * 16));
+                if (ty * kSyT + 32 * quarter + r < H && z < D)
+                    *reinterpret_cast<uint4 *>(yrow + (long long)r * W * ycs) = val;
+            }
+            __syncwarp();   // the staging rows are rewritten for the next slice
+        }
+        if constexpr (POOL) {
+            // the y pair is lanes l and l ^ 1 (D, H even: a pair is whole or outside)
+#pragma unroll
+            for (int pp = 0; pp < 2; ++pp)
+#pragma unroll
+                for (int k = 0; k < 8; ++k) mx[pp][k] = max_bf16x2(mx[pp][k], __shfl_xor_sync(0xffffffffu, mx[pp][k], 1));
+            if (yok && (lane & 1) == 0) {
+                const int Dh = D >> 1, Hh = H >> 1, Wh = W >> 1;
+#pragma unroll
+                for (int pp = 0; pp < 2; ++pp) {
+                    uint4 *dst = reinterpret_cast<uint4 *>(
+                        pooled + (((nb * Dh + tz) * Hh + (yy >> 1)) * (long long)Wh + (x0w >> 1) + pp) * 16);
+                    dst[0] = make_uint4(mx[pp][0], mx[pp][1], mx[pp][2], mx[pp][3]);
+                    dst[1] = make_uint4(mx[pp][4], mx[pp][5], mx[pp][6], mx[pp][7]);
+                }
+            }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        __syncthreads();   // TMEM read and the staged tile consumed before the next tile's MMAs
+    }
+    if (timed_out) {
+        if (tid == 0) {
+            atomicOr(err, DEV_ERR_TIMEOUT);
+            // the MMAs in flight must finish before their accumulators are freed
+            mbar_wait_bounded(&mma_bar, phase ^ 1u, timeout_ns);
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256));
+    }
+}
+
 typedef CUresult (*PFN_encode5)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
                                 const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
@@ -665,6 +958,22 @@ static cudaError_t tc_err_address(unsigned **out) {
         g_tc_err_addr[dev] = static_cast<unsigned *>(p);
     }
     *out = g_tc_err_addr[dev];
+    return cudaSuccess;
+}
+
+// Streaming multiprocessors of the current device (cached per device).
+static cudaError_t sm_count(int *out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (!g_num_sms[dev]) {
+        int v = 0;
+        e = cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
+        g_num_sms[dev] = v > 0 ? v : 1;
+    }
+    *out = g_num_sms[dev];
     return cudaSuccess;
 }
 
@@ -729,17 +1038,10 @@ cudaError_t conv_fwd_tc(const void *x, int xcs, int xco, const void *w, const fl
                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
-        int dev = 0;
-        cudaError_t e = cudaGetDevice(&dev);
+        int sms = 0;
+        cudaError_t e = sm_count(&sms);
         if (e != cudaSuccess) return e;
-        if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-        if (!g_num_sms[dev]) {
-            int v = 0;
-            e = cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
-            if (e != cudaSuccess) return e;
-            g_num_sms[dev] = v > 0 ? v : 1;
-        }
-        const unsigned grid = (unsigned)(nblk < g_num_sms[dev] ? nblk : g_num_sms[dev]);
+        const unsigned grid = (unsigned)(nblk < sms ? nblk : sms);
         const HeadArgs ha{head_w, head_b, head_res, head_out};
 #define TCP_CASE(C, E, T)                                                                                       \
     {                                                                                                           \
@@ -795,6 +1097,37 @@ cudaError_t conv_fwd_tc(const void *x, int xcs, int xco, const void *w, const fl
         }
     }
 #undef TC_CASE
+}
+
+// The tcgen05 input layer takes Cout 16 at widths that are multiples of 8,
+// with 16-byte aligned tensors and channel offsets, unless
+// cnn_set_tensor_path(0) selects mma.sync.
+bool stem_tc_applies(const float *x, const void *y, int ycs, int yco, const void *pooled, int wd, int cout) {
+    return g_tc_mode != 0 && cout == 16 && wd >= kSxT && wd % kSxT == 0 && ycs % 8 == 0 && yco % 8 == 0 &&
+           (reinterpret_cast<uintptr_t>(x) & 15) == 0 && (reinterpret_cast<uintptr_t>(y) & 15) == 0 &&
+           (reinterpret_cast<uintptr_t>(pooled) & 15) == 0;
+}
+
+cudaError_t stem_fwd_tc_launch(const float *x, const void *w, const float *b, void *y, int ycs, int yco,
+                               void *pooled, int n, int d, int h, int wd, int relu, cudaStream_t st) {
+    unsigned *err = nullptr;
+    cudaError_t e = tc_err_address(&err);
+    if (e != cudaSuccess) return e;
+    const long long nt = (long long)n * (wd / kSxT) * ((h + kSyT - 1) / kSyT) * ((d + kSzT - 1) / kSzT);
+    if (nt <= 0) return cudaSuccess;
+    if (nt > 0x7fffffffLL) return cudaErrorInvalidValue;
+    int sms = 0;
+    e = sm_count(&sms);
+    if (e != cudaSuccess) return e;
+    const long long g2 = 2LL * sms;
+    const unsigned grid = (unsigned)(nt < g2 ? nt : g2);
+    auto k = pooled ? (relu ? stem_fwd_tc<true, true> : stem_fwd_tc<true, false>)
+                    : (relu ? stem_fwd_tc<false, true> : stem_fwd_tc<false, false>);
+    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, kSSmem);
+    if (e != cudaSuccess) return e;
+    k<<<grid, kSThreads, kSSmem, st>>>(x, (const bf16 *)w, b, (bf16 *)y, ycs, yco, (bf16 *)pooled, d, h, wd,
+                                       (int)nt, err, 2000000000ull);
+    return cudaGetLastError();
 }
 
 }  // namespace bp

@@ -500,8 +500,20 @@ bp_status launched(const char *what) {
 
 using namespace bp;
 
+namespace bp {
+bool stem_tc_applies(const float *x, const void *y, int ycs, int yco, const void *pooled, int wd, int cout);
+cudaError_t stem_fwd_tc_launch(const float *x, const void *w, const float *b, void *y, int ycs, int yco,
+                               void *pooled, int n, int d, int h, int wd, int relu, cudaStream_t st);
+}  // namespace bp
+
 static bp_status launch_stem(const float *x, const void *w, const float *b, void *y, int y_cstride, int y_coff,
                              void *pooled, int n, int d, int h, int wd, int cout, int relu, void *stream) {
+    // tcgen05 with the x taps in K (k_conv_tc.cu) where its tile fits
+    if (stem_tc_applies(x, y, y_cstride, y_coff, pooled, wd, cout)) {
+        cudaError_t e = stem_fwd_tc_launch(x, w, b, y, y_cstride, y_coff, pooled, n, d, h, wd, relu,
+                                           (cudaStream_t)stream);
+        return e == cudaSuccess ? BP_OK : cuda_fail(nullptr, e, "stem_fwd_tc");
+    }
     const int tx = (wd + kStTX - 1) / kStTX, ty = (h + kStTY - 1) / kStTY, tz = (d + kStTZ - 1) / kStTZ;
     const long long nt = (long long)n * tx * ty * tz;
     if (nt > 0x7fffffffLL) return fail(nullptr, BP_ERR_INVALID_ARG, "stem: volume too large");

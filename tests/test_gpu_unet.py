@@ -149,7 +149,8 @@ def test_pool_upsample_relu():
 @pytest.mark.parametrize("shape", [(1, 8, 12, 16, 16), (2, 5, 7, 20, 16), (1, 4, 4, 8, 32), (1, 6, 9, 132, 8)],
                          ids=lambda s: "n%d_%dx%dx%d_co%d" % s)
 def test_stem_forward_wgrad(shape):
-    """The one-channel input layer (CUDA cores) against the FP64 oracle's
+    """The one-channel input layer (tcgen05 at widths that are multiples of
+    8, mma.sync otherwise) against the FP64 oracle's
     convolution with Cin = 1, the input pre-rounded to BF16 as the kernel
     rounds it: forward FP32-accurate before the BF16 store, weight and bias
     gradients within 1e-4."""
@@ -190,6 +191,56 @@ def test_stem_rejects_bad_layouts():
     assert lib.cnn_stem_forward(P(x), P(w), None, P(y), 16, 0, 1, 4, 4, 3, 16, 1, S()) == _lib.BP_ERR_INVALID_ARG
     assert lib.cnn_stem_forward(P(x), P(w), None, P(y), 16, 0, 1, 4, 4, 4, 12, 1, S()) == _lib.BP_ERR_INVALID_ARG
     assert lib.cnn_stem_wgrad(P(x), P(y), 16, 8, P(x), None, 1, 4, 4, 4, 16, S()) == _lib.BP_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("dims", [(1, 4, 130, 16), (2, 5, 12, 8), (1, 6, 128, 24), (1, 2, 256, 40)],
+                         ids=["ragged_h", "odd_d_batch2", "tile_h", "two_y_tiles"])
+def test_stem_tensor_core_against_oracle_and_mma_sync(dims):
+    """The tcgen05 input layer (x taps in K, banded weights): a channel slice
+    of a wider output, ragged y tiles, an odd depth, a batch of two and a
+    single x tile whose halo lies outside on both sides. Against the FP64
+    oracle within BF16 output rounding, against the mma.sync kernel on the
+    same inputs within one BF16 step (the two sum the same products in
+    different orders), and with the pooling (where d and h are even) bit for
+    bit the separate pooling."""
+    n, d, h, w = dims
+    lib = _lib.load()
+    rng = np.random.default_rng(sum(dims) + 3)
+    x = rng.normal(size=(n, d, h, w)).astype(np.float32)
+    wt = bf16_round(rng.normal(size=(16, 27, 1)) * 0.2)
+    b = rng.normal(size=16).astype(np.float32)
+    xd = torch.from_numpy(x).cuda()
+    wd = torch.from_numpy(wt.astype(np.float32)).cuda().to(torch.bfloat16)
+    bd = torch.from_numpy(b).cuda()
+    ref = np.maximum(oracle.conv3d(bf16_round(x)[..., None], wt, b), 0)
+    outs = []
+    for path in (1, 0):
+        _lib.check(lib.cnn_set_tensor_path(path))
+        try:
+            y = torch.zeros((n, d, h, w, 24), dtype=torch.bfloat16, device="cuda")
+            _lib.check(lib.cnn_stem_forward(P(xd), P(wd), P(bd), P(y), 24, 8, n, d, h, w, 16, 1, S()))
+            _lib.check(lib.cnn_device_status(S()))
+        finally:
+            _lib.check(lib.cnn_set_tensor_path(1))
+        yb = y.float().cpu().numpy()
+        assert np.all(yb[..., :8] == 0)
+        assert rel(yb[..., 8:], ref) <= 8e-3
+        outs.append(yb[..., 8:])
+    tc, ms = outs
+    step = np.maximum(np.abs(tc), np.abs(ms)) * 2.0 ** -7 + 1e-5   # sums near zero may differ in sign before ReLU
+    assert np.all(np.abs(tc - ms) <= step)
+    if d % 2 == 0 and h % 2 == 0:
+        y1 = torch.zeros((n, d, h, w, 24), dtype=torch.bfloat16, device="cuda")
+        y2 = torch.zeros_like(y1)
+        p1 = torch.empty((n, d // 2, h // 2, w // 2, 16), dtype=torch.bfloat16, device="cuda")
+        p2 = torch.empty_like(p1)
+        _lib.check(lib.cnn_stem_forward(P(xd), P(wd), P(bd), P(y1), 24, 8, n, d, h, w, 16, 1, S()))
+        ys = y1[..., 8:].contiguous()
+        _lib.check(lib.cnn_maxpool2_forward(P(ys), 16, 0, P(p1), n, d, h, w, 16, S()))
+        _lib.check(lib.cnn_stem_pool_forward(P(xd), P(wd), P(bd), P(y2), 24, 8, P(p2), n, d, h, w, 16, 1, S()))
+        _lib.check(lib.cnn_device_status(S()))
+        assert torch.equal(y1, y2)
+        assert torch.equal(p1, p2)
 
 
 def test_head1_forward_backward():
