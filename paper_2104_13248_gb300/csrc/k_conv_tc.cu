@@ -634,27 +634,36 @@ conv3d_fwd_tcp(const __grid_constant__ CUtensorMap xmap, int xco, const bf16 *__
 //   D[y][16 xo + c] += A_(z, kz, ky)[y][j] B_(kz, ky)[16 xo + c][j]
 // with M = 128 rows along y, N = 128 (8 voxels x 16 channels), K = 16: nine
 // MMAs per output slice, 2304 products per voxel for the 432 of the tap sum.
+// K slots 0 and 1 (outside every output's taps) are staged as 1.0 and carry
+// the bias (hi and lo BF16 parts) in the weights of (kz, ky) = (0, 0).
 // A TMEM lane is one y row, so an epilogue thread holds all 16 channels of
-// its voxels: whole-voxel 16-byte stores, and the 2 x 2 x 2 pooling needs one
-// lane shuffle (the y pair); the x pair and the z pair are its own columns.
-// Persistent: two CTAs per SM, each builds the banded weights once and walks
-// the tiles; the next tile's input is loaded into registers while the MMAs of
-// the current one run.
+// its voxels: whole-voxel stores, and the 2 x 2 x 2 pooling needs one lane
+// shuffle (the y pair); the x pair and the z pair are its own columns.
+//
+// Persistent and warp-specialised, one CTA per SM: four producer warps load
+// a tile's input (FP32), round it to BF16 and stage it in one of two A
+// buffers; one thread issues the MMAs into one of two TMEM accumulator sets
+// (256 columns each), committing each output slice separately; eight
+// epilogue warps drain a slice (ReLU in the BF16 conversion), stage each
+// warp's 32 rows in shared memory and store them transposed (four whole
+// 128-byte lines per instruction). Loads, MMAs and stores of successive
+// tiles overlap; every wait is bounded.
 constexpr int kSxT = 8, kSyT = 128, kSzT = 2;
 constexpr int kSRows = kSyT + 2;                          // staged rows per plane (y halo)
 constexpr int kSPlanes = kSzT + 2;                        // staged planes (z halo)
 constexpr int kSHalf = kSPlanes * kSRows * 16;            // bytes of one 8-value K half: 8320
-constexpr int kSABytes = 2 * kSHalf;                      // staged input (A): 16640
+constexpr int kSABytes = 2 * kSHalf;                      // one staged input tile (A): 16640
 constexpr int kSBBytes = 9 * 2 * 128 * 16;                // banded weights (B): 36864
-constexpr int kSThreads = 256;
-constexpr int kSCBytes = (kSThreads / 32) * 32 * 128;   // epilogue staging: 32 rows x 128 bytes a warp
+constexpr int kSEpiWarps = 8, kSProdWarps = 4;
+constexpr int kSThreads = (kSEpiWarps + kSProdWarps + 1) * 32;   // + the MMA warp: 416
+constexpr int kSCBytes = kSEpiWarps * 32 * 128;           // epilogue staging: 32 rows x 128 bytes a warp
 constexpr int kSChunks = kSPlanes * kSRows * 4;           // float4 chunks of a staged tile: 2080
-constexpr int kSPer = (kSChunks + kSThreads - 1) / kSThreads;   // 9 per thread
-// 86 KB a CTA: two CTAs share an SM (each holds 256 TMEM columns), never three
-constexpr int kSSmem = 86 * 1024;
-static_assert(kSABytes + kSBBytes + kSCBytes + 128 <= kSSmem, "stem buffers exceed the shared-memory request");
-static_assert(3 * (kSSmem + 2048) > 228 * 1024, "a third CTA per SM would wait for tensor memory");
-static_assert(kSHalf % 16 == 0, "operand halves start 16-byte aligned");
+constexpr int kSPer = (kSChunks + kSProdWarps * 32 - 1) / (kSProdWarps * 32);   // 17 per producer thread
+// 120 KB a CTA: one CTA per SM (it holds all 512 TMEM columns)
+constexpr int kSSmem = 120 * 1024;
+static_assert(2 * kSABytes + kSBBytes + kSCBytes + 128 <= kSSmem, "stem buffers exceed the shared-memory request");
+static_assert(2 * (kSSmem + 2048) > 228 * 1024, "a second CTA per SM would wait for tensor memory");
+static_assert(kSHalf % 16 == 0 && kSABytes % 128 == 0, "operand buffers start 16-byte aligned");
 
 __device__ __forceinline__ void tmem_ld32(unsigned addr, float *v) {
     unsigned r[32];
@@ -694,35 +703,56 @@ __device__ __forceinline__ unsigned bf16x2_bits(float lo, float hi) {
     return *reinterpret_cast<unsigned *>(&h);
 }
 
+struct StemTile {
+    int tx, ty, tz;
+    long long nb;
+};
+__device__ __forceinline__ StemTile stem_tile(int t, int ntx, int nty, int ntz) {
+    StemTile r;
+    r.tx = t % ntx;
+    t /= ntx;
+    r.ty = t % nty;
+    t /= nty;
+    r.tz = t % ntz;
+    r.nb = t / ntz;
+    return r;
+}
+
 template <bool POOL, bool RELU>
-__global__ void __launch_bounds__(kSThreads, 2)
+__global__ void __launch_bounds__(kSThreads, 1)
 stem_fwd_tc(const float *__restrict__ x, const bf16 *__restrict__ w, const float *__restrict__ b,
             bf16 *__restrict__ y, int ycs, int yco, bf16 *__restrict__ pooled, int D, int H, int W,
             int ntiles, unsigned *err, unsigned long long timeout_ns) {
     extern __shared__ unsigned char smem_raw[];
     unsigned char *smem = reinterpret_cast<unsigned char *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~(uintptr_t)127);
-    unsigned char *As = smem;              // [half][plane][row][8 BF16]: staged input
-    unsigned char *Bs = smem + kSABytes;   // [kz ky][half][16 xo + c][8 BF16]: banded weights
-    unsigned char *Cs = Bs + kSBBytes;     // per warp [row][8 x 16 bytes], 16-byte slots XOR-swizzled by row
-    __shared__ __align__(8) unsigned long long mma_bar;
+    unsigned char *As = smem;                  // two of [half][plane][row][8 BF16]: staged input
+    unsigned char *Bs = smem + 2 * kSABytes;   // [kz ky][half][16 xo + c][8 BF16]: banded weights
+    unsigned char *Cs = Bs + kSBBytes;         // per epilogue warp [row][8 x 16 bytes], slots XOR-swizzled by row
+    __shared__ __align__(8) unsigned long long a_full[2], a_empty[2], t_full[2][kSzT], t_empty[2], done_bar;
     __shared__ unsigned tmem_base;
     __shared__ float wsm[16 * 27];
-    __shared__ float bsm[16];   // bias, carried by the MMA: K slots 0 and 1 of every staged row hold 1.0
+    __shared__ float bsm[16];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int ntx = W / kSxT, nty = (H + kSyT - 1) / kSyT, ntz = (D + kSzT - 1) / kSzT;
+    const int mma_warp = kSEpiWarps + kSProdWarps;
 
     for (int i = tid; i < 16 * 27; i += kSThreads) wsm[i] = __bfloat162float(w[i]);
     if (tid < 16) bsm[tid] = b ? b[tid] : 0.0f;
     if (tid == 0) {
-        mbar_init(&mma_bar, 1);
+        for (int s = 0; s < 2; ++s) {
+            mbar_init(&a_full[s], kSProdWarps * 32);
+            mbar_init(&a_empty[s], 1);
+            mbar_init(&t_empty[s], kSEpiWarps);
+            for (int zz = 0; zz < kSzT; ++zz) mbar_init(&t_full[s][zz], 1);
+        }
+        mbar_init(&done_bar, 1);
         fence_barrier_init();
     }
     __syncthreads();
-    // banded weights: 16-byte row (g = 3 kz + ky, half, n = 16 xo + c) holds j = 8 half .. 8 half + 7.
-    // The band uses j = 3 .. 12; in (kz, ky) = (0, 0), j = 0 and 1 carry the
-    // bias as hi = bf16(b) and lo = bf16(b - hi) (within 2^-16 of b), against
-    // the 1.0 staged in those K slots.
+    // banded weights: 16-byte row (g = 3 kz + ky, half, n = 16 xo + c) holds j = 8 half .. 8 half + 7;
+    // the band uses j = 3 .. 12, and j = 0, 1 of (kz, ky) = (0, 0) hold the bias as
+    // hi = bf16(b) and lo = bf16(b - hi) (within 2^-16 of b)
     for (int q = tid; q < 9 * 2 * 128; q += kSThreads) {
         const int nn = q & 127, half = (q >> 7) & 1, g = q >> 8;
         const int xo = nn >> 4, c = nn & 15;
@@ -742,9 +772,9 @@ stem_fwd_tc(const float *__restrict__ x, const bf16 *__restrict__ w, const float
         }
         *reinterpret_cast<uint4 *>(Bs + q * 16) = make_uint4(v[0], v[1], v[2], v[3]);
     }
-    if (warp == 0) {
+    if (warp == mma_warp) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(s_u32(&tmem_base)),
-                     "r"(256));
+                     "r"(512));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // generic writes -> tensor core reads
@@ -753,166 +783,185 @@ stem_fwd_tc(const float *__restrict__ x, const bf16 *__restrict__ w, const float
     asm volatile("tcgen05.fence::after_thread_sync;");
     const unsigned tmem = tmem_base;
 
-    // Input chunk i of this thread: float4 q = tid + 256 i of the staged tile,
-    // row q / 4 (plane p, row r), values 4 (q mod 4) .. + 3 of the K window.
-    float4 pre[kSPer];
-    auto load_tile = [&](int tile) {
-        int t = tile;
-        const int tx = t % ntx;
-        t /= ntx;
-        const int ty = t % nty;
-        t /= nty;
-        const int tz = t % ntz;
-        const long long nb = t / ntz;
+    if (warp >= kSEpiWarps && warp < mma_warp) {
+        // ---- producers: input chunk i of thread p is float4 q = p + 128 i of the
+        // tile, staged row q / 4 (plane, row), K values 4 (q mod 4) .. + 3
+        const int p = tid - kSEpiWarps * 32;
+        int s = 0;
+        unsigned ph = 0;
+        for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+            const StemTile T = stem_tile(tile, ntx, nty, ntz);
+            float4 pre[kSPer];
 #pragma unroll
-        for (int i = 0; i < kSPer; ++i) {
-            const int q = tid + kSThreads * i;
-            const int row = q >> 2, part = q & 3;
-            const int p = row / kSRows, r = row - p * kSRows;
-            const int z = tz * kSzT - 1 + p, yy = ty * kSyT - 1 + r, xx = tx * kSxT - 4 + 4 * part;
-            const bool ok = q < kSChunks && z >= 0 && z < D && yy >= 0 && yy < H && xx >= 0 && xx < W;
-            pre[i] = ok ? __ldg(reinterpret_cast<const float4 *>(x + ((nb * D + z) * H + yy) * (long long)W + xx))
-                        : make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-    };
-    auto store_tile = [&]() {
-#pragma unroll
-        for (int i = 0; i < kSPer; ++i) {
-            const int q = tid + kSThreads * i;
-            if (q < kSChunks) {
+            for (int i = 0; i < kSPer; ++i) {
+                const int q = p + kSProdWarps * 32 * i;
                 const int row = q >> 2, part = q & 3;
-                const unsigned a = s_u32(As + (part >> 1) * kSHalf + row * 16 + (part & 1) * 8);
-                // K slots 0 and 1 (values x0 - 4, x0 - 3, outside every output's taps) hold 1.0
-                const unsigned lo = part == 0 ? 0x3F803F80u : bf16x2_bits(pre[i].x, pre[i].y);
-                asm volatile("st.shared.v2.b32 [%0], {%1, %2};" ::"r"(a), "r"(lo), "r"(bf16x2_bits(pre[i].z, pre[i].w))
-                             : "memory");
+                const int pl = row / kSRows, r = row - pl * kSRows;
+                const int z = T.tz * kSzT - 1 + pl, yy = T.ty * kSyT - 1 + r, xx = T.tx * kSxT - 4 + 4 * part;
+                const bool ok = q < kSChunks && z >= 0 && z < D && yy >= 0 && yy < H && xx >= 0 && xx < W;
+                pre[i] = ok ? __ldg(reinterpret_cast<const float4 *>(x + ((T.nb * D + z) * H + yy) * (long long)W + xx))
+                            : make_float4(0.f, 0.f, 0.f, 0.f);
             }
+            if (!mbar_wait_bounded(&a_empty[s], ph ^ 1u, timeout_ns)) {
+                atomicOr(err, DEV_ERR_TIMEOUT);
+                break;
+            }
+            unsigned char *A = As + s * kSABytes;
+#pragma unroll
+            for (int i = 0; i < kSPer; ++i) {
+                const int q = p + kSProdWarps * 32 * i;
+                if (q < kSChunks) {
+                    const int row = q >> 2, part = q & 3;
+                    const unsigned a = s_u32(A + (part >> 1) * kSHalf + row * 16 + (part & 1) * 8);
+                    const unsigned lo = part == 0 ? 0x3F803F80u : bf16x2_bits(pre[i].x, pre[i].y);
+                    asm volatile("st.shared.v2.b32 [%0], {%1, %2};" ::"r"(a), "r"(lo),
+                                 "r"(bf16x2_bits(pre[i].z, pre[i].w))
+                                 : "memory");
+                }
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            mbar_arrive(&a_full[s]);
+            s ^= 1;
+            ph ^= (unsigned)(s == 0);
         }
-    };
-
-    const int quarter = warp & 3, xh = warp >> 2;   // TMEM lanes 32 quarter .., voxels xo = 4 xh .. 4 xh + 3
-    unsigned phase = 0;
-    bool timed_out = false;
-    if (blockIdx.x < ntiles) load_tile(blockIdx.x);
-    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        store_tile();
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        asm volatile("tcgen05.fence::before_thread_sync;");
-        __syncthreads();
-        asm volatile("tcgen05.fence::after_thread_sync;");
-        if (tid == 0) {
-            // A: no swizzle, K halves kSHalf apart (LBO), 8-row groups 128 bytes apart (SBO)
-            const unsigned a_base = s_u32(As), b_base = s_u32(Bs);
+    } else if (warp == mma_warp) {
+        // ---- MMA issue (lane 0): 9 MMAs per output slice, each slice committed on its own
+        if (lane == 0) {
+            int s = 0, a = 0;
+            unsigned ph = 0, aph = 0;
             const unsigned idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(128 >> 3) << 17) |
                                    ((unsigned)(128 >> 4) << 24);
-#pragma unroll
-            for (int zz = 0; zz < kSzT; ++zz)
-#pragma unroll
-                for (int g = 0; g < 9; ++g) {
-                    const int kz = g / 3, ky = g % 3;
-                    const unsigned long long ad = smem_desc(a_base + ((zz + kz) * kSRows + ky) * 16, kSHalf, 128);
-                    const unsigned long long bd = smem_desc(b_base + g * 4096, 2048, 128);
-                    asm volatile(
-                        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem + (unsigned)(zz * 128)),
-                        "l"(ad), "l"(bd), "r"(idesc), "r"(g > 0 ? 1u : 0u));
+            const unsigned b_base = s_u32(Bs);
+            for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+                if (!mbar_wait_bounded(&t_empty[a], aph ^ 1u, timeout_ns) ||
+                    !mbar_wait_bounded(&a_full[s], ph, timeout_ns)) {
+                    atomicOr(err, DEV_ERR_TIMEOUT);
+                    break;
                 }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                s_u32(&mma_bar)));
-        }
-        const int tile_now = tile;
-        if (tile + (int)gridDim.x < ntiles) load_tile(tile + gridDim.x);   // lands while the MMAs run
-        const bool ok = mbar_wait_bounded(&mma_bar, phase, timeout_ns);
-        phase ^= 1u;
-        if (__syncthreads_or(!ok)) {
-            timed_out = true;
-            break;
-        }
-        asm volatile("tcgen05.fence::after_thread_sync;");
-        // ---- epilogue: lane = row y0 + 32 quarter + lane, columns 16 xo + c of slices z0, z0 + 1
-        int t = tile_now;
-        const int tx = t % ntx;
-        t /= ntx;
-        const int ty = t % nty;
-        t /= nty;
-        const int tz = t % ntz;
-        const long long nb = t / ntz;
-        const int yy = ty * kSyT + 32 * quarter + lane;
-        const bool yok = yy < H;
-        // A thread's row is 4 voxels = 128 contiguous bytes of y; the rows of a
-        // warp lie W voxels apart. Each warp stages its 32 rows in shared memory
-        // and stores them transposed: 8 lanes per row, 4 whole rows (128-byte
-        // lines) per instruction, where direct stores would touch 32 lines each.
-        unsigned char *cw = Cs + warp * 4096;
-        const int x0w = tx * kSxT + 4 * xh;   // first voxel of the warp's rows
-        unsigned mx[2][8];                    // running maxima of the pooling windows, BF16 pairs
-#pragma unroll 1
-        for (int zz = 0; zz < kSzT; ++zz) {
-            const int z = tz * kSzT + zz;
+                asm volatile("tcgen05.fence::after_thread_sync;");
+                const unsigned a_base = s_u32(As + s * kSABytes);
 #pragma unroll
-            for (int pp = 0; pp < 2; ++pp) {   // voxels 4 xh + 2 pp, + 1
-                float v[32];
-                tmem_ld32(tmem + ((unsigned)(32 * quarter) << 16) + (unsigned)(zz * 128 + (4 * xh + 2 * pp) * 16), v);
+                for (int zz = 0; zz < kSzT; ++zz) {
 #pragma unroll
-                for (int e = 0; e < 2; ++e) {
-                    unsigned q[8];
-#pragma unroll
-                    for (int k = 0; k < 8; ++k) {
-                        q[k] = cvt_bf16x2<RELU>(v[16 * e + 2 * k], v[16 * e + 2 * k + 1]);
-                        if constexpr (POOL) mx[pp][k] = (zz == 0 && e == 0) ? q[k] : max_bf16x2(mx[pp][k], q[k]);
+                    for (int g = 0; g < 9; ++g) {
+                        const int kz = g / 3, ky = g % 3;
+                        // A: no swizzle, K halves kSHalf apart (LBO), 8-row groups 128 bytes apart (SBO)
+                        const unsigned long long ad = smem_desc(a_base + ((zz + kz) * kSRows + ky) * 16, kSHalf, 128);
+                        const unsigned long long bd = smem_desc(b_base + g * 4096, 2048, 128);
+                        asm volatile(
+                            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(
+                                tmem + (unsigned)(a * 256 + zz * 128)),
+                            "l"(ad), "l"(bd), "r"(idesc), "r"(g > 0 ? 1u : 0u));
                     }
-                    const int xo = 2 * pp + e;
-                    const int s0 = (2 * xo) ^ (lane & 7), s1 = (2 * xo + 1) ^ (lane & 7);
-                    *reinterpret_cast<uint4 *>(cw + lane * 128 + s0 * 16) = make_uint4(q[0], q[1], q[2], q[3]);
-                    *reinterpret_cast<uint4 *>(cw + lane * 128 + s1 * 16) = make_uint4(q[4], q[5], q[6], q[7]);
+                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                        s_u32(&t_full[a][zz])));
                 }
+                // the A buffer is free once these MMAs have read it
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                    s_u32(&a_empty[s])));
+                s ^= 1;
+                ph ^= (unsigned)(s == 0);
+                a ^= 1;
+                aph ^= (unsigned)(a == 0);
             }
+            // every MMA issued must be complete before the accumulators are freed
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                s_u32(&done_bar)));
+            if (!mbar_wait_bounded(&done_bar, 0, timeout_ns)) atomicOr(err, DEV_ERR_TIMEOUT);
+        }
+        __syncwarp();
+    } else {
+        // ---- epilogue: warp w drains TMEM lanes 32 (w mod 4) .. (rows y0 + 32 (w mod 4) + lane)
+        // and voxels 4 (w / 4) .. 4 (w / 4) + 3 of the tile
+        const int quarter = warp & 3, xh = warp >> 2;
+        unsigned char *cw = Cs + warp * 4096;
+        int a = 0;
+        unsigned aph = 0;
+        bool ok = true;
+        for (int tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
+            const StemTile T = stem_tile(tile, ntx, nty, ntz);
+            const int yy = T.ty * kSyT + 32 * quarter + lane;
+            const int x0w = T.tx * kSxT + 4 * xh;   // first voxel of the warp's rows
+            unsigned mx[2][8];                      // running maxima of the pooling windows, BF16 pairs
+#pragma unroll 1
+            for (int zz = 0; zz < kSzT; ++zz) {
+                int okw = lane == 0 ? (mbar_wait_bounded(&t_full[a][zz], aph, timeout_ns) ? 1 : 0) : 0;
+                okw = __shfl_sync(0xffffffffu, okw, 0);
+                if (!okw) {
+                    if (lane == 0) atomicOr(err, DEV_ERR_TIMEOUT);
+                    ok = false;
+                    break;
+                }
+                __syncwarp();
+                asm volatile("tcgen05.fence::after_thread_sync;");
+                const int z = T.tz * kSzT + zz;
+#pragma unroll
+                for (int pp = 0; pp < 2; ++pp) {   // voxels 4 xh + 2 pp, + 1
+                    float v[32];
+                    tmem_ld32(tmem + ((unsigned)(32 * quarter) << 16) +
+                                  (unsigned)(a * 256 + zz * 128 + (4 * xh + 2 * pp) * 16),
+                              v);
+#pragma unroll
+                    for (int e = 0; e < 2; ++e) {
+                        unsigned q[8];
+#pragma unroll
+                        for (int k = 0; k < 8; ++k) {
+                            q[k] = cvt_bf16x2<RELU>(v[16 * e + 2 * k], v[16 * e + 2 * k + 1]);
+                            if constexpr (POOL) mx[pp][k] = (zz == 0 && e == 0) ? q[k] : max_bf16x2(mx[pp][k], q[k]);
+                        }
+                        const int xo = 2 * pp + e;
+                        const int s0 = (2 * xo) ^ (lane & 7), s1 = (2 * xo + 1) ^ (lane & 7);
+                        *reinterpret_cast<uint4 *>(cw + lane * 128 + s0 * 16) = make_uint4(q[0], q[1], q[2], q[3]);
+                        *reinterpret_cast<uint4 *>(cw + lane * 128 + s1 * 16) = make_uint4(q[4], q[5], q[6], q[7]);
+                    }
+                }
+                __syncwarp();
+                // 8 lanes per row, 4 rows (128-byte lines) per store instruction
+                const int k = lane & 7;
+                bf16 *yrow = y + (((T.nb * D + z) * H + T.ty * kSyT + 32 * quarter) * (long long)W + x0w + (k >> 1)) *
+                                     ycs + yco + (k & 1) * 8;
+#pragma unroll
+                for (int it = 0; it < 8; ++it) {
+                    const int r = 4 * it + (lane >> 3);   // row of the warp
+                    const uint4 val = *reinterpret_cast<const uint4 *>(cw + r * 128 + ((k ^ (r & 7)) * 16));
+                    if (T.ty * kSyT + 32 * quarter + r < H && z < D)
+                        *reinterpret_cast<uint4 *>(yrow + (long long)r * W * ycs) = val;
+                }
+                __syncwarp();   // the staging rows are rewritten for the next slice
+            }
+            if (!ok) break;
+            // this accumulator set is read: the MMAs of a later tile may overwrite it
+            asm volatile("tcgen05.fence::before_thread_sync;");
             __syncwarp();
-            // 8 lanes per row, 4 rows (128-byte lines) per store instruction
-            const int k = lane & 7;
-            bf16 *yrow = y + (((nb * D + z) * H + ty * kSyT + 32 * quarter) * (long long)W + x0w + (k >> 1)) * ycs +
-                         yco + (k & 1) * 8;
+            if (lane == 0) mbar_arrive(&t_empty[a]);
+            a ^= 1;
+            aph ^= (unsigned)(a == 0);
+            if constexpr (POOL) {
+                // the y pair is lanes l and l ^ 1 (D, H even: a pair is whole or outside)
 #pragma unroll
-            for (int it = 0; it < 8; ++it) {
-                const int r = 4 * it + (lane >> 3);   // row of the warp
-                const uint4 val = *reinterpret_cast<const uint4 *>(cw + r * 128 + ((k ^ (r & 7)) * 16));
-                if (ty * kSyT + 32 * quarter + r < H && z < D)
-                    *reinterpret_cast<uint4 *>(yrow + (long long)r * W * ycs) = val;
-            }
-            __syncwarp();   // the staging rows are rewritten for the next slice
-        }
-        if constexpr (POOL) {
-            // the y pair is lanes l and l ^ 1 (D, H even: a pair is whole or outside)
+                for (int pp = 0; pp < 2; ++pp)
 #pragma unroll
-            for (int pp = 0; pp < 2; ++pp)
+                    for (int k = 0; k < 8; ++k)
+                        mx[pp][k] = max_bf16x2(mx[pp][k], __shfl_xor_sync(0xffffffffu, mx[pp][k], 1));
+                if (yy < H && (lane & 1) == 0) {
+                    const int Dh = D >> 1, Hh = H >> 1, Wh = W >> 1;
 #pragma unroll
-                for (int k = 0; k < 8; ++k) mx[pp][k] = max_bf16x2(mx[pp][k], __shfl_xor_sync(0xffffffffu, mx[pp][k], 1));
-            if (yok && (lane & 1) == 0) {
-                const int Dh = D >> 1, Hh = H >> 1, Wh = W >> 1;
-#pragma unroll
-                for (int pp = 0; pp < 2; ++pp) {
-                    uint4 *dst = reinterpret_cast<uint4 *>(
-                        pooled + (((nb * Dh + tz) * Hh + (yy >> 1)) * (long long)Wh + (x0w >> 1) + pp) * 16);
-                    dst[0] = make_uint4(mx[pp][0], mx[pp][1], mx[pp][2], mx[pp][3]);
-                    dst[1] = make_uint4(mx[pp][4], mx[pp][5], mx[pp][6], mx[pp][7]);
+                    for (int pp = 0; pp < 2; ++pp) {
+                        uint4 *dst = reinterpret_cast<uint4 *>(
+                            pooled + (((T.nb * Dh + T.tz) * Hh + (yy >> 1)) * (long long)Wh + (x0w >> 1) + pp) * 16);
+                        dst[0] = make_uint4(mx[pp][0], mx[pp][1], mx[pp][2], mx[pp][3]);
+                        dst[1] = make_uint4(mx[pp][4], mx[pp][5], mx[pp][6], mx[pp][7]);
+                    }
                 }
             }
-        }
-        asm volatile("tcgen05.fence::before_thread_sync;");
-        __syncthreads();   // TMEM read and the staged tile consumed before the next tile's MMAs
-    }
-    if (timed_out) {
-        if (tid == 0) {
-            atomicOr(err, DEV_ERR_TIMEOUT);
-            // the MMAs in flight must finish before their accumulators are freed
-            mbar_wait_bounded(&mma_bar, phase ^ 1u, timeout_ns);
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
-    if (warp == 0) {
+    if (warp == mma_warp) {
         asm volatile("tcgen05.fence::after_thread_sync;");
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256));
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
     }
 }
 
@@ -1119,8 +1168,7 @@ cudaError_t stem_fwd_tc_launch(const float *x, const void *w, const float *b, vo
     int sms = 0;
     e = sm_count(&sms);
     if (e != cudaSuccess) return e;
-    const long long g2 = 2LL * sms;
-    const unsigned grid = (unsigned)(nt < g2 ? nt : g2);
+    const unsigned grid = (unsigned)(nt < sms ? nt : sms);   // one CTA per SM
     auto k = pooled ? (relu ? stem_fwd_tc<true, true> : stem_fwd_tc<true, false>)
                     : (relu ? stem_fwd_tc<false, true> : stem_fwd_tc<false, false>);
     e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, kSSmem);
