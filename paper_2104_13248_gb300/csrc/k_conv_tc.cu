@@ -640,9 +640,11 @@ conv3d_fwd_tcp(const __grid_constant__ CUtensorMap xmap, int xco, const bf16 *__
 // its voxels: whole-voxel stores, and the 2 x 2 x 2 pooling needs one lane
 // shuffle (the y pair); the x pair and the z pair are its own columns.
 //
-// Persistent and warp-specialised, one CTA per SM: four producer warps load
-// a tile's input (FP32), round it to BF16 and stage it in one of two A
-// buffers; one thread issues the MMAs into one of two TMEM accumulator sets
+// Persistent and warp-specialised, one CTA per SM: a tile's FP32 input
+// (16 x 130 x 4 values, zero outside the volume) arrives by one TMA load two
+// tiles ahead into one of two staging buffers; four producer warps round it
+// to BF16 into one of two A buffers; one thread issues the MMAs into one of
+// two TMEM accumulator sets
 // (256 columns each), committing each output slice separately; eight
 // epilogue warps drain a slice (ReLU in the BF16 conversion), stage each
 // warp's 32 rows in shared memory and store them transposed (four whole
@@ -659,9 +661,11 @@ constexpr int kSThreads = (kSEpiWarps + kSProdWarps + 1) * 32;   // + the MMA wa
 constexpr int kSCBytes = kSEpiWarps * 32 * 128;           // epilogue staging: 32 rows x 128 bytes a warp
 constexpr int kSChunks = kSPlanes * kSRows * 4;           // float4 chunks of a staged tile: 2080
 constexpr int kSPer = (kSChunks + kSProdWarps * 32 - 1) / (kSProdWarps * 32);   // 17 per producer thread
-// 120 KB a CTA: one CTA per SM (it holds all 512 TMEM columns)
-constexpr int kSSmem = 120 * 1024;
-static_assert(2 * kSABytes + kSBBytes + kSCBytes + 128 <= kSSmem, "stem buffers exceed the shared-memory request");
+constexpr int kSFBytes = kSChunks * 16;                   // one FP32 input tile as the TMA writes it: 33280
+// one CTA per SM (it holds all 512 TMEM columns)
+constexpr int kSSmem = 2 * kSFBytes + 2 * kSABytes + kSBBytes + kSCBytes + 128;
+static_assert(kSSmem <= 227 * 1024, "stem buffers exceed the shared memory of a CTA");
+static_assert(kSFBytes % 128 == 0, "TMA destinations start 128-byte aligned");
 static_assert(2 * (kSSmem + 2048) > 228 * 1024, "a second CTA per SM would wait for tensor memory");
 static_assert(kSHalf % 16 == 0 && kSABytes % 128 == 0, "operand buffers start 16-byte aligned");
 
@@ -720,16 +724,18 @@ __device__ __forceinline__ StemTile stem_tile(int t, int ntx, int nty, int ntz) 
 
 template <bool POOL, bool RELU>
 __global__ void __launch_bounds__(kSThreads, 1)
-stem_fwd_tc(const float *__restrict__ x, const bf16 *__restrict__ w, const float *__restrict__ b,
+stem_fwd_tc(const __grid_constant__ CUtensorMap xmap, const bf16 *__restrict__ w, const float *__restrict__ b,
             bf16 *__restrict__ y, int ycs, int yco, bf16 *__restrict__ pooled, int D, int H, int W,
             int ntiles, unsigned *err, unsigned long long timeout_ns) {
     extern __shared__ unsigned char smem_raw[];
     unsigned char *smem = reinterpret_cast<unsigned char *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~(uintptr_t)127);
-    unsigned char *As = smem;                  // two of [half][plane][row][8 BF16]: staged input
-    unsigned char *Bs = smem + 2 * kSABytes;   // [kz ky][half][16 xo + c][8 BF16]: banded weights
+    unsigned char *Fs = smem;                  // two of [plane][row][16 FP32]: the input as loaded
+    unsigned char *As = Fs + 2 * kSFBytes;     // two of [half][plane][row][8 BF16]: staged input
+    unsigned char *Bs = As + 2 * kSABytes;     // [kz ky][half][16 xo + c][8 BF16]: banded weights
     unsigned char *Cs = Bs + kSBBytes;         // per epilogue warp [row][8 x 16 bytes], slots XOR-swizzled by row
-    __shared__ __align__(8) unsigned long long a_full[2], a_empty[2], t_full[2][kSzT], t_empty[2], done_bar;
+    __shared__ __align__(8) unsigned long long f_full[2], a_full[2], a_empty[2], t_full[2][kSzT], t_empty[2],
+        done_bar;
     __shared__ unsigned tmem_base;
     __shared__ float wsm[16 * 27];
     __shared__ float bsm[16];
@@ -741,6 +747,7 @@ stem_fwd_tc(const float *__restrict__ x, const bf16 *__restrict__ w, const float
     if (tid < 16) bsm[tid] = b ? b[tid] : 0.0f;
     if (tid == 0) {
         for (int s = 0; s < 2; ++s) {
+            mbar_init(&f_full[s], 1);
             mbar_init(&a_full[s], kSProdWarps * 32);
             mbar_init(&a_empty[s], 1);
             mbar_init(&t_empty[s], kSEpiWarps);
@@ -784,45 +791,69 @@ stem_fwd_tc(const float *__restrict__ x, const bf16 *__restrict__ w, const float
     const unsigned tmem = tmem_base;
 
     if (warp >= kSEpiWarps && warp < mma_warp) {
-        // ---- producers: input chunk i of thread p is float4 q = p + 128 i of the
-        // tile, staged row q / 4 (plane, row), K values 4 (q mod 4) .. + 3
+        // ---- producers: thread p rounds float4 chunks q = p + 128 i of the loaded
+        // tile (row q / 4, K values 4 (q mod 4) .. + 3) into the A buffer
         const int p = tid - kSEpiWarps * 32;
-        int s = 0;
-        unsigned ph = 0;
-        for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const bool leader = p == 0;
+        auto issue = [&](int tile, int fs) {
             const StemTile T = stem_tile(tile, ntx, nty, ntz);
-            float4 pre[kSPer];
-#pragma unroll
-            for (int i = 0; i < kSPer; ++i) {
-                const int q = p + kSProdWarps * 32 * i;
-                const int row = q >> 2, part = q & 3;
-                const int pl = row / kSRows, r = row - pl * kSRows;
-                const int z = T.tz * kSzT - 1 + pl, yy = T.ty * kSyT - 1 + r, xx = T.tx * kSxT - 4 + 4 * part;
-                const bool ok = q < kSChunks && z >= 0 && z < D && yy >= 0 && yy < H && xx >= 0 && xx < W;
-                pre[i] = ok ? __ldg(reinterpret_cast<const float4 *>(x + ((T.nb * D + z) * H + yy) * (long long)W + xx))
-                            : make_float4(0.f, 0.f, 0.f, 0.f);
-            }
-            if (!mbar_wait_bounded(&a_empty[s], ph ^ 1u, timeout_ns)) {
+            mbar_arrive_expect_tx(&f_full[fs], (unsigned)kSFBytes);
+            tma_load_4d(Fs + fs * kSFBytes, &xmap, T.tx * kSxT - 4, T.ty * kSyT - 1, T.tz * kSzT - 1, (int)T.nb,
+                        &f_full[fs]);
+        };
+        if (leader) {
+            for (int k = 0; k < 2; ++k)
+                if (blockIdx.x + k * (int)gridDim.x < ntiles) issue(blockIdx.x + k * gridDim.x, k);
+        }
+        int s = 0, k = 0;
+        unsigned ph = 0;
+        bool ok = true;
+        for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++k) {
+            const int fs = k & 1;
+            if (!mbar_wait_bounded(&f_full[fs], (unsigned)(k >> 1) & 1u, timeout_ns) ||
+                !mbar_wait_bounded(&a_empty[s], ph ^ 1u, timeout_ns)) {
                 atomicOr(err, DEV_ERR_TIMEOUT);
+                ok = false;
+            }
+            // the producers leave together if any wait ran out (they meet on named barrier 1)
+            unsigned any_out;
+            asm volatile(
+                "{\n .reg .pred q, r;\n setp.ne.u32 q, %1, 0;\n bar.red.or.pred r, 1, %2, q;\n"
+                " selp.u32 %0, 1, 0, r;\n}"
+                : "=r"(any_out)
+                : "r"(ok ? 0u : 1u), "r"(kSProdWarps * 32));
+            if (any_out) {
+                ok = false;
                 break;
             }
+            const unsigned char *F = Fs + fs * kSFBytes;
             unsigned char *A = As + s * kSABytes;
 #pragma unroll
             for (int i = 0; i < kSPer; ++i) {
                 const int q = p + kSProdWarps * 32 * i;
                 if (q < kSChunks) {
+                    const float4 v = *reinterpret_cast<const float4 *>(F + q * 16);
                     const int row = q >> 2, part = q & 3;
                     const unsigned a = s_u32(A + (part >> 1) * kSHalf + row * 16 + (part & 1) * 8);
-                    const unsigned lo = part == 0 ? 0x3F803F80u : bf16x2_bits(pre[i].x, pre[i].y);
-                    asm volatile("st.shared.v2.b32 [%0], {%1, %2};" ::"r"(a), "r"(lo),
-                                 "r"(bf16x2_bits(pre[i].z, pre[i].w))
+                    // K slots 0 and 1 (values x0 - 4, x0 - 3, outside every output's taps) hold 1.0
+                    const unsigned lo = part == 0 ? 0x3F803F80u : bf16x2_bits(v.x, v.y);
+                    asm volatile("st.shared.v2.b32 [%0], {%1, %2};" ::"r"(a), "r"(lo), "r"(bf16x2_bits(v.z, v.w))
                                  : "memory");
                 }
             }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             mbar_arrive(&a_full[s]);
+            // the loaded buffer is read by every producer: reload it two tiles ahead
+            asm volatile("bar.sync 1, %0;" ::"r"(kSProdWarps * 32));
+            if (leader && tile + 2 * (int)gridDim.x < ntiles) issue(tile + 2 * gridDim.x, fs);
             s ^= 1;
             ph ^= (unsigned)(s == 0);
+        }
+        // loads still in flight land before the CTA leaves
+        if (leader) {
+            for (int kk = k; kk < k + 2; ++kk)
+                if (blockIdx.x + kk * (int)gridDim.x < ntiles)
+                    mbar_wait_bounded(&f_full[kk & 1], (unsigned)(kk >> 1) & 1u, timeout_ns);
         }
     } else if (warp == mma_warp) {
         // ---- MMA issue (lane 0): 9 MMAs per output slice, each slice committed on its own
@@ -1169,11 +1200,23 @@ cudaError_t stem_fwd_tc_launch(const float *x, const void *w, const float *b, vo
     e = sm_count(&sms);
     if (e != cudaSuccess) return e;
     const unsigned grid = (unsigned)(nt < sms ? nt : sms);   // one CTA per SM
+    // the input as a 4-D FP32 tensor (x, y, z, batch); a box is one tile with
+    // its halo, zero outside the volume
+    if (!encode_fn()) return cudaErrorNotSupported;
+    CUtensorMap map;
+    cuuint64_t dims[4] = {(cuuint64_t)wd, (cuuint64_t)h, (cuuint64_t)d, (cuuint64_t)n};
+    cuuint64_t strides[3] = {(cuuint64_t)wd * 4, (cuuint64_t)wd * h * 4, (cuuint64_t)wd * h * d * 4};
+    cuuint32_t box[4] = {16, (cuuint32_t)kSRows, (cuuint32_t)kSPlanes, 1};
+    cuuint32_t estr[4] = {1, 1, 1, 1};
+    CUresult r = encode_fn()(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<float *>(x), dims, strides, box,
+                             estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
     auto k = pooled ? (relu ? stem_fwd_tc<true, true> : stem_fwd_tc<true, false>)
                     : (relu ? stem_fwd_tc<false, true> : stem_fwd_tc<false, false>);
     e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, kSSmem);
     if (e != cudaSuccess) return e;
-    k<<<grid, kSThreads, kSSmem, st>>>(x, (const bf16 *)w, b, (bf16 *)y, ycs, yco, (bf16 *)pooled, d, h, wd,
+    k<<<grid, kSThreads, kSSmem, st>>>(map, (const bf16 *)w, b, (bf16 *)y, ycs, yco, (bf16 *)pooled, d, h, wd,
                                        (int)nt, err, 2000000000ull);
     return cudaGetLastError();
 }
