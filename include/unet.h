@@ -142,13 +142,16 @@ bp_status cnn_relu_backward(void *g, int g_cstride, int g_coff, const void *y, i
 bp_status cnn_pack_input(const float *x, void *y, int cstride, long long nvox, void *stream);
 
 /* Input layer for a one-channel FP32 volume x [N][D][H][W] (the network's
- * first convolution, a GEMM whose K dimension is the 27 taps, on the tensor
- * cores with mma.sync; a GEMM over channels would spend 15/16 of its
- * products on zero channels):
+ * first convolution; a GEMM over channels would spend 15/16 of its products
+ * on zero channels):
  *   y[v][y_coff + co] = act(b[co] + sum_tap w[co][tap] * bf16(x[v + tap]))
  * x is rounded to BF16 (the network's activation type) before the products,
- * which accumulate in FP32 from the bias in tap order; act = ReLU when
- * relu != 0. w is BF16 [cout][27] (tap index (dz*3+dy)*3+dx), b FP32 [cout]
+ * which accumulate in FP32; act = ReLU when relu != 0. With cout 16, wd a
+ * multiple of 8 and x 16-byte aligned it runs on tcgen05, the three x taps
+ * in K against banded weights and the bias carried in the sum as two BF16
+ * parts (within 2^-16 of b); otherwise on mma.sync with K = the 27 taps,
+ * summed from the bias (cnn_set_tensor_path(0) forces mma.sync). The two
+ * differ by rounding order only. w is BF16 [cout][27] (tap index (dz*3+dy)*3+dx), b FP32 [cout]
  * (may be NULL), y BF16 [N][D][H][W][y_cstride]. cout is a multiple of 8 up
  * to 32, wd a multiple of 4, y_cstride and y_coff multiples of 8, y 16-byte
  * aligned; anything else returns BP_ERR_INVALID_ARG. */

@@ -1,8 +1,10 @@
 // The one-channel input layer and the additive skip connections of the
 // few-view correction network. The paper has no learned component; these
-// calls serve the few-view workload. The input layer's GEMM runs on the
-// tensor cores with mma.sync (its K dimension is the 27 taps); the skip
-// connections and the rest are element-wise passes on the CUDA cores.
+// calls serve the few-view workload. Where the width is a multiple of 8 and
+// Cout is 16 (the network's input layer), the layer runs on tcgen05 with the
+// x taps in K (stem_fwd_tc in k_conv_tc.cu); otherwise on the tensor cores
+// with mma.sync, its K dimension the 27 taps (below). The skip connections
+// and the rest are element-wise passes on the CUDA cores.
 //
 //   stem_fwd_mma    y[v][co] = act(b[co] + sum_tap w[co][tap] bf16(x[v + tap]))
 //                   for a one-channel FP32 volume: a GEMM whose K dimension
