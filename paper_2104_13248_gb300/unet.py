@@ -18,8 +18,9 @@ reaches about the same held-out error (RMSE ratio 0.39 against 0.36).
 
 The skip connections add (a projection to the finer level's width, nearest
 upsampling, then the sum), so every level-1 convolution has 16 input and 16
-output channels. The one-channel input layer is a tap GEMM
-(cnn_stem_forward), the output head is the usual U-Net 1x1x1 projection
+output channels. The one-channel input layer (cnn_stem_forward, or
+cnn_stem_pool_forward with the first pooling) puts its taps into the GEMM's
+K dimension instead of channels, the output head is the usual U-Net 1x1x1 projection
 (cnn_head1_*); every other convolution is a BF16 implicit GEMM on the
 tensor cores with FP32 accumulation (cnn_conv3d_* in include/unet.h).
 Activations and their gradients are BF16 channels-last tensors; the master
