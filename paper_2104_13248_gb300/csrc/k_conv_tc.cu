@@ -1106,11 +1106,14 @@ cudaError_t conv_fwd_tc(const void *x, int xcs, int xco, const void *w, const fl
     const unsigned long long timeout_ns = 2000000000ull;
     const int nch = cin / 16;
     // the persistent kernel keeps every chunk's weights resident; Cout 64
-    // (width-64 layers) runs as two launches of 32 output channels, each
-    // writing its channel slice (the bricks stay in L2 between them)
-    const int cpl = cout == 64 ? 32 : cout;   // output channels per launch
+    // (width-64 layers) runs in one launch where all 64 channels' weights fit
+    // beside the bricks (Cin 32), otherwise as two launches of 32 output
+    // channels, each writing its channel slice (the bricks stay in L2 between them)
+    const bool one64 = cout == 64 && TW == 64 && TcpCfg<64, 64>::smem(nch) <= kPSmemLimit;
+    const int cpl = cout == 64 && !one64 ? 32 : cout;   // output channels per launch
     const int psmem = TW == 128 ? (cpl == 16 ? TcpCfg<16, 128>::smem(nch) : TcpCfg<32, 128>::smem(nch))
-                                : (cpl == 16 ? TcpCfg<16, 64>::smem(nch) : TcpCfg<32, 64>::smem(nch));
+                                : (cpl == 16 ? TcpCfg<16, 64>::smem(nch)
+                                             : cpl == 32 ? TcpCfg<32, 64>::smem(nch) : TcpCfg<64, 64>::smem(nch));
     if (g_tc_mode == 1 && psmem <= kPSmemLimit && (TW == 64 || cout != 64)) {
         // rows of 16 channels (32 bytes), 32-byte swizzle
         cuuint32_t box16[5] = {16, (cuuint32_t)(TW + 2), (cuuint32_t)kBY, (cuuint32_t)kBZ, 1};
@@ -1144,7 +1147,9 @@ cudaError_t conv_fwd_tc(const void *x, int xcs, int xco, const void *w, const fl
                 if (fused_head) TCP_CASE(32, kEpiHead, 128) else if (yf32) TCP_CASE(32, kEpiF32, 128) else TCP_CASE(32, kEpiBf16, 128)
             }
         } else {
-            if (cpl == 16) {
+            if (cpl == 64) {
+                if (yf32) TCP_CASE(64, kEpiF32, 64) else TCP_CASE(64, kEpiBf16, 64)
+            } else if (cpl == 16) {
                 if (yf32) TCP_CASE(16, kEpiF32, 64) else TCP_CASE(16, kEpiBf16, 64)
             } else {
                 if (yf32) TCP_CASE(32, kEpiF32, 64) else TCP_CASE(32, kEpiBf16, 64)
